@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""RMTR seconds per load step on the 3D 129^3 four-level workload (20
+penny-shaped fractures, pressure ramp p_t = 5e-4 t), plus the Hessian-vector
+product's throughput and roofline, on one GB300.
+
+One "step" is one pseudo-time load step: pressure_set + rmtr_load_step (all
+of the hot path: energy, gradient, hessvec, projected CG, TR control,
+transfers, coarse feasible set, level model, V-cycles).  Inputs are seeded
+synthetic fracture networks (no dataset); the state lives in HBM.
+
+  python bench.py [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference      # the FP64 CPU oracle, bounded sample
+
+Multi-GPU: the path does not shard across GPUs here, so N ranks run N
+independent replicas (one workload each; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pfinputs as PI  # noqa: E402
+
+WORKLOAD = {
+    "workload": "3d_129^3_q1_4level_20discs_ramp",
+    "dim": 3, "n_coarse": [17, 17, 17], "levels": 4, "h_coarse": 1.0 / 16,
+    "E": 1.0, "nu": 0.25, "Gc": 1.0, "ls_over_h": 2.0,
+    "fractures": 20, "seed": PI.SEED_3D_PLAIN, "dp": 5e-4,
+}
+METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same GB300"
+UNIT = "s/load-step"
+
+# Finest-level-equivalent element passes per load step of the CUDA path on
+# this workload (FP64, first-order coarse model), measured by this script's
+# GPU arm (printed as "work_model"); they scale the oracle's per-pass
+# seconds to seconds per load step for the CPU baseline and reference arm.
+REF_WORK_MODEL = {"fe_hessvec": 400.0, "fe_gradient": 10.0, "fe_energy": 30.0}
+
+# FP64 flops per element of the Hessian-vector product as implemented
+# (sum-factorised interpolation of 8 fields, 8 Gauss-point updates, 4
+# adjoint contractions; an FMA counts 2).
+HESSVEC_FP64_FLOPS_PER_ELEMENT = 2500.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--coarse-model", choices=["first_order", "galerkin"], default="first_order")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_pass_seconds(budget_s=20.0):
+    """Seconds per finest-level hessvec / gradient / energy-difference pass of
+    the FP64 oracle on the 129^3 workload state (one call each, repeated
+    while the budget lasts)."""
+    from oracle import pf_oracle as O
+    W = WORKLOAD
+    H = O.Hierarchy(3, W["n_coarse"], W["h_coarse"], W["levels"],
+                    O.Params(E=W["E"], nu=W["nu"], Gc=W["Gc"], p=W["dp"]))
+    g = H.fine
+    x = np.zeros(4 * g.N)
+    x[3 * g.N:] = O.rasterize(g, O.DISC3D, PI.disc_network_3d(W["seed"], W["fractures"]), g.h)
+    x[:3 * g.N] = PI.random_direction(5, 3 * g.N, 1e-4)
+    v = PI.random_direction(6, x.size, 1e-4)
+    times = {"hessvec": [], "gradient": [], "energy": []}
+    t_end = time.perf_counter() + budget_s
+    while True:
+        t = time.perf_counter(); O.hessvec(g, H.prm, x, v); times["hessvec"].append(time.perf_counter() - t)
+        t = time.perf_counter(); O.gradient(g, H.prm, x); times["gradient"].append(time.perf_counter() - t)
+        t = time.perf_counter(); O.energy_diff(g, H.prm, x, v); times["energy"].append(time.perf_counter() - t)
+        if time.perf_counter() > t_end:
+            break
+    return {k: min(v) for k, v in times.items()}, g
+
+
+def oracle_seconds_per_load_step(pass_s, work):
+    return (pass_s["hessvec"] * work["fe_hessvec"] + pass_s["gradient"] * work["fe_gradient"]
+            + pass_s["energy"] * work["fe_energy"])
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    vals = []
+    sample = None
+    for _ in range(args.warmup):
+        oracle_pass_seconds(budget_s=0.0)
+    for _ in range(args.steps):
+        pass_s, g = oracle_pass_seconds(budget_s=0.0)
+        vals.append(oracle_seconds_per_load_step(pass_s, REF_WORK_MODEL))
+        sample = pass_s
+    v = statistics.median(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {k: WORKLOAD[k] for k in ("workload", "n_coarse", "levels", "fractures")},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": ("one FP64 numpy oracle pass each of hessvec, gradient and energy "
+                                    "difference on the full 129^3 state per step, scaled by the CUDA path's "
+                                    f"finest-equivalent passes per load step {REF_WORK_MODEL}"),
+                         "pass_seconds": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2007_12908_gb300 import build
+    build.build()
+    import paper_2007_12908_gb300 as pf
+    from paper_2007_12908_gb300 import _binding as B
+
+    W = WORKLOAD
+    prm = pf.default_params(
+        precision=pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64,
+        coarse_model=pf.PF_GALERKIN if args.coarse_model == "galerkin" else pf.PF_FIRST_ORDER)
+    H = pf.mesh_hierarchy_create(3, W["n_coarse"], W["levels"], W["h_coarse"], E=W["E"],
+                                 nu=W["nu"], Gc=W["Gc"], ls_over_h=W["ls_over_h"])
+    g_n, g_h, N = H.levels[-1]
+    ndof = H.ndof()
+    x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
+    rows = PI.disc_network_3d(W["seed"], W["fractures"])
+    pf.fractures_set(H, pf.PF_DISC3D, rows, g_h, x)
+    stream = torch.cuda.current_stream()
+
+    def load_step(t, xx):
+        pf.pressure_set(H, W["dp"] * t)
+        return pf.rmtr_load_step(H, xx, prm, check=False)
+
+    for t in range(1, args.warmup + 1):
+        st = load_step(t, x)
+    x_after_warmup = x.clone()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+        stats.append(load_step(t, x))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+
+    # ---- dominant kernel: Hessian-vector product at the finest level
+    v = torch.from_numpy(PI.random_direction(77, ndof, 1e-3)).cuda()
+    out = torch.empty_like(v)
+
+    def time_kernel(fn, reps=20):
+        for _ in range(3):
+            fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e-3
+
+    level = W["levels"] - 1
+    t64 = time_kernel(lambda: pf.hessvec(H, level, x, v, out))
+    x32, v32 = x.float(), v.float()
+    o32 = torch.empty_like(v32)
+    t32 = time_kernel(lambda: pf.hessvec(H, level, x32, v32, o32))
+    t_grad = time_kernel(lambda: pf.gradient(H, level, x, out))
+    n_elem = (g_n[0] - 1) * (g_n[1] - 1) * (g_n[2] - 1)
+    fma64 = B.probe_fma(pf.PF_FP64)
+    hbm = None
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        hbm_src = "measured"
+    except (OSError, KeyError, ValueError):
+        hbm, hbm_src = 6800.0, "fallback"
+    bytes64 = 24.0 * ndof
+    bytes32 = 12.0 * ndof
+    flops64 = HESSVEC_FP64_FLOPS_PER_ELEMENT * n_elem
+    roof64 = {"kernel": "hessvec_fp64", "bound": "alu", "achieved": flops64 / t64 / 1e12,
+              "peak": fma64 / 1e12, "unit": "TFLOP/s", "frac": flops64 / t64 / fma64,
+              "traffic": None, "peak_source": "measured FP64 FMA probe (pf_probe_fma)",
+              "hbm_gbs": bytes64 / t64 / 1e9, "hbm_frac": bytes64 / t64 / 1e9 / hbm,
+              "gdofs": ndof / t64 / 1e9, "us_per_launch": t64 * 1e6}
+    roof32 = {"kernel": "hessvec_fp32", "bound": "hbm", "achieved": bytes32 / t32 / 1e9,
+              "peak": hbm, "unit": "GB/s", "frac": bytes32 / t32 / 1e9 / hbm, "traffic": None,
+              "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+              "gdofs": ndof / t32 / 1e9, "us_per_launch": t32 * 1e6}
+    roofline = roof64 if args.precision == "fp64" else roof32
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(ndof, dtype=torch.float64, pin_memory=True)
+        xh.copy_(x_after_warmup.cpu())
+        xn = xh.numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+            pf.pressure_set(H, W["dp"] * t)
+            pf.rmtr_load_step_host(H, xn, prm, check=False)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
+               "d2h_bytes_per_step": 8 * ndof}
+
+    work = {k: statistics.mean(s[k] for s in stats) for k in ("fe_hessvec", "fe_gradient", "fe_energy")}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pass_s, _ = oracle_pass_seconds(budget_s=10.0)
+        cpu = {"value": oracle_seconds_per_load_step(pass_s, work), "unit": UNIT,
+               "cores": 1, "kind": "oracle",
+               "sample": ("FP64 numpy oracle: one hessvec, gradient and energy-difference pass on the "
+                          "full 129^3 state (best of repeats within 10 s), scaled by this run's "
+                          "finest-equivalent passes per load step"),
+               "pass_seconds": pass_s}
+
+    launches = int(sum(s["launches"] for s in stats))
+    value = ms / 1e3
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": W["workload"], "grid": list(g_n), "levels": W["levels"],
+                       "dofs": ndof, "fractures": W["fractures"], "pressure_steps": [
+                           W["dp"] * t for t in range(args.warmup + 1, args.warmup + args.steps + 1)],
+                       "precision": args.precision, "coarse_model": args.coarse_model,
+                       "parallelism": f"replicas{world}",
+                       "l2": "working set > L2 (FP64 vectors 69 MB each, >20 resident)"},
+            "roofline": roofline,
+            "roofline_other": roof32 if roofline is roof64 else roof64,
+            "hessvec_gdofs": {"fp64": ndof / t64 / 1e9, "fp32": ndof / t32 / 1e9},
+            "gradient_fp64_us": t_grad * 1e6,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "work_model": work,
+            "solver": {k: [s[k] for s in stats] for k in ("cycles", "converged", "cg", "tr_its",
+                                                          "tr_rejected", "coarse_rejected", "status")},
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

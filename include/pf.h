@@ -1,0 +1,196 @@
+/*
+ * libpf -- GB300 (sm_103a) hot path of the recursive multilevel trust-region
+ * (RMTR) solver for pressure-induced AT2 phase-field fracture.
+ *
+ * Method: Zulian, Kopanicakova et al., "Large scale simulation of pressure
+ * induced phase-field fracture propagation using Utopia" (arXiv 2007.12908).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns a pf_status and never aborts.  pf_last_error() returns
+ *   a message for the calling thread's most recent failure.
+ * - State vectors hold (d+1) planes [u_x, u_y, (u_z), c] of N nodal values
+ *   each, lexicographic with x fastest (node (i,j,k) -> i + n_x (j + n_y k)).
+ *   A level's vector therefore has (d+1) * N entries.
+ * - "dev" pointers are device memory owned by the caller (borrowed: they must
+ *   stay valid until the library's stream is synchronised).  "host" pointers
+ *   are ordinary host memory read or written before the call returns.
+ * - All device work is enqueued on the cudaStream_t given in pf_mesh_desc
+ *   (passed as void*).  Calls returning host scalars synchronise that stream.
+ * - Precision codes: PF_FP64 (double) or PF_FP32 (float) for vector arguments.
+ * - Level index 0 is the coarsest grid, n_levels-1 the finest (the paper's
+ *   l = 1 ... L).
+ * - The library owns only its internal buffers; pf_mesh_hierarchy_destroy
+ *   frees them.
+ */
+#ifndef PF_H
+#define PF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pf_status;
+#define PF_OK 0
+#define PF_EINVAL 1      /* bad argument (size, level, pointer, kind)        */
+#define PF_ENOMEM 2      /* device or host allocation failed                 */
+#define PF_ECUDA 3       /* a CUDA runtime call failed                       */
+#define PF_ENONFINITE 4  /* a NaN/Inf appeared in an input or a result       */
+#define PF_ENOTCONV 5    /* rmtr_load_step hit max_cycles                    */
+#define PF_ETIMEOUT 6    /* a bounded device wait ran out                    */
+#define PF_ESTATE 7      /* call order violated (e.g. no fractures set)      */
+
+#define PF_FP64 0
+#define PF_FP32 1
+
+#define PF_GALERKIN 0    /* coarse model Hessian R H_{l+1} I (second order)   */
+#define PF_FIRST_ORDER 1 /* coarse model Hessian = Hessian of f~ at x0        */
+
+#define PF_LINE2D 0 /* rows [cx, cy, theta, half_length]                      */
+#define PF_DISC3D 1 /* rows [cx, cy, cz, nx, ny, nz, radius], |n| = 1         */
+
+typedef struct pf_hierarchy pf_hierarchy;
+
+/* Structured grid hierarchy and material (Sec. 2 and Sec. 4.1, steps 2-4). */
+typedef struct {
+  int dim;            /* 2 or 3                                              */
+  int n_coarse[3];    /* nodes per axis on the coarsest level (>= 2)         */
+  int n_levels;       /* >= 1; level l has (n_coarse-1) 2^l + 1 nodes/axis   */
+  double h_coarse;    /* node spacing of the coarsest level                  */
+  double E, nu;       /* Young's modulus, Poisson ratio (Lame via plane strain
+                         in 2D)                                              */
+  double Gc;          /* fracture toughness                                  */
+  double ls_over_h;   /* l_s = ls_over_h * h_finest on every level (Sec. 5: 2) */
+  double k_res;       /* residual stiffness in g(c) = (1-k)(1-c)^2 + k (0)   */
+  void* stream;       /* cudaStream_t for all work (NULL = legacy stream)    */
+} pf_mesh_desc;
+
+/* Trust-region and RMTR controls (Algorithms 1-3). */
+typedef struct {
+  double eta1, eta2;     /* acceptance / expansion thresholds (0.1, 0.75)    */
+  double gamma1, gamma2; /* radius shrink / expand factors (0.5, 2.0)        */
+  double delta0;         /* initial TR radius (inf-norm) per load step (1.0) */
+  double delta_max;      /* cap on the radius (1.0)                          */
+  int mu1, mu2;          /* pre/post smoothing TR steps (1, 1)               */
+  int coarse_its;        /* TR steps on the coarsest level (10)              */
+  int cg_fine;           /* CG budget per subproblem, finest level (50)      */
+  int cg_smooth;         /* ... intermediate levels (10)                     */
+  int cg_coarse;         /* ... coarsest level (500)                         */
+  int cauchy_backtracks; /* Cauchy / projected-search halvings (30)          */
+  double cauchy_c;       /* sufficient-decrease constant (0.01)              */
+  int max_cycles;        /* V-cycles per load step (200)                     */
+  double rtol;           /* stop when ||x - P(x - grad f)|| <= rtol * start  */
+  double atol;           /* ... or <= atol                                   */
+  int coarse_model;      /* PF_GALERKIN or PF_FIRST_ORDER                    */
+  int precision;         /* PF_FP64, or PF_FP32 = mixed: FP32 hessvec and CG,
+                            FP64 energy, gradient, rho, radius, norms        */
+} pf_rmtr_params;
+
+typedef struct {
+  int cycles;            /* V-cycles taken                                   */
+  int converged;         /* 1 if the stopping test passed                    */
+  double energy;         /* E(x) at return (FP64)                            */
+  double pg0, pg;        /* projected-gradient norm at start / at return     */
+  long long hessvecs;    /* Hessian-vector products on any level             */
+  long long cg;          /* CG iterations                                    */
+  long long tr_its;      /* TR iterations on all levels                      */
+  long long tr_rejected; /* rejected TR steps                                */
+  long long coarse_rejected; /* rejected coarse corrections (eq. rho_ml)     */
+  double seconds;        /* wall time of the call                            */
+  long long launches;    /* CUDA kernel launches made by the call            */
+  double fe_hessvec;     /* Hessian-vector products, in finest-level units
+                            (a level-l call counts N_l / N_finest)           */
+  double fe_gradient;    /* gradients, finest-level units                    */
+  double fe_energy;      /* energy / energy-difference passes, finest units  */
+} pf_rmtr_stats;
+
+/* Fills p with the defaults listed beside each field above. */
+void pf_rmtr_params_default(pf_rmtr_params* p);
+
+/* Message of this thread's last failure ("" if none). */
+const char* pf_last_error(void);
+
+/* Builds the level grids, Gauss/shape tables, transfer stencils and per-level
+ * work buffers (Sec. 4.1 steps 2-4 and 6).  *out receives an owned handle.
+ * Errors: PF_EINVAL for a bad descriptor, PF_ENOMEM, PF_ECUDA. */
+pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* desc, pf_hierarchy** out);
+pf_status pf_mesh_hierarchy_destroy(pf_hierarchy* h);
+
+/* Nodes per axis, spacing and node count of one level. */
+pf_status pf_level_info(const pf_hierarchy* h, int level, int n_out[3],
+                        double* h_out, long long* nodes_out);
+
+/* Fracture initialisation (Sec. 5): the c plane of the finest-level FP64
+ * state x_dev is set to 1 at nodes within band_half_width of a fracture's
+ * mid-line (PF_LINE2D) or mid-disc (PF_DISC3D) and inside its extent, else 0
+ * (union over rows).  u planes are not touched.  c_prev := c.
+ * rows_host: n rows of 4 (LINE2D) or 7 (DISC3D) doubles.  Node coordinates
+ * are i*h in FP64; comparisons are inclusive.
+ * Errors: PF_EINVAL (kind/dim mismatch, n < 0, band <= 0). */
+pf_status pf_fractures_set(pf_hierarchy* h, int kind, int n, const double* rows_host,
+                           double band_half_width, void* x_dev);
+
+/* Uniform pressure p of eq. (pressurized) for all following calls. */
+pf_status pf_pressure_set(pf_hierarchy* h, double p);
+
+/* Discrete energy of eq. (pressurized) (AT2, sign reading +p g(c) div u,
+ * clamped boundary terms vanish) on `level`, unconstrained, at x_dev
+ * (precision prec).  FP64 result written to *E_host (stream synchronised).
+ * Deterministic: fixed-order reduction. */
+pf_status pf_energy(pf_hierarchy* h, int level, const void* x_dev, int prec, double* E_host);
+
+/* E(x + s) - E(x) = a1 + a2 + a3 + a4, the exact quartic expansion along s
+ * (coefficients written to a_host[4]); used for the trust-region ratios
+ * eq. (rho_tr) and eq. (rho_ml) without cancellation. */
+pf_status pf_energy_diff(pf_hierarchy* h, int level, const void* x_dev, const void* s_dev,
+                         int prec, double* a_host);
+
+/* Gradient of the energy at x_dev written to g_dev (same precision, same
+ * layout), all dofs, no boundary masking. */
+pf_status pf_gradient(pf_hierarchy* h, int level, const void* x_dev, void* g_dev, int prec);
+
+/* Hessian of the energy at x_lin_dev applied to v_dev, written to Hv_dev;
+ * matrix-free (Sec. 4.2.1 Hessian; applied, not assembled).  All three
+ * vectors in precision prec, computed in that precision. */
+pf_status pf_hessvec(pf_hierarchy* h, int level, const void* x_lin_dev, const void* v_dev,
+                     void* Hv_dev, int prec);
+
+/* Transfers between level `coarse` and coarse+1 (Sec. 3), per plane:
+ * prolong: Q1 interpolation I (fine = I coarse);
+ * restrict: R = I^T (coarse = R fine);
+ * project: P = diag(R 1)^-1 R (coarse = P fine), for iterates. */
+pf_status pf_prolong(pf_hierarchy* h, int coarse, const void* vc_dev, void* vf_dev, int prec);
+pf_status pf_restrict(pf_hierarchy* h, int coarse, const void* vf_dev, void* vc_dev, int prec);
+pf_status pf_project(pf_hierarchy* h, int coarse, const void* vf_dev, void* vc_dev, int prec);
+
+/* Coarse feasible set (Sec. 3.2 F^l): lo_c = max of lo_f over the fine
+ * support of each coarse basis function, hi_c = min of hi_f.  FP64. */
+pf_status pf_coarse_bounds(pf_hierarchy* h, int coarse, const double* lo_f_dev,
+                           const double* hi_f_dev, double* lo_c_dev, double* hi_c_dev);
+
+/* One pseudo-time load step (Sec. 4.1 step 7): c_prev := c of x, then RMTR
+ * V-cycles (Algorithm 1, mu1 = mu2 = 1, Hessian lagging of Sec. 4.2.1) until
+ * the projected gradient meets rtol/atol or max_cycles.  x_dev: finest FP64
+ * state, updated in place.  params NULL = defaults.  stats may be NULL.
+ * Errors: PF_ENOTCONV (x still updated), PF_ENONFINITE, PF_ECUDA. */
+pf_status pf_rmtr_load_step(pf_hierarchy* h, void* x_dev, const pf_rmtr_params* params,
+                            pf_rmtr_stats* stats);
+
+/* Same as pf_rmtr_load_step with the state in host memory: copied to the
+ * device, solved, copied back, all inside the call. */
+pf_status pf_rmtr_load_step_host(pf_hierarchy* h, double* x_host, const pf_rmtr_params* params,
+                                 pf_rmtr_stats* stats);
+
+/* Copies the finest-level c_prev (FP64, N values) to c_prev_dev. */
+pf_status pf_get_c_prev(pf_hierarchy* h, double* c_prev_dev);
+
+/* Measurement helper with no counterpart in the paper: runs a kernel of
+ * independent fused multiply-adds in precision prec on the legacy stream
+ * and writes the achieved rate (flop/s, an FMA counted as 2) to *flops_host.
+ * Used as the ALU roofline denominator of the element kernels. */
+pf_status pf_probe_fma(int prec, double* flops_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) hot path of the RMTR solver for pressure-induced AT2
+phase-field fracture (Zulian, Kopanicakova et al., arXiv 2007.12908).
+
+The compute path is libpf.so (hand-written CUDA kernels behind a C-ABI,
+declared in include/pf.h); this package is its thin ctypes binding.  There
+is no CPU fallback: calls raise if the library is not built or no CUDA
+device is present."""
+from ._binding import (  # noqa: F401
+    PF_DISC3D, PF_FIRST_ORDER, PF_FP32, PF_FP64, PF_GALERKIN, PF_LINE2D, PfError,
+    coarse_bounds, default_params, energy, energy_diff, fractures_set, get_c_prev, gradient,
+    hessvec, mesh_hierarchy_create, pressure_set, project, prolong, restrict, rmtr_load_step,
+    rmtr_load_step_host,
+)

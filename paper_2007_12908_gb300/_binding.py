@@ -1,0 +1,318 @@
+"""ctypes binding of libpf (argument marshalling only: every step of the
+path runs in the library's CUDA kernels).  Device vectors are torch CUDA
+tensors (float64 or float32, contiguous); PyTorch supplies device memory and
+the stream, nothing else.  Importing this module fails loudly if libpf.so
+has not been built."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpf.so")
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ENOTCONV, PF_ETIMEOUT, PF_ESTATE = range(8)
+PF_FP64, PF_FP32 = 0, 1
+PF_GALERKIN, PF_FIRST_ORDER = 0, 1
+PF_LINE2D, PF_DISC3D = 0, 1
+
+STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ENONFINITE",
+                5: "PF_ENOTCONV", 6: "PF_ETIMEOUT", 7: "PF_ESTATE"}
+
+# every symbol include/pf.h declares
+EXPORTS = [
+    "pf_rmtr_params_default", "pf_last_error", "pf_mesh_hierarchy_create",
+    "pf_mesh_hierarchy_destroy", "pf_level_info", "pf_fractures_set", "pf_pressure_set",
+    "pf_energy", "pf_energy_diff", "pf_gradient", "pf_hessvec", "pf_prolong", "pf_restrict",
+    "pf_project", "pf_coarse_bounds", "pf_rmtr_load_step", "pf_rmtr_load_step_host",
+    "pf_get_c_prev", "pf_probe_fma",
+]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_coarse", C.c_int * 3), ("n_levels", C.c_int),
+                ("h_coarse", C.c_double), ("E", C.c_double), ("nu", C.c_double),
+                ("Gc", C.c_double), ("ls_over_h", C.c_double), ("k_res", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class RmtrParams(C.Structure):
+    _fields_ = [("eta1", C.c_double), ("eta2", C.c_double), ("gamma1", C.c_double),
+                ("gamma2", C.c_double), ("delta0", C.c_double), ("delta_max", C.c_double),
+                ("mu1", C.c_int), ("mu2", C.c_int), ("coarse_its", C.c_int),
+                ("cg_fine", C.c_int), ("cg_smooth", C.c_int), ("cg_coarse", C.c_int),
+                ("cauchy_backtracks", C.c_int), ("cauchy_c", C.c_double),
+                ("max_cycles", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
+                ("coarse_model", C.c_int), ("precision", C.c_int)]
+
+
+class RmtrStats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("converged", C.c_int), ("energy", C.c_double),
+                ("pg0", C.c_double), ("pg", C.c_double), ("hessvecs", C.c_longlong),
+                ("cg", C.c_longlong), ("tr_its", C.c_longlong), ("tr_rejected", C.c_longlong),
+                ("coarse_rejected", C.c_longlong), ("seconds", C.c_double),
+                ("launches", C.c_longlong), ("fe_hessvec", C.c_double),
+                ("fe_gradient", C.c_double), ("fe_energy", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libpf.so not built at {path}; run paper_2007_12908_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "pf_rmtr_params_default": (None, [C.POINTER(RmtrParams)]),
+        "pf_last_error": (C.c_char_p, []),
+        "pf_mesh_hierarchy_create": (i, [C.POINTER(MeshDesc), C.POINTER(vp)]),
+        "pf_mesh_hierarchy_destroy": (i, [vp]),
+        "pf_level_info": (i, [vp, i, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(C.c_longlong)]),
+        "pf_fractures_set": (i, [vp, i, i, vp, d, vp]),
+        "pf_pressure_set": (i, [vp, d]),
+        "pf_energy": (i, [vp, i, vp, i, C.POINTER(d)]),
+        "pf_energy_diff": (i, [vp, i, vp, vp, i, vp]),
+        "pf_gradient": (i, [vp, i, vp, vp, i]),
+        "pf_hessvec": (i, [vp, i, vp, vp, vp, i]),
+        "pf_prolong": (i, [vp, i, vp, vp, i]),
+        "pf_restrict": (i, [vp, i, vp, vp, i]),
+        "pf_project": (i, [vp, i, vp, vp, i]),
+        "pf_coarse_bounds": (i, [vp, i, vp, vp, vp, vp]),
+        "pf_rmtr_load_step": (i, [vp, vp, C.POINTER(RmtrParams), C.POINTER(RmtrStats)]),
+        "pf_rmtr_load_step_host": (i, [vp, vp, C.POINTER(RmtrParams), C.POINTER(RmtrStats)]),
+        "pf_get_c_prev": (i, [vp, vp]),
+        "pf_probe_fma": (i, [i, C.POINTER(d)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def _check(status):
+    if status != PF_OK:
+        raise PfError(status, lib().pf_last_error().decode())
+
+
+def default_params(**overrides) -> RmtrParams:
+    p = RmtrParams()
+    lib().pf_rmtr_params_default(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+# ------------------------------------------------------------------ tensors
+def _prec(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return PF_FP64
+    if t.dtype == torch.float32:
+        return PF_FP32
+    raise TypeError("vectors must be float64 or float32")
+
+
+def _dev(t, n=None, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} values, got {t.numel()}")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Hierarchy:
+    """Owns a pf_hierarchy*.  Level 0 is the coarsest grid."""
+
+    def __init__(self, handle, dim, n_levels, stream):
+        self.handle = handle
+        self.dim = dim
+        self.n_levels = n_levels
+        self.stream = stream
+        self.levels = []
+        for l in range(n_levels):
+            n = (C.c_int * 3)()
+            hh = C.c_double()
+            nodes = C.c_longlong()
+            _check(lib().pf_level_info(handle, l, n, C.byref(hh), C.byref(nodes)))
+            self.levels.append((tuple(n[k] for k in range(dim)), hh.value, nodes.value))
+
+    def nodes(self, level=-1):
+        return self.levels[level][2]
+
+    def ndof(self, level=-1):
+        return (self.dim + 1) * self.nodes(level)
+
+    def close(self):
+        if self.handle:
+            lib().pf_mesh_hierarchy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mesh_hierarchy_create(dim, n_coarse, n_levels, h_coarse, E=1.0, nu=0.3, Gc=1.0,
+                          ls_over_h=2.0, k_res=0.0, stream=None) -> Hierarchy:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    d = MeshDesc()
+    d.dim = dim
+    for k in range(3):
+        d.n_coarse[k] = int(n_coarse[k]) if k < dim else 1
+    d.n_levels = n_levels
+    d.h_coarse = h_coarse
+    d.E, d.nu, d.Gc, d.ls_over_h, d.k_res = E, nu, Gc, ls_over_h, k_res
+    d.stream = C.c_void_p(stream.cuda_stream)
+    h = C.c_void_p()
+    _check(lib().pf_mesh_hierarchy_create(C.byref(d), C.byref(h)))
+    return Hierarchy(h, dim, n_levels, stream)
+
+
+def fractures_set(H: Hierarchy, kind: int, rows, band_half_width: float, x):
+    import torch
+    rows = np.ascontiguousarray(np.atleast_2d(np.asarray(rows, dtype=np.float64)))
+    width = 4 if kind == PF_LINE2D else 7
+    if rows.size and rows.shape[1] != width:
+        raise ValueError(f"fracture rows must have {width} columns")
+    n = rows.shape[0] if rows.size else 0
+    _check(lib().pf_fractures_set(H.handle, kind, n, rows.ctypes.data_as(C.c_void_p),
+                                  band_half_width, _dev(x, H.ndof(), torch.float64)))
+
+
+def pressure_set(H: Hierarchy, p: float):
+    _check(lib().pf_pressure_set(H.handle, float(p)))
+
+
+def energy(H: Hierarchy, level: int, x) -> float:
+    out = C.c_double()
+    _check(lib().pf_energy(H.handle, level, _dev(x, H.ndof(level)), _prec(x), C.byref(out)))
+    return out.value
+
+
+def energy_diff(H: Hierarchy, level: int, x, s) -> np.ndarray:
+    if x.dtype != s.dtype:
+        raise TypeError("x and s must share a dtype")
+    out = np.zeros(4)
+    _check(lib().pf_energy_diff(H.handle, level, _dev(x, H.ndof(level)), _dev(s, H.ndof(level)),
+                                _prec(x), out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def gradient(H: Hierarchy, level: int, x, out=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().pf_gradient(H.handle, level, _dev(x, H.ndof(level)), _dev(out, H.ndof(level), x.dtype),
+                             _prec(x)))
+    return out
+
+
+def hessvec(H: Hierarchy, level: int, x_lin, v, out=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(v)
+    n = H.ndof(level)
+    _check(lib().pf_hessvec(H.handle, level, _dev(x_lin, n, v.dtype), _dev(v, n), _dev(out, n, v.dtype),
+                            _prec(v)))
+    return out
+
+
+def _xfer(fn, H, coarse, src, n_src, n_dst, out):
+    import torch
+    if out is None:
+        out = torch.empty(n_dst, dtype=src.dtype, device=src.device)
+    _check(fn(H.handle, coarse, _dev(src, n_src), _dev(out, n_dst, src.dtype), _prec(src)))
+    return out
+
+
+def prolong(H: Hierarchy, coarse: int, vc, out=None):
+    return _xfer(lib().pf_prolong, H, coarse, vc, H.ndof(coarse), H.ndof(coarse + 1), out)
+
+
+def restrict(H: Hierarchy, coarse: int, vf, out=None):
+    return _xfer(lib().pf_restrict, H, coarse, vf, H.ndof(coarse + 1), H.ndof(coarse), out)
+
+
+def project(H: Hierarchy, coarse: int, xf, out=None):
+    return _xfer(lib().pf_project, H, coarse, xf, H.ndof(coarse + 1), H.ndof(coarse), out)
+
+
+def coarse_bounds(H: Hierarchy, coarse: int, lo_f, hi_f):
+    import torch
+    nf, nc = H.ndof(coarse + 1), H.ndof(coarse)
+    lo_c = torch.empty(nc, dtype=torch.float64, device=lo_f.device)
+    hi_c = torch.empty_like(lo_c)
+    _check(lib().pf_coarse_bounds(H.handle, coarse, _dev(lo_f, nf, torch.float64),
+                                  _dev(hi_f, nf, torch.float64), _dev(lo_c, nc), _dev(hi_c, nc)))
+    return lo_c, hi_c
+
+
+def rmtr_load_step(H: Hierarchy, x, params: RmtrParams | None = None, check=True) -> dict:
+    import torch
+    st = RmtrStats()
+    p = params if params is not None else default_params()
+    rc = lib().pf_rmtr_load_step(H.handle, _dev(x, H.ndof(), torch.float64), C.byref(p), C.byref(st))
+    if check and rc not in (PF_OK,):
+        _check(rc)
+    d = st.as_dict()
+    d["status"] = rc
+    return d
+
+
+def rmtr_load_step_host(H: Hierarchy, x: np.ndarray, params: RmtrParams | None = None,
+                        check=True) -> dict:
+    if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.size != H.ndof():
+        raise ValueError("x must be a contiguous float64 array of the finest size")
+    st = RmtrStats()
+    p = params if params is not None else default_params()
+    rc = lib().pf_rmtr_load_step_host(H.handle, x.ctypes.data_as(C.c_void_p), C.byref(p), C.byref(st))
+    if check and rc not in (PF_OK,):
+        _check(rc)
+    d = st.as_dict()
+    d["status"] = rc
+    return d
+
+
+def get_c_prev(H: Hierarchy):
+    import torch
+    out = torch.empty(H.nodes(), dtype=torch.float64, device="cuda")
+    _check(lib().pf_get_c_prev(H.handle, _dev(out, H.nodes())))
+    return out
+
+
+def probe_fma(prec: int) -> float:
+    """Measured FMA throughput (flop/s) of this GPU in the given precision."""
+    out = C.c_double()
+    _check(lib().pf_probe_fma(prec, C.byref(out)))
+    return out.value

@@ -1,0 +1,409 @@
+// C-ABI of libpf: argument checks, hierarchy set-up and dispatch to kernels.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "pf_hier.h"
+
+namespace pf {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace pf
+
+using namespace pf;
+
+#define PF_TRY_CUDA(call, what)                                                       \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error(std::string(what) + ": " + cudaGetErrorString(e_));                   \
+      return e_ == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA;                  \
+    }                                                                                 \
+  } while (0)
+
+static bool valid_level(const pf_hierarchy* h, int level) {
+  return h && level >= 0 && level < h->L;
+}
+
+static pf_status bad(const char* msg) {
+  set_error(msg);
+  return PF_EINVAL;
+}
+
+template <class T>
+__global__ void k_fma_probe(T* out, int reps, T a, T b) {
+  T v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = T(threadIdx.x + k) * T(1e-3);
+  for (int r = 0; r < reps; ++r) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = v[k] * a + b;
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += v[k];
+  if (s == T(-12345.678)) out[0] = s;  // keeps the chains live
+}
+
+extern "C" {
+
+void pf_rmtr_params_default(pf_rmtr_params* p) {
+  if (!p) return;
+  p->eta1 = 0.1;
+  p->eta2 = 0.75;
+  p->gamma1 = 0.5;
+  p->gamma2 = 2.0;
+  p->delta0 = 1.0;
+  p->delta_max = 1.0;
+  p->mu1 = 1;
+  p->mu2 = 1;
+  p->coarse_its = 10;
+  p->cg_fine = 50;
+  p->cg_smooth = 10;
+  p->cg_coarse = 500;
+  p->cauchy_backtracks = 30;
+  p->cauchy_c = 0.01;
+  p->max_cycles = 200;
+  p->rtol = 1e-10;
+  p->atol = 0.0;
+  p->coarse_model = PF_FIRST_ORDER;
+  p->precision = PF_FP64;
+}
+
+const char* pf_last_error(void) { return g_last_error.c_str(); }
+
+static pf_status alloc(pf_hierarchy* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return PF_ENOMEM;
+  }
+  h->allocations.push_back(*p);
+  return PF_OK;
+}
+
+pf_status pf_mesh_hierarchy_destroy(pf_hierarchy* h) {
+  if (!h) return PF_OK;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->h_res) cudaFreeHost(h->h_res);
+  delete h;
+  return PF_OK;
+}
+
+pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
+  if (!d || !out) return bad("mesh_hierarchy_create: null argument");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return bad("mesh_hierarchy_create: dim must be 2 or 3");
+  if (d->n_levels < 1 || d->n_levels > 12) return bad("mesh_hierarchy_create: n_levels out of range");
+  for (int k = 0; k < d->dim; ++k)
+    if (d->n_coarse[k] < 2) return bad("mesh_hierarchy_create: n_coarse must be >= 2");
+  if (!(d->h_coarse > 0) || !(d->E > 0) || !(d->Gc > 0) || !(d->ls_over_h > 0) ||
+      !(d->nu > -1.0 && d->nu < 0.5) || !(d->k_res >= 0 && d->k_res < 1))
+    return bad("mesh_hierarchy_create: invalid material or spacing");
+  pf_hierarchy* h = new pf_hierarchy();
+  h->dim = d->dim;
+  h->L = d->n_levels;
+  h->E = d->E;
+  h->nu = d->nu;
+  h->Gc = d->Gc;
+  h->k_res = d->k_res;
+  h->st = static_cast<cudaStream_t>(d->stream);
+  for (int l = 0; l < h->L; ++l) {
+    int n[3] = {1, 1, 1};
+    for (int k = 0; k < d->dim; ++k) {
+      const long long v = (long long)(d->n_coarse[k] - 1) * (1LL << l) + 1;
+      if (v > (1LL << 20)) {
+        delete h;
+        return bad("mesh_hierarchy_create: grid too large");
+      }
+      n[k] = int(v);
+    }
+    h->geo.push_back(make_geom(d->dim, n, d->h_coarse / double(1LL << l)));
+  }
+  h->ls = d->ls_over_h * h->geo.back().h;
+  for (int l = 0; l < h->L; ++l)
+    h->mat.push_back(make_mat(h->geo[l], h->E, h->nu, h->Gc, h->ls, h->k_res, 0.0));
+  pf_status rc;
+  const int F = d->dim + 1;
+  if ((rc = alloc(h, (void**)&h->scratch.partials, sizeof(double) * kMaxSlots * kMaxBlocks)) ||
+      (rc = alloc(h, (void**)&h->scratch.counter, sizeof(unsigned))) ||
+      (rc = alloc(h, (void**)&h->d_res, sizeof(double) * kMaxSlots)) ||
+      (rc = alloc(h, (void**)&h->c_prev, sizeof(double) * h->geo.back().N))) {
+    pf_mesh_hierarchy_destroy(h);
+    return rc;
+  }
+  if (cudaMallocHost((void**)&h->h_res, sizeof(double) * kMaxSlots) != cudaSuccess) {
+    pf_mesh_hierarchy_destroy(h);
+    set_error("cudaMallocHost failed");
+    return PF_ENOMEM;
+  }
+  cudaMemsetAsync(h->scratch.counter, 0, sizeof(unsigned), h->st);
+  cudaMemsetAsync(h->c_prev, 0, sizeof(double) * h->geo.back().N, h->st);
+  h->lv.resize(h->L);
+  for (int l = 0; l < h->L; ++l) {
+    LevelBuf& B = h->lv[l];
+    B.n = F * h->geo[l].N;
+    const size_t bytes = sizeof(double) * B.n;
+    double** vecs[] = {&B.x, &B.lb, &B.ub, &B.x0, &B.xlag, &B.dg, &B.g, &B.s, &B.lo, &B.hi,
+                       &B.Hs, &B.r, &B.p, &B.q, &B.w, &B.Hw, &B.t1, &B.t2, &B.t3, &B.gin,
+                       &B.gout, &B.dh};
+    for (double** v : vecs)
+      if ((rc = alloc(h, (void**)v, bytes))) {
+        pf_mesh_hierarchy_destroy(h);
+        return rc;
+      }
+    float** f32[] = {&B.xlag32, &B.v32, &B.hv32};
+    for (float** v : f32)
+      if ((rc = alloc(h, (void**)v, sizeof(float) * B.n))) {
+        pf_mesh_hierarchy_destroy(h);
+        return rc;
+      }
+  }
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+    pf_mesh_hierarchy_destroy(h);
+    set_error("mesh_hierarchy_create: stream error");
+    return PF_ECUDA;
+  }
+  *out = h;
+  return PF_OK;
+}
+
+pf_status pf_level_info(const pf_hierarchy* h, int level, int n_out[3], double* h_out,
+                        long long* nodes_out) {
+  if (!valid_level(h, level)) return bad("level_info: bad handle or level");
+  const Geom& g = h->geo[level];
+  if (n_out)
+    for (int k = 0; k < 3; ++k) n_out[k] = g.n[k];
+  if (h_out) *h_out = g.h;
+  if (nodes_out) *nodes_out = g.N;
+  return PF_OK;
+}
+
+pf_status pf_fractures_set(pf_hierarchy* h, int kind, int n, const double* rows,
+                           double band_half_width, void* x_dev) {
+  if (!h || !x_dev) return bad("fractures_set: null argument");
+  if (n < 0 || (n > 0 && !rows)) return bad("fractures_set: bad row count");
+  if (!(band_half_width > 0)) return bad("fractures_set: band_half_width must be > 0");
+  if ((kind == PF_LINE2D && h->dim != 2) || (kind == PF_DISC3D && h->dim != 3) ||
+      (kind != PF_LINE2D && kind != PF_DISC3D))
+    return bad("fractures_set: kind does not match the dimension");
+  const Geom& g = h->geo.back();
+  // device rows: LINE2D [cx, cy, cos, sin, -sin, cos, half_length]
+  //              DISC3D [cx, cy, cz, nx, ny, nz, radius]
+  double* pack = new double[7 * (n > 0 ? n : 1)];
+  for (int k = 0; k < n; ++k) {
+    double* q = pack + 7 * k;
+    if (kind == PF_LINE2D) {
+      const double* r = rows + 4 * k;
+      const double c = std::cos(r[2]), s = std::sin(r[2]);
+      q[0] = r[0]; q[1] = r[1]; q[2] = c; q[3] = s; q[4] = -s; q[5] = c; q[6] = r[3];
+    } else {
+      const double* r = rows + 7 * k;
+      for (int j = 0; j < 7; ++j) q[j] = r[j];
+    }
+    for (int j = 0; j < 7; ++j)
+      if (!std::isfinite(q[j])) {
+        delete[] pack;
+        set_error("fractures_set: non-finite fracture row");
+        return PF_ENONFINITE;
+      }
+  }
+  double* rows_dev = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&rows_dev, sizeof(double) * 7 * (n > 0 ? n : 1), h->st);
+  if (e != cudaSuccess) {
+    delete[] pack;
+    set_error("fractures_set: allocation failed");
+    return PF_ENOMEM;
+  }
+  e = cudaMemcpyAsync(rows_dev, pack, sizeof(double) * 7 * n, cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess)
+    e = rasterize(g, kind, n, rows_dev, band_half_width,
+                  static_cast<double*>(x_dev) + h->dim * g.N, h->c_prev, h->st);
+  cudaFreeAsync(rows_dev, h->st);
+  cudaError_t e2 = cudaStreamSynchronize(h->st);
+  delete[] pack;
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    set_error(std::string("fractures_set: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return PF_ECUDA;
+  }
+  h->have_fractures = true;
+  return PF_OK;
+}
+
+pf_status pf_pressure_set(pf_hierarchy* h, double p) {
+  if (!h) return bad("pressure_set: null handle");
+  if (!std::isfinite(p)) {
+    set_error("pressure_set: non-finite pressure");
+    return PF_ENONFINITE;
+  }
+  h->p = p;
+  for (auto& m : h->mat) m.p = p;
+  return PF_OK;
+}
+
+static pf_status check_prec(int prec) {
+  return (prec == PF_FP64 || prec == PF_FP32) ? PF_OK : bad("precision must be PF_FP64 or PF_FP32");
+}
+
+pf_status pf_energy(pf_hierarchy* h, int level, const void* x, int prec, double* E_host) {
+  if (!valid_level(h, level) || !x || !E_host) return bad("energy: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  PF_TRY_CUDA(elem_energy(h->geo[level], h->mat[level], x, prec, h->scratch, h->d_res, h->st), "energy");
+  PF_TRY_CUDA(cudaMemcpyAsync(h->h_res, h->d_res, sizeof(double), cudaMemcpyDeviceToHost, h->st), "energy");
+  PF_TRY_CUDA(cudaStreamSynchronize(h->st), "energy");
+  *E_host = h->h_res[0];
+  if (!std::isfinite(*E_host)) {
+    set_error("energy: non-finite result");
+    return PF_ENONFINITE;
+  }
+  return PF_OK;
+}
+
+pf_status pf_energy_diff(pf_hierarchy* h, int level, const void* x, const void* s, int prec,
+                         double* a_host) {
+  if (!valid_level(h, level) || !x || !s || !a_host) return bad("energy_diff: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  PF_TRY_CUDA(elem_energy_diff(h->geo[level], h->mat[level], x, s, prec, h->scratch, h->d_res, h->st),
+              "energy_diff");
+  PF_TRY_CUDA(cudaMemcpyAsync(h->h_res, h->d_res, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st),
+              "energy_diff");
+  PF_TRY_CUDA(cudaStreamSynchronize(h->st), "energy_diff");
+  for (int k = 0; k < 4; ++k) a_host[k] = h->h_res[k];
+  return PF_OK;
+}
+
+pf_status pf_gradient(pf_hierarchy* h, int level, const void* x, void* g, int prec) {
+  if (!valid_level(h, level) || !x || !g) return bad("gradient: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  PF_TRY_CUDA(elem_gradient(h->geo[level], h->mat[level], x, g, prec, h->st), "gradient");
+  return PF_OK;
+}
+
+pf_status pf_hessvec(pf_hierarchy* h, int level, const void* x, const void* v, void* Hv, int prec) {
+  if (!valid_level(h, level) || !x || !v || !Hv) return bad("hessvec: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  PF_TRY_CUDA(elem_hessvec(h->geo[level], h->mat[level], x, v, Hv, prec, h->st), "hessvec");
+  return PF_OK;
+}
+
+pf_status pf_prolong(pf_hierarchy* h, int coarse, const void* vc, void* vf, int prec) {
+  if (!h || coarse < 0 || coarse + 1 >= h->L || !vc || !vf) return bad("prolong: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  PF_TRY_CUDA(xfer_prolong(h->geo[coarse], h->geo[coarse + 1], h->dim + 1, vc, vf, prec, h->st), "prolong");
+  return PF_OK;
+}
+
+pf_status pf_restrict(pf_hierarchy* h, int coarse, const void* vf, void* vc, int prec) {
+  if (!h || coarse < 0 || coarse + 1 >= h->L || !vc || !vf) return bad("restrict: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  PF_TRY_CUDA(xfer_restrict(h->geo[coarse], h->geo[coarse + 1], h->dim + 1, vf, vc, prec, false, h->st),
+              "restrict");
+  return PF_OK;
+}
+
+pf_status pf_project(pf_hierarchy* h, int coarse, const void* vf, void* vc, int prec) {
+  if (!h || coarse < 0 || coarse + 1 >= h->L || !vc || !vf) return bad("project: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  PF_TRY_CUDA(xfer_restrict(h->geo[coarse], h->geo[coarse + 1], h->dim + 1, vf, vc, prec, true, h->st),
+              "project");
+  return PF_OK;
+}
+
+pf_status pf_coarse_bounds(pf_hierarchy* h, int coarse, const double* lo_f, const double* hi_f,
+                           double* lo_c, double* hi_c) {
+  if (!h || coarse < 0 || coarse + 1 >= h->L || !lo_f || !hi_f || !lo_c || !hi_c)
+    return bad("coarse_bounds: bad argument");
+  PF_TRY_CUDA(xfer_bounds(h->geo[coarse], h->geo[coarse + 1], h->dim + 1, lo_f, hi_f, lo_c, hi_c, h->st),
+              "coarse_bounds");
+  return PF_OK;
+}
+
+static pf_status check_params(const pf_rmtr_params& P) {
+  if (!(P.eta1 > 0 && P.eta1 <= P.eta2 && P.eta2 <= 1) || !(P.gamma1 > 0 && P.gamma1 <= 1) ||
+      !(P.gamma2 >= 1) || !(P.delta0 > 0) || !(P.delta_max >= P.delta0) || P.mu1 < 0 ||
+      P.mu2 < 0 || P.coarse_its < 0 || P.cg_fine < 0 || P.cg_smooth < 0 || P.cg_coarse < 0 ||
+      P.cauchy_backtracks < 0 || !(P.cauchy_c > 0 && P.cauchy_c < 1) || P.max_cycles < 0 ||
+      !(P.rtol >= 0) || !(P.atol >= 0) ||
+      (P.coarse_model != PF_GALERKIN && P.coarse_model != PF_FIRST_ORDER) ||
+      (P.precision != PF_FP64 && P.precision != PF_FP32))
+    return bad("rmtr_load_step: invalid parameters");
+  return PF_OK;
+}
+
+pf_status pf_rmtr_load_step(pf_hierarchy* h, void* x, const pf_rmtr_params* params,
+                            pf_rmtr_stats* stats) {
+  if (!h || !x) return bad("rmtr_load_step: null argument");
+  pf_rmtr_params P;
+  if (params) P = *params;
+  else pf_rmtr_params_default(&P);
+  if (check_params(P)) return PF_EINVAL;
+  return rmtr_load_step_impl(h, static_cast<double*>(x), P, stats);
+}
+
+pf_status pf_rmtr_load_step_host(pf_hierarchy* h, double* x_host, const pf_rmtr_params* params,
+                                 pf_rmtr_stats* stats) {
+  if (!h || !x_host) return bad("rmtr_load_step_host: null argument");
+  pf_rmtr_params P;
+  if (params) P = *params;
+  else pf_rmtr_params_default(&P);
+  if (check_params(P)) return PF_EINVAL;
+  // the finest level's dH scratch is unused by a load step: stage the state there
+  LevelBuf& B = h->lv.back();
+  double* stage = B.dh;
+  PF_TRY_CUDA(cudaMemcpyAsync(stage, x_host, sizeof(double) * B.n, cudaMemcpyHostToDevice, h->st),
+              "rmtr_load_step_host");
+  pf_status rc = rmtr_load_step_impl(h, stage, P, stats);
+  if (rc != PF_OK && rc != PF_ENOTCONV && rc != PF_ENONFINITE) return rc;
+  PF_TRY_CUDA(cudaMemcpyAsync(x_host, stage, sizeof(double) * B.n, cudaMemcpyDeviceToHost, h->st),
+              "rmtr_load_step_host");
+  PF_TRY_CUDA(cudaStreamSynchronize(h->st), "rmtr_load_step_host");
+  return rc;
+}
+
+pf_status pf_get_c_prev(pf_hierarchy* h, double* out) {
+  if (!h || !out) return bad("get_c_prev: null argument");
+  PF_TRY_CUDA(cudaMemcpyAsync(out, h->c_prev, sizeof(double) * h->geo.back().N,
+                              cudaMemcpyDeviceToDevice, h->st),
+              "get_c_prev");
+  return PF_OK;
+}
+
+pf_status pf_probe_fma(int prec, double* flops) {
+  if (!flops) return bad("probe_fma: null argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  int dev = 0, sms = 0;
+  PF_TRY_CUDA(cudaGetDevice(&dev), "probe_fma");
+  PF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "probe_fma");
+  void* out = nullptr;
+  PF_TRY_CUDA(cudaMalloc(&out, 16), "probe_fma");
+  const int blocks = sms * 8, threads = 256;
+  const int reps = prec ? 1 << 16 : 1 << 11;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float ms = 0.f;
+  for (int pass = 0; pass < 2; ++pass) {  // first pass warms up
+    cudaEventRecord(e0, 0);
+    if (prec)
+      k_fma_probe<float><<<blocks, threads>>>(static_cast<float*>(out), reps, 0.999f, 1e-4f);
+    else
+      k_fma_probe<double><<<blocks, threads>>>(static_cast<double*>(out), reps, 0.999, 1e-4);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess) {
+    set_error(std::string("probe_fma: ") + cudaGetErrorString(e));
+    return PF_ECUDA;
+  }
+  *flops = 2.0 * 8.0 * double(reps) * double(blocks) * threads / (double(ms) * 1e-3);
+  return PF_OK;
+}
+
+}  // extern "C"

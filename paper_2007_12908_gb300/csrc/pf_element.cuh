@@ -1,0 +1,417 @@
+// Q1 element algebra of the pressurised AT2 functional (Sec. 2, eq.
+// pressurized with the +p g(c) div u sign reading), evaluated per element at
+// the 2^d Gauss points of a uniform cell.
+//
+// Interpolation to the Gauss points and the test-function contraction back to
+// the corners are sum-factorised along the axes: one pass per axis, each a
+// 2-point linear blend (values) or a difference (derivatives, constant along
+// their own axis for Q1).  Corner a = ax + 2 ay + 4 az, Gauss point
+// q = qx + 2 qy + 4 qz; 1D shape values at the Gauss points are
+// N(q=0) = (XI1, XI0), N(q=1) = (XI0, XI1) with XI0 + XI1 = 1.
+// Derivatives here are raw nodal differences; callers scale by 1/h.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pf {
+
+// (1 -+ 1/sqrt(3)) / 2
+#define PF_XI0 0.21132486540518711775
+#define PF_XI1 0.78867513459481288225
+
+template <class T>
+struct Mat {
+  T lam, mu, Gc, ls, k, p;  // Lame, toughness, length scale, residual, pressure
+  T inv_h;                  // 1/h
+  T w;                      // Gauss weight times det J = h^d / 2^d
+};
+
+// ---------------------------------------------------------------- 3D passes
+template <class T>
+__device__ __forceinline__ void interp3(const T f[8], T val[8], T gx[8], T gy[8], T gz[8]) {
+  const T x0 = T(PF_XI0), x1 = T(PF_XI1);
+  T X[2][2][2], DX[2][2];
+#pragma unroll
+  for (int az = 0; az < 2; ++az)
+#pragma unroll
+    for (int ay = 0; ay < 2; ++ay) {
+      const T v0 = f[2 * ay + 4 * az], d = f[1 + 2 * ay + 4 * az] - v0;
+      DX[ay][az] = d;
+      X[0][ay][az] = v0 + x0 * d;
+      X[1][ay][az] = v0 + x1 * d;
+    }
+  T XY[2][2][2], DY[2][2], DXY[2][2];
+#pragma unroll
+  for (int az = 0; az < 2; ++az) {
+#pragma unroll
+    for (int qx = 0; qx < 2; ++qx) {
+      const T v0 = X[qx][0][az], d = X[qx][1][az] - v0;
+      DY[qx][az] = d;
+      XY[qx][0][az] = v0 + x0 * d;
+      XY[qx][1][az] = v0 + x1 * d;
+    }
+    const T v0 = DX[0][az], d = DX[1][az] - v0;
+    DXY[0][az] = v0 + x0 * d;
+    DXY[1][az] = v0 + x1 * d;
+  }
+#pragma unroll
+  for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+    for (int qx = 0; qx < 2; ++qx) {
+      const int q = qx + 2 * qy;
+      const T v0 = XY[qx][qy][0], d = XY[qx][qy][1] - v0;
+      val[q] = v0 + x0 * d;
+      val[q + 4] = v0 + x1 * d;
+      gz[q] = d;
+      gz[q + 4] = d;
+    }
+#pragma unroll
+  for (int qy = 0; qy < 2; ++qy) {
+    const T v0 = DXY[qy][0], d = DXY[qy][1] - v0;
+    const T a = v0 + x0 * d, b = v0 + x1 * d;
+    gx[2 * qy] = a; gx[1 + 2 * qy] = a;
+    gx[2 * qy + 4] = b; gx[1 + 2 * qy + 4] = b;
+  }
+#pragma unroll
+  for (int qx = 0; qx < 2; ++qx) {
+    const T v0 = DY[qx][0], d = DY[qx][1] - v0;
+    const T a = v0 + x0 * d, b = v0 + x1 * d;
+    gy[qx] = a; gy[qx + 2] = a;
+    gy[qx + 4] = b; gy[qx + 6] = b;
+  }
+}
+
+// r[a] = sum_q s0[q] N_a(q) + sx[q] Dx_a(q) + sy[q] Dy_a(q) + sz[q] Dz_a(q)
+// (raw derivatives), the adjoint of interp3.
+template <class T>
+__device__ __forceinline__ void test3(const T s0[8], const T sx[8], const T sy[8], const T sz[8],
+                                      T r[8]) {
+  const T x0 = T(PF_XI0), x1 = T(PF_XI1);
+  T XYb[2][2][2], DXYb[2][2], DYb[2][2];
+#pragma unroll
+  for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+    for (int qx = 0; qx < 2; ++qx) {
+      const int q = qx + 2 * qy;
+      const T zs = sz[q] + sz[q + 4];
+      XYb[qx][qy][0] = x1 * s0[q] + x0 * s0[q + 4] - zs;
+      XYb[qx][qy][1] = x0 * s0[q] + x1 * s0[q + 4] + zs;
+    }
+#pragma unroll
+  for (int qy = 0; qy < 2; ++qy) {
+    const T a = sx[2 * qy] + sx[1 + 2 * qy], b = sx[2 * qy + 4] + sx[1 + 2 * qy + 4];
+    DXYb[qy][0] = x1 * a + x0 * b;
+    DXYb[qy][1] = x0 * a + x1 * b;
+  }
+#pragma unroll
+  for (int qx = 0; qx < 2; ++qx) {
+    const T a = sy[qx] + sy[qx + 2], b = sy[qx + 4] + sy[qx + 6];
+    DYb[qx][0] = x1 * a + x0 * b;
+    DYb[qx][1] = x0 * a + x1 * b;
+  }
+  T Xb[2][2][2], DXb[2][2];
+#pragma unroll
+  for (int az = 0; az < 2; ++az) {
+#pragma unroll
+    for (int qx = 0; qx < 2; ++qx) {
+      Xb[qx][0][az] = x1 * XYb[qx][0][az] + x0 * XYb[qx][1][az] - DYb[qx][az];
+      Xb[qx][1][az] = x0 * XYb[qx][0][az] + x1 * XYb[qx][1][az] + DYb[qx][az];
+    }
+    DXb[0][az] = x1 * DXYb[0][az] + x0 * DXYb[1][az];
+    DXb[1][az] = x0 * DXYb[0][az] + x1 * DXYb[1][az];
+  }
+#pragma unroll
+  for (int az = 0; az < 2; ++az)
+#pragma unroll
+    for (int ay = 0; ay < 2; ++ay) {
+      r[2 * ay + 4 * az] = x1 * Xb[0][ay][az] + x0 * Xb[1][ay][az] - DXb[ay][az];
+      r[1 + 2 * ay + 4 * az] = x0 * Xb[0][ay][az] + x1 * Xb[1][ay][az] + DXb[ay][az];
+    }
+}
+
+// ---------------------------------------------------------------- 2D passes
+template <class T>
+__device__ __forceinline__ void interp2(const T f[4], T val[4], T gx[4], T gy[4]) {
+  const T x0 = T(PF_XI0), x1 = T(PF_XI1);
+  T X[2][2], DX[2];
+#pragma unroll
+  for (int ay = 0; ay < 2; ++ay) {
+    const T v0 = f[2 * ay], d = f[1 + 2 * ay] - v0;
+    DX[ay] = d;
+    X[0][ay] = v0 + x0 * d;
+    X[1][ay] = v0 + x1 * d;
+  }
+#pragma unroll
+  for (int qx = 0; qx < 2; ++qx) {
+    const T v0 = X[qx][0], d = X[qx][1] - v0;
+    val[qx] = v0 + x0 * d;
+    val[qx + 2] = v0 + x1 * d;
+    gy[qx] = d;
+    gy[qx + 2] = d;
+  }
+  const T v0 = DX[0], d = DX[1] - v0;
+  const T a = v0 + x0 * d, b = v0 + x1 * d;
+  gx[0] = a; gx[1] = a; gx[2] = b; gx[3] = b;
+}
+
+template <class T>
+__device__ __forceinline__ void test2(const T s0[4], const T sx[4], const T sy[4], T r[4]) {
+  const T x0 = T(PF_XI0), x1 = T(PF_XI1);
+  T Xb[2][2];
+#pragma unroll
+  for (int qx = 0; qx < 2; ++qx) {
+    const T ys = sy[qx] + sy[qx + 2];
+    Xb[qx][0] = x1 * s0[qx] + x0 * s0[qx + 2] - ys;
+    Xb[qx][1] = x0 * s0[qx] + x1 * s0[qx + 2] + ys;
+  }
+  const T a = sx[0] + sx[1], b = sx[2] + sx[3];
+  const T DXb0 = x1 * a + x0 * b, DXb1 = x0 * a + x1 * b;
+#pragma unroll
+  for (int ay = 0; ay < 2; ++ay) {
+    const T dxb = ay ? DXb1 : DXb0;
+    r[2 * ay] = x1 * Xb[0][ay] + x0 * Xb[1][ay] - dxb;
+    r[1 + 2 * ay] = x0 * Xb[0][ay] + x1 * Xb[1][ay] + dxb;
+  }
+}
+
+// ---------------------------------------------------------------- dispatch
+template <int D, class T>
+__device__ __forceinline__ void interp(const T* f, T* val, T (*g)[1 << D]) {
+  if constexpr (D == 3) interp3<T>(f, val, g[0], g[1], g[2]);
+  else interp2<T>(f, val, g[0], g[1]);
+}
+
+template <int D, class T>
+__device__ __forceinline__ void test(const T* s0, T (*s1)[1 << D], T* r) {
+  if constexpr (D == 3) test3<T>(s0, s1[0], s1[1], s1[2], r);
+  else test2<T>(s0, s1[0], s1[1], r);
+}
+
+template <int D, class T>
+__device__ __forceinline__ void zero_test(T* r) {
+#pragma unroll
+  for (int a = 0; a < (1 << D); ++a) r[a] = T(0);
+}
+
+// Strain of a displacement gradient G[i][k] = d u_i / d x_k.
+template <int D, class T>
+struct Strain {
+  T eps[D][D];
+  T tr;
+  __device__ __forceinline__ void set(const T G[D][D]) {
+    tr = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      tr += G[i][i];
+#pragma unroll
+      for (int k = 0; k < D; ++k) eps[i][k] = T(0.5) * (G[i][k] + G[k][i]);
+    }
+  }
+  __device__ __forceinline__ T ddot(const Strain& o) const {
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += eps[i][k] * o.eps[i][k];
+    return s;
+  }
+};
+
+// ---------------------------------------------------------------- element ops
+// Every op takes the element's nodal values xe[f][a] (f = field plane,
+// a = corner) and, for hessvec / energy_diff, a second vector ve[f][a].
+
+// Energy of one element: sum_q w [g psi + Gc/2 (c^2/ls + ls |grad c|^2) + p g tr]
+template <int D, class T>
+__device__ __forceinline__ T elem_energy(const T (*xe)[1 << D], const Mat<T>& m) {
+  constexpr int NQ = 1 << D;
+  T gu[D][D][NQ], cv[NQ], gc[D][NQ], dummy[NQ];
+#pragma unroll
+  for (int i = 0; i < D; ++i) interp<D, T>(xe[i], dummy, gu[i]);
+  interp<D, T>(xe[D], cv, gc);
+  T e = T(0);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T G[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) G[i][k] = gu[i][k][q] * m.inv_h;
+    Strain<D, T> s;
+    s.set(G);
+    const T psi = T(0.5) * m.lam * s.tr * s.tr + m.mu * s.ddot(s);
+    const T omc = T(1) - cv[q];
+    const T g = (T(1) - m.k) * omc * omc + m.k;
+    T gc2 = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const T t = gc[k][q] * m.inv_h;
+      gc2 += t * t;
+    }
+    e += g * psi + T(0.5) * m.Gc * (cv[q] * cv[q] / m.ls + m.ls * gc2) + m.p * g * s.tr;
+  }
+  return m.w * e;
+}
+
+// Quartic coefficients of E_e(x + t s) - E_e(x).
+template <int D, class T>
+__device__ __forceinline__ void elem_energy_diff(const T (*xe)[1 << D], const T (*se)[1 << D],
+                                                 const Mat<T>& m, T a[4]) {
+  constexpr int NQ = 1 << D;
+  T gu[D][D][NQ], cv[NQ], gc[D][NQ], dummy[NQ];
+  T gs[D][D][NQ], sc[NQ], gsc[D][NQ];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    interp<D, T>(xe[i], dummy, gu[i]);
+    interp<D, T>(se[i], dummy, gs[i]);
+  }
+  interp<D, T>(xe[D], cv, gc);
+  interp<D, T>(se[D], sc, gsc);
+  T a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T G[D][D], Gs[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        G[i][k] = gu[i][k][q] * m.inv_h;
+        Gs[i][k] = gs[i][k][q] * m.inv_h;
+      }
+    Strain<D, T> e0, e1;
+    e0.set(G);
+    e1.set(Gs);
+    const T psi0 = T(0.5) * m.lam * e0.tr * e0.tr + m.mu * e0.ddot(e0);
+    const T psi2 = T(0.5) * m.lam * e1.tr * e1.tr + m.mu * e1.ddot(e1);
+    const T psi1 = m.lam * e0.tr * e1.tr + T(2) * m.mu * e0.ddot(e1);
+    const T omk = T(1) - m.k, omc = T(1) - cv[q], s = sc[q];
+    const T g0 = omk * omc * omc + m.k;
+    const T g1 = T(-2) * omk * omc * s;
+    const T g2 = omk * s * s;
+    T cg = 0, gg = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const T u = gc[k][q] * m.inv_h, v = gsc[k][q] * m.inv_h;
+      cg += u * v;
+      gg += v * v;
+    }
+    a1 += g0 * psi1 + g1 * psi0 + m.p * (g0 * e1.tr + g1 * e0.tr) +
+          m.Gc * (cv[q] * s / m.ls + m.ls * cg);
+    a2 += g0 * psi2 + g1 * psi1 + g2 * psi0 + m.p * (g1 * e1.tr + g2 * e0.tr) +
+          T(0.5) * m.Gc * (s * s / m.ls + m.ls * gg);
+    a3 += g1 * psi2 + g2 * psi1 + m.p * g2 * e1.tr;
+    a4 += g2 * psi2;
+  }
+  a[0] = m.w * a1; a[1] = m.w * a2; a[2] = m.w * a3; a[3] = m.w * a4;
+}
+
+// Gradient: u-rows  int g (sigma + p I) : grad phi,
+//           c-row   int [g'(psi + p tr) + Gc c/ls] phi + Gc ls grad c . grad phi
+template <int D, class T>
+__device__ __forceinline__ void elem_gradient(const T (*xe)[1 << D], const Mat<T>& m,
+                                              T (*out)[1 << D]) {
+  constexpr int NQ = 1 << D;
+  T gu[D][D][NQ], cv[NQ], gc[D][NQ], dummy[NQ];
+#pragma unroll
+  for (int i = 0; i < D; ++i) interp<D, T>(xe[i], dummy, gu[i]);
+  interp<D, T>(xe[D], cv, gc);
+  T su[D][D][NQ], s0[NQ], sc[D][NQ], zero[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    zero[q] = T(0);
+    T G[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) G[i][k] = gu[i][k][q] * m.inv_h;
+    Strain<D, T> s;
+    s.set(G);
+    const T psi = T(0.5) * m.lam * s.tr * s.tr + m.mu * s.ddot(s);
+    const T omk = T(1) - m.k, omc = T(1) - cv[q];
+    const T g = omk * omc * omc + m.k;
+    const T dg = T(-2) * omk * omc;
+    // weight and 1/h of the test gradient folded into the coefficient
+    const T wg = m.w * m.inv_h * g;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        T sig = T(2) * m.mu * s.eps[i][k];
+        if (i == k) sig += m.lam * s.tr + m.p;
+        su[i][k][q] = wg * sig;
+      }
+    s0[q] = m.w * (dg * (psi + m.p * s.tr) + m.Gc * cv[q] / m.ls);
+    const T f = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
+#pragma unroll
+    for (int k = 0; k < D; ++k) sc[k][q] = f * gc[k][q];
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) test<D, T>(zero, su[i], out[i]);
+  test<D, T>(s0, sc, out[D]);
+}
+
+// Hessian at x applied to v:
+//   u-rows  int [g sigma(v_u) + g' v_c (sigma(u) + p I)] : grad phi
+//   c-row   int [g' (sigma(u) + p I) : eps(v_u) + (g''(psi + p tr) + Gc/ls) v_c] phi
+//               + Gc ls grad v_c . grad phi
+template <int D, class T>
+__device__ __forceinline__ void elem_hessvec(const T (*xe)[1 << D], const T (*ve)[1 << D],
+                                             const Mat<T>& m, T (*out)[1 << D]) {
+  constexpr int NQ = 1 << D;
+  T su[D][D][NQ], s0[NQ], sc[D][NQ], zero[NQ];
+  {
+    T gu[D][D][NQ], cv[NQ], dummy[NQ], gdummy[D][NQ];
+    T gv[D][D][NQ], vc[NQ], gvc[D][NQ];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      interp<D, T>(xe[i], dummy, gu[i]);
+      interp<D, T>(ve[i], dummy, gv[i]);
+    }
+    interp<D, T>(xe[D], cv, gdummy);
+    interp<D, T>(ve[D], vc, gvc);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      zero[q] = T(0);
+      T G[D][D], Gv[D][D];
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          G[i][k] = gu[i][k][q] * m.inv_h;
+          Gv[i][k] = gv[i][k][q] * m.inv_h;
+        }
+      Strain<D, T> e, ev;
+      e.set(G);
+      ev.set(Gv);
+      const T psi = T(0.5) * m.lam * e.tr * e.tr + m.mu * e.ddot(e);
+      const T omk = T(1) - m.k, omc = T(1) - cv[q];
+      const T g = omk * omc * omc + m.k;
+      const T dg = T(-2) * omk * omc;
+      const T ddg = T(2) * omk;
+      const T dgv = dg * vc[q];
+      const T wh = m.w * m.inv_h;
+      T Tev = T(0);  // (sigma(u) + p I) : eps(v)
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          T Tik = T(2) * m.mu * e.eps[i][k];
+          T Sv = T(2) * m.mu * ev.eps[i][k];
+          if (i == k) {
+            Tik += m.lam * e.tr + m.p;
+            Sv += m.lam * ev.tr;
+          }
+          Tev += Tik * ev.eps[i][k];
+          su[i][k][q] = wh * (g * Sv + dgv * Tik);
+        }
+      s0[q] = m.w * (dg * Tev + (ddg * (psi + m.p * e.tr) + m.Gc / m.ls) * vc[q]);
+      const T f = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
+#pragma unroll
+      for (int k = 0; k < D; ++k) sc[k][q] = f * gvc[k][q];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) test<D, T>(zero, su[i], out[i]);
+  test<D, T>(s0, sc, out[D]);
+}
+
+}  // namespace pf

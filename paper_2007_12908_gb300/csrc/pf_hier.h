@@ -1,0 +1,48 @@
+// The opaque pf_hierarchy: level grids, material, reduction scratch and the
+// per-level solver buffers (all device-resident, allocated once at create).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_internal.h"
+
+namespace pf {
+
+// Device buffers of one level.  Vectors hold (dim+1)*N doubles.
+struct LevelBuf {
+  long long n = 0;  // dofs
+  double *x = nullptr, *lb = nullptr, *ub = nullptr;  // iterate and feasible set
+  double *x0 = nullptr, *xlag = nullptr, *dg = nullptr;  // level model
+  double *g = nullptr, *s = nullptr, *lo = nullptr, *hi = nullptr;  // TR step
+  double *Hs = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;    // CG
+  double *w = nullptr, *Hw = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
+  double *gin = nullptr, *gout = nullptr;  // Galerkin recursion through this level
+  double *dh = nullptr;                    // dH scratch
+  float *xlag32 = nullptr, *v32 = nullptr, *hv32 = nullptr;  // mixed-precision hessvec
+};
+
+void set_error(const std::string& msg);
+
+}  // namespace pf
+
+struct pf_hierarchy {
+  int dim = 0, L = 0;
+  std::vector<pf::Geom> geo;
+  std::vector<pf::Mat<double>> mat;  // per level (ls = ls_over_h * h_finest)
+  double E = 1, nu = 0.3, Gc = 1, ls = 0, k_res = 0, p = 0;
+  cudaStream_t st = nullptr;
+  pf::Scratch scratch{nullptr, nullptr};
+  double* d_res = nullptr;  // device result slots
+  double* h_res = nullptr;  // pinned host mirror
+  double* c_prev = nullptr; // finest N values
+  bool have_fractures = false;
+  std::vector<pf::LevelBuf> lv;
+  std::vector<void*> allocations;
+};
+
+namespace pf {
+pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_params& P,
+                              pf_rmtr_stats* stats);
+void refresh_pressure(pf_hierarchy* H);
+}  // namespace pf

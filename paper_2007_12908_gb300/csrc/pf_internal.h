@@ -1,0 +1,57 @@
+// Internal interfaces between the kernel, solver and C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pf_element.cuh"
+
+namespace pf {
+
+// One level's structured grid: n[k] nodes per axis, spacing h.
+struct Geom {
+  int dim;
+  int n[3];
+  long long N;   // nodes
+  int ne[3];     // elements per axis
+  long long NE;  // elements
+  double h;
+};
+
+// Fixed-size deterministic reduction scratch: one partial per block (up to
+// kMaxBlocks per slot, kMaxSlots slots) and a completion counter.  The last
+// block to finish sums the partials in block order.
+constexpr int kMaxBlocks = 1216;  // 8 x 152 SMs
+constexpr int kMaxSlots = 8;
+struct Scratch {
+  double* partials;   // kMaxSlots * kMaxBlocks
+  unsigned* counter;  // 1, zero between reductions
+};
+
+Geom make_geom(int dim, const int n[3], double h);
+Mat<double> make_mat(const Geom& g, double E, double nu, double Gc, double ls, double k,
+                     double p);
+
+// Element kernels.  x, v, y hold (dim+1) planes of g.N values in precision
+// prec (0 = double, 1 = float).  Reductions write FP64 results to out_dev.
+cudaError_t elem_energy(const Geom& g, const Mat<double>& m, const void* x, int prec,
+                        const Scratch& s, double* out_dev, cudaStream_t st);
+cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x, const void* sv,
+                             int prec, const Scratch& s, double* out_dev, cudaStream_t st);
+cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, void* y, int prec,
+                          cudaStream_t st);
+cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
+                         void* y, int prec, cudaStream_t st);
+
+// Fracture band rasterisation into the c plane (FP64) of x and c_prev.
+// rows: device array of precomputed shape rows (see pf_kernels.cu).
+cudaError_t rasterize(const Geom& g, int kind, int n, const double* rows_dev, double band,
+                      double* c_plane, double* c_prev, cudaStream_t st);
+
+// Transfers between a coarse grid gc and its 2:1 refinement gf, nf planes.
+cudaError_t xfer_prolong(const Geom& gc, const Geom& gf, int nf, const void* in, void* out,
+                         int prec, cudaStream_t st);
+cudaError_t xfer_restrict(const Geom& gc, const Geom& gf, int nf, const void* in, void* out,
+                          int prec, bool normalise, cudaStream_t st);
+cudaError_t xfer_bounds(const Geom& gc, const Geom& gf, int nf, const double* lo_f,
+                        const double* hi_f, double* lo_c, double* hi_c, cudaStream_t st);
+
+}  // namespace pf

@@ -1,0 +1,464 @@
+// Element kernels (energy, quartic energy difference, gradient, Hessian-vector
+// product), fracture rasterisation and grid transfers for sm_103a.
+//
+// Element loops are owner-computes: a CTA owns a tile of nodes, evaluates
+// every element touching them (one halo layer on the low side) and sums the
+// corner contributions in shared memory in 2^d colour phases (phase a adds
+// corner a of every element; distinct elements hit distinct nodes within a
+// phase).  Each owned node therefore receives its element contributions in
+// a fixed order: results are bitwise reproducible, with no atomics.
+#include <cmath>
+#include <cstdio>
+
+#include "pf_internal.h"
+#include "pf_reduce.cuh"
+
+namespace pf {
+
+Geom make_geom(int dim, const int n[3], double h) {
+  Geom g;
+  g.dim = dim;
+  g.N = 1;
+  g.NE = 1;
+  for (int k = 0; k < 3; ++k) {
+    g.n[k] = k < dim ? n[k] : 1;
+    g.ne[k] = k < dim ? n[k] - 1 : 1;
+    g.N *= g.n[k];
+    g.NE *= g.ne[k];
+  }
+  g.h = h;
+  return g;
+}
+
+Mat<double> make_mat(const Geom& g, double E, double nu, double Gc, double ls, double k,
+                     double p) {
+  Mat<double> m;
+  m.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  m.mu = E / (2.0 * (1.0 + nu));
+  m.Gc = Gc;
+  m.ls = ls;
+  m.k = k;
+  m.p = p;
+  m.inv_h = 1.0 / g.h;
+  m.w = std::pow(g.h, g.dim) / double(1 << g.dim);
+  return m;
+}
+
+template <class T>
+static Mat<T> cast_mat(const Mat<double>& m) {
+  Mat<T> r;
+  r.lam = T(m.lam); r.mu = T(m.mu); r.Gc = T(m.Gc); r.ls = T(m.ls); r.k = T(m.k);
+  r.p = T(m.p); r.inv_h = T(m.inv_h); r.w = T(m.w);
+  return r;
+}
+
+// ------------------------------------------------------------ gathers
+template <int D>
+__device__ __forceinline__ long long corner_node(const Geom& g, int ex, int ey, int ez, int a) {
+  const long long ix = ex + (a & 1), iy = ey + ((a >> 1) & 1);
+  if constexpr (D == 3) {
+    const long long iz = ez + ((a >> 2) & 1);
+    return ix + g.n[0] * (iy + (long long)g.n[1] * iz);
+  } else {
+    return ix + g.n[0] * iy;
+  }
+}
+
+template <int D, class T>
+__device__ __forceinline__ void gather(const Geom& g, const T* __restrict__ x, int ex, int ey,
+                                       int ez, T (*xe)[1 << D]) {
+#pragma unroll
+  for (int a = 0; a < (1 << D); ++a) {
+    const long long idx = corner_node<D>(g, ex, ey, ez, a);
+#pragma unroll
+    for (int f = 0; f <= D; ++f) xe[f][a] = x[f * g.N + idx];
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void elem_coords(const Geom& g, long long e, int& ex, int& ey, int& ez) {
+  ex = int(e % g.ne[0]);
+  const long long r = e / g.ne[0];
+  if constexpr (D == 3) {
+    ey = int(r % g.ne[1]);
+    ez = int(r / g.ne[1]);
+  } else {
+    ey = int(r);
+    ez = 0;
+  }
+}
+
+// ------------------------------------------------------------ energy
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_energy(Geom g, Mat<double> m, const T* __restrict__ x,
+                                                double* partials, unsigned* counter, double* out) {
+  double acc[1] = {0.0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.NE;
+       e += (long long)gridDim.x * blockDim.x) {
+    int ex, ey, ez;
+    elem_coords<D>(g, e, ex, ey, ez);
+    T xt[D + 1][1 << D];
+    gather<D, T>(g, x, ex, ey, ez, xt);
+    double xe[D + 1][1 << D];
+#pragma unroll
+    for (int f = 0; f <= D; ++f)
+#pragma unroll
+      for (int a = 0; a < (1 << D); ++a) xe[f][a] = double(xt[f][a]);
+    acc[0] += elem_energy<D, double>(xe, m);
+  }
+  grid_finish<1, OpSum>(acc, partials, counter, out);
+}
+
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_energy_diff(Geom g, Mat<double> m,
+                                                     const T* __restrict__ x,
+                                                     const T* __restrict__ s, double* partials,
+                                                     unsigned* counter, double* out) {
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.NE;
+       e += (long long)gridDim.x * blockDim.x) {
+    int ex, ey, ez;
+    elem_coords<D>(g, e, ex, ey, ez);
+    T xt[D + 1][1 << D], st[D + 1][1 << D];
+    gather<D, T>(g, x, ex, ey, ez, xt);
+    gather<D, T>(g, s, ex, ey, ez, st);
+    double xe[D + 1][1 << D], se[D + 1][1 << D];
+#pragma unroll
+    for (int f = 0; f <= D; ++f)
+#pragma unroll
+      for (int a = 0; a < (1 << D); ++a) {
+        xe[f][a] = double(xt[f][a]);
+        se[f][a] = double(st[f][a]);
+      }
+    double a4[4];
+    elem_energy_diff<D, double>(xe, se, m, a4);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] += a4[k];
+  }
+  grid_finish<4, OpSum>(acc, partials, counter, out);
+}
+
+// ------------------------------------------------------------ scatter ops
+template <int D>
+struct Tile;
+template <>
+struct Tile<3> {
+  static constexpr int X = 8, Y = 8, Z = 8, THREADS = 256;
+};
+template <>
+struct Tile<2> {
+  static constexpr int X = 32, Y = 8, Z = 1, THREADS = 128;
+};
+
+enum { OP_GRAD = 0, OP_HESS = 1 };
+
+template <int D, class T, int OP>
+__global__ void __launch_bounds__(Tile<D>::THREADS)
+    k_elem_scatter(Geom g, Mat<T> m, const T* __restrict__ x, const T* __restrict__ v,
+                   T* __restrict__ y) {
+  constexpr int F = D + 1, NC = 1 << D;
+  constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+  constexpr int EX = TX + 1, EY = TY + 1, EZ = D == 3 ? TZ + 1 : 1;
+  constexpr int NEL = EX * EY * EZ, NOWN = TX * TY * TZ, NT = Tile<D>::THREADS;
+  __shared__ T acc[F][NOWN];
+  const int ox = blockIdx.x * TX, oy = blockIdx.y * TY, oz = D == 3 ? blockIdx.z * TZ : 0;
+  for (int i = threadIdx.x; i < F * NOWN; i += NT) (&acc[0][0])[i] = T(0);
+  __syncthreads();
+  for (int base = 0; base < NEL; base += NT) {
+    const int e = base + threadIdx.x;
+    const int lx = e % EX - 1, ly = (e / EX) % EY - 1, lz = D == 3 ? e / (EX * EY) - 1 : 0;
+    const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+    bool valid = e < NEL && gx >= 0 && gx < g.ne[0] && gy >= 0 && gy < g.ne[1];
+    if constexpr (D == 3) valid = valid && gz >= 0 && gz < g.ne[2];
+    T out[F][NC];
+    if (valid) {
+      T xe[F][NC];
+      gather<D, T>(g, x, gx, gy, gz, xe);
+      if constexpr (OP == OP_HESS) {
+        T ve[F][NC];
+        gather<D, T>(g, v, gx, gy, gz, ve);
+        elem_hessvec<D, T>(xe, ve, m, out);
+      } else {
+        elem_gradient<D, T>(xe, m, out);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+      const int nx = lx + (a & 1), ny = ly + ((a >> 1) & 1), nz = lz + ((a >> 2) & 1);
+      bool own = valid && nx >= 0 && nx < TX && ny >= 0 && ny < TY;
+      if constexpr (D == 3) own = own && nz >= 0 && nz < TZ;
+      if (own) {
+        const int li = nx + TX * (ny + TY * (D == 3 ? nz : 0));
+#pragma unroll
+        for (int f = 0; f < F; ++f) acc[f][li] += out[f][a];
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < NOWN; i += NT) {
+    const int nx = i % TX, ny = (i / TX) % TY, nz = D == 3 ? i / (TX * TY) : 0;
+    const int gx = ox + nx, gy = oy + ny, gz = oz + nz;
+    if (gx < g.n[0] && gy < g.n[1] && gz < g.n[2]) {
+      const long long idx = gx + g.n[0] * (gy + (long long)g.n[1] * gz);
+#pragma unroll
+      for (int f = 0; f < F; ++f) y[f * g.N + idx] = acc[f][i];
+    }
+  }
+}
+
+template <int D>
+static dim3 scatter_grid(const Geom& g) {
+  return dim3((g.n[0] + Tile<D>::X - 1) / Tile<D>::X, (g.n[1] + Tile<D>::Y - 1) / Tile<D>::Y,
+              D == 3 ? (g.n[2] + Tile<D>::Z - 1) / Tile<D>::Z : 1);
+}
+
+template <int D, class T, int OP>
+static cudaError_t launch_scatter(const Geom& g, const Mat<double>& m, const void* x,
+                                  const void* v, void* y, cudaStream_t st) {
+  k_elem_scatter<D, T, OP><<<scatter_grid<D>(g), Tile<D>::THREADS, 0, st>>>(
+      g, cast_mat<T>(m), static_cast<const T*>(x), static_cast<const T*>(v), static_cast<T*>(y));
+  return cudaGetLastError();
+}
+
+cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, void* y, int prec,
+                          cudaStream_t st) {
+  if (g.dim == 3)
+    return prec ? launch_scatter<3, float, OP_GRAD>(g, m, x, nullptr, y, st)
+                : launch_scatter<3, double, OP_GRAD>(g, m, x, nullptr, y, st);
+  return prec ? launch_scatter<2, float, OP_GRAD>(g, m, x, nullptr, y, st)
+              : launch_scatter<2, double, OP_GRAD>(g, m, x, nullptr, y, st);
+}
+
+cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
+                         void* y, int prec, cudaStream_t st) {
+  if (g.dim == 3)
+    return prec ? launch_scatter<3, float, OP_HESS>(g, m, x, v, y, st)
+                : launch_scatter<3, double, OP_HESS>(g, m, x, v, y, st);
+  return prec ? launch_scatter<2, float, OP_HESS>(g, m, x, v, y, st)
+              : launch_scatter<2, double, OP_HESS>(g, m, x, v, y, st);
+}
+
+template <int D, class T>
+static cudaError_t launch_energy(const Geom& g, const Mat<double>& m, const void* x,
+                                 const Scratch& s, double* out, cudaStream_t st) {
+  const int nb = reduce_grid(g.NE, 256);
+  k_energy<D, T><<<nb, 256, 0, st>>>(g, m, static_cast<const T*>(x), s.partials, s.counter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t elem_energy(const Geom& g, const Mat<double>& m, const void* x, int prec,
+                        const Scratch& s, double* out, cudaStream_t st) {
+  if (g.dim == 3)
+    return prec ? launch_energy<3, float>(g, m, x, s, out, st)
+                : launch_energy<3, double>(g, m, x, s, out, st);
+  return prec ? launch_energy<2, float>(g, m, x, s, out, st)
+              : launch_energy<2, double>(g, m, x, s, out, st);
+}
+
+template <int D, class T>
+static cudaError_t launch_energy_diff(const Geom& g, const Mat<double>& m, const void* x,
+                                      const void* sv, const Scratch& s, double* out,
+                                      cudaStream_t st) {
+  const int nb = reduce_grid(g.NE, 256);
+  k_energy_diff<D, T><<<nb, 256, 0, st>>>(g, m, static_cast<const T*>(x),
+                                           static_cast<const T*>(sv), s.partials, s.counter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x, const void* sv,
+                             int prec, const Scratch& s, double* out, cudaStream_t st) {
+  if (g.dim == 3)
+    return prec ? launch_energy_diff<3, float>(g, m, x, sv, s, out, st)
+                : launch_energy_diff<3, double>(g, m, x, sv, s, out, st);
+  return prec ? launch_energy_diff<2, float>(g, m, x, sv, s, out, st)
+              : launch_energy_diff<2, double>(g, m, x, sv, s, out, st);
+}
+
+// ------------------------------------------------------------ rasterisation
+// LINE2D device rows: [cx, cy, tx, ty, nx, ny, half_length]
+// DISC3D device rows: [cx, cy, cz, nx, ny, nz, radius]
+// Products and sums are rounded one by one (no contraction) so that the
+// band test takes the same FP64 decisions as a plain evaluation.
+__global__ void k_raster(Geom g, int kind, int nrows, const double* __restrict__ rows,
+                         double band, double* __restrict__ c, double* __restrict__ cprev) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long ix = i % g.n[0];
+    const long long r = i / g.n[0];
+    const long long iy = r % g.n[1];
+    const long long iz = r / g.n[1];
+    const double X = __dmul_rn(double(ix), g.h), Y = __dmul_rn(double(iy), g.h),
+                 Z = __dmul_rn(double(iz), g.h);
+    bool in = false;
+    for (int k = 0; k < nrows && !in; ++k) {
+      const double* q = rows + 7 * k;
+      if (kind == 0) {
+        const double dx = __dadd_rn(X, -q[0]), dy = __dadd_rn(Y, -q[1]);
+        const double dn = fabs(__dadd_rn(__dmul_rn(q[4], dx), __dmul_rn(q[5], dy)));
+        const double dt = fabs(__dadd_rn(__dmul_rn(q[2], dx), __dmul_rn(q[3], dy)));
+        in = dn <= band && dt <= q[6];
+      } else {
+        const double dx = __dadd_rn(X, -q[0]), dy = __dadd_rn(Y, -q[1]), dz = __dadd_rn(Z, -q[2]);
+        const double dn = __dadd_rn(__dadd_rn(__dmul_rn(q[3], dx), __dmul_rn(q[4], dy)),
+                                    __dmul_rn(q[5], dz));
+        const double px = __dadd_rn(dx, -__dmul_rn(dn, q[3]));
+        const double py = __dadd_rn(dy, -__dmul_rn(dn, q[4]));
+        const double pz = __dadd_rn(dz, -__dmul_rn(dn, q[5]));
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+        in = fabs(dn) <= band && r2 <= __dmul_rn(q[6], q[6]);
+      }
+    }
+    const double val = in ? 1.0 : 0.0;
+    c[i] = val;
+    cprev[i] = val;
+  }
+}
+
+cudaError_t rasterize(const Geom& g, int kind, int n, const double* rows_dev, double band,
+                      double* c_plane, double* c_prev, cudaStream_t st) {
+  long long nb = (g.N + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  k_raster<<<int(nb), 256, 0, st>>>(g, kind, n, rows_dev, band, c_plane, c_prev);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ transfers
+// Q1 prolongation: a fine node on an even index coincides with a coarse
+// node; on an odd index it averages its two coarse neighbours (per axis).
+template <class T>
+__global__ void k_prolong(Geom gc, Geom gf, int nf, const T* __restrict__ in, T* __restrict__ out) {
+  const long long total = gf.N * nf;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int f = int(t / gf.N);
+    const long long i = t - f * gf.N;
+    const int ix = int(i % gf.n[0]);
+    const long long r = i / gf.n[0];
+    const int iy = int(r % gf.n[1]);
+    const int iz = int(r / gf.n[1]);
+    int c0[3] = {ix >> 1, iy >> 1, iz >> 1};
+    int odd[3] = {ix & 1, iy & 1, iz & 1};
+    const T* src = in + f * gc.N;
+    T acc = T(0);
+    for (int dz = 0; dz <= odd[2]; ++dz)
+      for (int dy = 0; dy <= odd[1]; ++dy)
+        for (int dx = 0; dx <= odd[0]; ++dx) {
+          T wgt = T(1);
+          if (odd[0]) wgt *= T(0.5);
+          if (odd[1]) wgt *= T(0.5);
+          if (odd[2]) wgt *= T(0.5);
+          const long long j = (c0[0] + dx) + gc.n[0] * ((c0[1] + dy) + (long long)gc.n[1] * (c0[2] + dz));
+          acc += wgt * src[j];
+        }
+    out[t] = acc;
+  }
+}
+
+// Restriction R = I^T: a coarse node collects the fine nodes within one fine
+// spacing, weight 1 on the coincident node and 1/2 per odd offset and axis.
+// With normalise, the sum is divided by the sum of the weights (P).
+template <class T>
+__global__ void k_restrict(Geom gc, Geom gf, int nf, const T* __restrict__ in,
+                           T* __restrict__ out, bool normalise) {
+  const long long total = gc.N * nf;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int f = int(t / gc.N);
+    const long long j = t - f * gc.N;
+    const int jx = int(j % gc.n[0]);
+    const long long r = j / gc.n[0];
+    const int jy = int(r % gc.n[1]);
+    const int jz = int(r / gc.n[1]);
+    const T* src = in + f * gf.N;
+    T acc = T(0), wsum = T(0);
+    const int zlo = gf.dim == 3 ? -1 : 0, zhi = gf.dim == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+      const int iz = 2 * jz + dz;
+      if (iz < 0 || iz >= gf.n[2]) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int iy = 2 * jy + dy;
+        if (iy < 0 || iy >= gf.n[1]) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ix = 2 * jx + dx;
+          if (ix < 0 || ix >= gf.n[0]) continue;
+          T wgt = T(1);
+          if (dx) wgt *= T(0.5);
+          if (dy) wgt *= T(0.5);
+          if (dz) wgt *= T(0.5);
+          acc += wgt * src[ix + gf.n[0] * (iy + (long long)gf.n[1] * iz)];
+          wsum += wgt;
+        }
+      }
+    }
+    out[t] = normalise ? acc / wsum : acc;
+  }
+}
+
+__global__ void k_bounds(Geom gc, Geom gf, int nf, const double* __restrict__ lo_f,
+                         const double* __restrict__ hi_f, double* __restrict__ lo_c,
+                         double* __restrict__ hi_c) {
+  const long long total = gc.N * nf;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int f = int(t / gc.N);
+    const long long j = t - f * gc.N;
+    const int jx = int(j % gc.n[0]);
+    const long long r = j / gc.n[0];
+    const int jy = int(r % gc.n[1]);
+    const int jz = int(r / gc.n[1]);
+    double lo = -INFINITY, hi = INFINITY;
+    const int zlo = gf.dim == 3 ? -1 : 0, zhi = gf.dim == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+      const int iz = 2 * jz + dz;
+      if (iz < 0 || iz >= gf.n[2]) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int iy = 2 * jy + dy;
+        if (iy < 0 || iy >= gf.n[1]) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ix = 2 * jx + dx;
+          if (ix < 0 || ix >= gf.n[0]) continue;
+          const long long i = f * gf.N + ix + gf.n[0] * (iy + (long long)gf.n[1] * iz);
+          lo = fmax(lo, lo_f[i]);
+          hi = fmin(hi, hi_f[i]);
+        }
+      }
+    }
+    lo_c[t] = lo;
+    hi_c[t] = hi;
+  }
+}
+
+static int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 8192) b = 8192;
+  if (b < 1) b = 1;
+  return int(b);
+}
+
+cudaError_t xfer_prolong(const Geom& gc, const Geom& gf, int nf, const void* in, void* out,
+                         int prec, cudaStream_t st) {
+  const int nb = grid_for(gf.N * nf);
+  if (prec)
+    k_prolong<float><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const float*>(in), static_cast<float*>(out));
+  else
+    k_prolong<double><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const double*>(in), static_cast<double*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t xfer_restrict(const Geom& gc, const Geom& gf, int nf, const void* in, void* out,
+                          int prec, bool normalise, cudaStream_t st) {
+  const int nb = grid_for(gc.N * nf);
+  if (prec)
+    k_restrict<float><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const float*>(in), static_cast<float*>(out), normalise);
+  else
+    k_restrict<double><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const double*>(in), static_cast<double*>(out), normalise);
+  return cudaGetLastError();
+}
+
+cudaError_t xfer_bounds(const Geom& gc, const Geom& gf, int nf, const double* lo_f,
+                        const double* hi_f, double* lo_c, double* hi_c, cudaStream_t st) {
+  k_bounds<<<grid_for(gc.N * nf), 256, 0, st>>>(gc, gf, nf, lo_f, hi_f, lo_c, hi_c);
+  return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -1,0 +1,586 @@
+// RMTR load step on the device (Algorithm 1 V-cycle, Algorithm 2 trust-region
+// method, Algorithm 3 Convergence_control, eq. rho_tr / rho_ml, Hessian
+// lagging of Sec. 4.2.1), with a projected-search truncated CG for the
+// trust-region subproblem eq. (model_qp).
+//
+// All vectors stay on the device.  The host keeps only the control flow: it
+// reads back the few scalars each branch needs (dot products, ratios) from
+// deterministic grid reductions.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <string>
+
+#include "pf_hier.h"
+#include "pf_reduce.cuh"
+
+namespace pf {
+
+struct CudaFail {
+  cudaError_t e;
+  const char* where;
+};
+
+static inline void ck(cudaError_t e, const char* where) {
+  if (e != cudaSuccess) throw CudaFail{e, where};
+}
+
+template <class F>
+__global__ void k_map(long long n, F f) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    f(i);
+}
+
+template <int K, class Op, class F>
+__global__ void __launch_bounds__(256) k_red(long long n, F f, double* partials, unsigned* counter,
+                                             double* out) {
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = Op::id();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v[K];
+    f(i, v);
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = Op::op(acc[k], v[k]);
+  }
+  grid_finish<K, Op>(acc, partials, counter, out);
+}
+
+static int map_grid(long long n) {
+  long long b = (n + 255) / 256;
+  return int(std::max(1LL, std::min(b, 4LL * 1216)));
+}
+
+// Is plane-local node i on the domain boundary?
+__device__ __forceinline__ bool on_boundary(const Geom& g, long long i) {
+  const int ix = int(i % g.n[0]);
+  const long long r = i / g.n[0];
+  const int iy = int(r % g.n[1]);
+  const int iz = int(r / g.n[1]);
+  bool b = ix == 0 || ix == g.n[0] - 1 || iy == 0 || iy == g.n[1] - 1;
+  if (g.dim == 3) b = b || iz == 0 || iz == g.n[2] - 1;
+  return b;
+}
+
+struct Solver {
+  pf_hierarchy* H;
+  const pf_rmtr_params& P;
+  pf_rmtr_stats& S;
+  cudaStream_t st;
+  int L, F;
+  bool mixed;
+
+  Solver(pf_hierarchy* h, const pf_rmtr_params& p, pf_rmtr_stats& s)
+      : H(h), P(p), S(s), st(h->st), L(h->L), F(h->dim + 1), mixed(p.precision == PF_FP32) {}
+
+  // ---------------------------------------------------------------- helpers
+  template <class Fn>
+  void map(long long n, Fn f) {
+    k_map<<<map_grid(n), 256, 0, st>>>(n, f);
+    ck(cudaGetLastError(), "map");
+    S.launches += 1;
+  }
+
+  template <int K, class Op, class Fn>
+  void reduce(long long n, Fn f, double* out) {
+    k_red<K, Op><<<reduce_grid(n), 256, 0, st>>>(n, f, H->scratch.partials, H->scratch.counter,
+                                                  H->d_res);
+    ck(cudaGetLastError(), "reduce");
+    S.launches += 1;
+    fetch(K, out);
+  }
+
+  void fetch(int K, double* out) {
+    ck(cudaMemcpyAsync(H->h_res, H->d_res, sizeof(double) * K, cudaMemcpyDeviceToHost, st), "fetch");
+    ck(cudaStreamSynchronize(st), "sync");
+    for (int k = 0; k < K; ++k) out[k] = H->h_res[k];
+  }
+
+  long long nd(int l) const { return H->lv[l].n; }
+  double frac(int l) const { return double(H->geo[l].N) / double(H->geo[L - 1].N); }
+
+  void copy(double* dst, const double* src, long long n) {
+    ck(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  }
+  void zero(double* a, long long n) { ck(cudaMemsetAsync(a, 0, sizeof(double) * n, st), "zero"); }
+
+  double dot(const double* a, const double* b, long long n) {
+    double r;
+    reduce<1, OpSum>(n, [=] __device__(long long i, double(&v)[1]) { v[0] = a[i] * b[i]; }, &r);
+    return r;
+  }
+
+  // ---------------------------------------------------------------- element ops
+  void hessvec(int l, const double* x, const double* v, double* out) {
+    ck(elem_hessvec(H->geo[l], H->mat[l], x, v, out, 0, st), "hessvec");
+    S.hessvecs += 1;
+    S.fe_hessvec += frac(l);
+    S.launches += 1;
+  }
+  void gradient(int l, const double* x, double* out) {
+    ck(elem_gradient(H->geo[l], H->mat[l], x, out, 0, st), "gradient");
+    S.fe_gradient += frac(l);
+    S.launches += 1;
+  }
+  double ediff(int l, const double* x, const double* s) {
+    ck(elem_energy_diff(H->geo[l], H->mat[l], x, s, 0, H->scratch, H->d_res, st), "ediff");
+    S.fe_energy += frac(l);
+    S.launches += 1;
+    double a[4];
+    fetch(4, a);
+    return a[0] + a[1] + a[2] + a[3];
+  }
+  double energy(int l, const double* x) {
+    ck(elem_energy(H->geo[l], H->mat[l], x, 0, H->scratch, H->d_res, st), "energy");
+    S.fe_energy += frac(l);
+    S.launches += 1;
+    double e;
+    fetch(1, &e);
+    return e;
+  }
+
+  // FP32 Hessian at the lagged point (mixed precision): v and out stay FP64.
+  void hessvec_lag32(int l, const double* v, double* out) {
+    LevelBuf& B = H->lv[l];
+    float* v32 = B.v32;
+    float* h32 = B.hv32;
+    map(B.n, [=] __device__(long long i) { v32[i] = float(v[i]); });
+    ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, v32, h32, 1, st), "hessvec32");
+    S.hessvecs += 1;
+    S.fe_hessvec += frac(l);
+    S.launches += 1;
+    map(B.n, [=] __device__(long long i) { out[i] = double(h32[i]); });
+  }
+
+  void set_lag(int l, const double* x) {
+    LevelBuf& B = H->lv[l];
+    copy(B.xlag, x, B.n);
+    if (mixed) {
+      float* d = B.xlag32;
+      const double* s = B.xlag;
+      map(B.n, [=] __device__(long long i) { d[i] = float(s[i]); });
+    }
+  }
+
+  // ---------------------------------------------------------------- level model h^l
+  bool finest(int l) const { return l == L - 1; }
+  bool galerkin(int l) const { return !finest(l) && P.coarse_model == PF_GALERKIN; }
+
+  // Lagged model Hessian: finest / FIRST_ORDER: Hessian at x_lag of the level;
+  // GALERKIN: R H_{l+1} I.
+  void Hlag(int l, const double* v, double* out) {
+    if (!galerkin(l)) {
+      if (mixed) hessvec_lag32(l, v, out);
+      else hessvec(l, H->lv[l].xlag, v, out);
+      return;
+    }
+    LevelBuf& F1 = H->lv[l + 1];
+    ck(xfer_prolong(H->geo[l], H->geo[l + 1], F, v, F1.gin, 0, st), "prolong");
+    S.launches += 1;
+    Hlag(l + 1, F1.gin, F1.gout);
+    ck(xfer_restrict(H->geo[l], H->geo[l + 1], F, F1.gout, out, 0, false, st), "restrict");
+    S.launches += 1;
+  }
+
+  // dH v = R H_{l+1} I v - Hess f~(x0) v  (GALERKIN); 0 otherwise.
+  void dH(int l, const double* v, double* out) {
+    LevelBuf& B = H->lv[l];
+    Hlag(l, v, out);
+    hessvec(l, B.x0, v, B.dh);
+    const double* t = B.dh;
+    map(B.n, [=] __device__(long long i) { out[i] -= t[i]; });
+  }
+
+  // grad h(x) = grad f~(x) + dg + dH (x - x0)
+  void grad_h(int l, const double* x, double* out) {
+    gradient(l, x, out);
+    if (finest(l)) return;
+    LevelBuf& B = H->lv[l];
+    const double* dg = B.dg;
+    if (!galerkin(l)) {
+      map(B.n, [=] __device__(long long i) { out[i] += dg[i]; });
+      return;
+    }
+    const double* x0 = B.x0;
+    double* d = B.t3;
+    map(B.n, [=] __device__(long long i) { d[i] = x[i] - x0[i]; });
+    dH(l, d, B.gout == nullptr ? B.t2 : B.t2);
+    const double* e = B.t2;
+    map(B.n, [=] __device__(long long i) { out[i] += dg[i] + e[i]; });
+  }
+
+  // h(x + s) - h(x) without subtracting totals
+  double diff_h(int l, const double* x, const double* s) {
+    double d = ediff(l, x, s);
+    if (finest(l)) return d;
+    LevelBuf& B = H->lv[l];
+    d += dot(B.dg, s, B.n);
+    if (!galerkin(l)) return d;
+    const double* x0 = B.x0;
+    double* t = B.t3;
+    map(B.n, [=] __device__(long long i) { t[i] = x[i] - x0[i]; });
+    dH(l, t, B.t2);
+    d += dot(s, B.t2, B.n);
+    dH(l, s, B.t2);
+    d += 0.5 * dot(s, B.t2, B.n);
+    return d;
+  }
+
+  // ---------------------------------------------------------------- subproblem
+  // Projected-search truncated CG for min g.s + 1/2 s.Hs over lo <= s <= hi.
+  // Uses B.s (result), B.Hs, B.r, B.p, B.q, B.w, B.Hw, B.t1 (s_new), B.t2.
+  void subproblem(int l, double delta, int cg_max) {
+    LevelBuf& B = H->lv[l];
+    const long long n = B.n;
+    const double *g = B.g, *lo = B.lo, *hi = B.hi;
+    double *s = B.s, *Hs = B.Hs, *r = B.r, *p = B.p, *q = B.q, *w = B.w, *Hw = B.Hw;
+    double *t1 = B.t1, *t2 = B.t2;
+    double gmax;
+    reduce<1, OpMax>(n, [=] __device__(long long i, double(&v)[1]) {
+      const bool mv = (g[i] < 0.0 && hi[i] > 0.0) || (g[i] > 0.0 && lo[i] < 0.0);
+      v[0] = mv ? fabs(g[i]) : 0.0;
+    }, &gmax);
+    zero(s, n);
+    if (!(gmax > 0.0)) return;
+    double t = delta / gmax;
+    // exact minimiser of the model along the movable part of -g
+    map(n, [=] __device__(long long i) {
+      const bool mv = (g[i] < 0.0 && hi[i] > 0.0) || (g[i] > 0.0 && lo[i] < 0.0);
+      t1[i] = mv ? g[i] : 0.0;
+    });
+    Hlag(l, t1, t2);
+    double cg2[2];
+    reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
+      v[0] = t1[i] * t2[i];
+      v[1] = t1[i] * t1[i];
+    }, cg2);
+    if (cg2[0] > 0.0) t = std::min(t, cg2[1] / cg2[0]);
+    bool ok = false;
+    for (int bt = 0; bt <= P.cauchy_backtracks; ++bt) {
+      const double tt = t;
+      map(n, [=] __device__(long long i) { s[i] = fmin(fmax(-tt * g[i], lo[i]), hi[i]); });
+      Hlag(l, s, Hs);
+      double a[2];
+      reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
+        v[0] = g[i] * s[i];
+        v[1] = s[i] * Hs[i];
+      }, a);
+      if (a[0] + 0.5 * a[1] <= P.cauchy_c * a[0]) {
+        ok = true;
+        break;
+      }
+      t *= 0.5;
+    }
+    if (!ok) {
+      zero(s, n);
+      return;
+    }
+    int used = 0;
+    double tol = -1.0;
+    while (used < cg_max) {
+      double rr;
+      reduce<1, OpSum>(n, [=] __device__(long long i, double(&v)[1]) {
+        const bool fr = lo[i] < s[i] && s[i] < hi[i];
+        const double ri = fr ? -(g[i] + Hs[i]) : 0.0;
+        r[i] = ri;
+        p[i] = ri;
+        w[i] = 0.0;
+        Hw[i] = 0.0;
+        v[0] = ri * ri;
+      }, &rr);
+      if (tol < 0.0) {
+        const double r0 = std::sqrt(rr);
+        tol = std::min(0.1, std::sqrt(r0)) * r0;
+      }
+      if (std::sqrt(rr) <= tol || rr == 0.0) break;
+      bool leave = false;
+      while (used < cg_max) {
+        Hlag(l, p, q);
+        double kappa;
+        reduce<1, OpSum>(n, [=] __device__(long long i, double(&v)[1]) {
+          const bool fr = lo[i] < s[i] && s[i] < hi[i];
+          const double qi = fr ? q[i] : 0.0;
+          q[i] = qi;
+          v[0] = p[i] * qi;
+        }, &kappa);
+        ++used;
+        S.cg += 1;
+        if (kappa <= 0.0) {
+          double amax;
+          reduce<1, OpMin>(n, [=] __device__(long long i, double(&v)[1]) {
+            const bool fr = lo[i] < s[i] && s[i] < hi[i];
+            const double sw = s[i] + w[i];
+            double a = INFINITY;
+            if (fr && p[i] > 0.0) a = (hi[i] - sw) / p[i];
+            if (fr && p[i] < 0.0) a = (lo[i] - sw) / p[i];
+            v[0] = a;
+          }, &amax);
+          amax = std::max(amax, 0.0);
+          if (std::isfinite(amax)) {
+            const double am = amax;
+            map(n, [=] __device__(long long i) {
+              w[i] += am * p[i];
+              Hw[i] += am * q[i];
+            });
+          }
+          leave = true;
+          break;
+        }
+        const double alpha = rr / kappa;
+        double u2[2];
+        reduce<2, OpMax>(n, [=] __device__(long long i, double(&v)[2]) {
+          const bool fr = lo[i] < s[i] && s[i] < hi[i];
+          const double wi = w[i] + alpha * p[i];
+          w[i] = wi;
+          Hw[i] += alpha * q[i];
+          const double ri = r[i] - alpha * q[i];
+          r[i] = ri;
+          const double sw = s[i] + wi;
+          v[0] = (fr && (sw < lo[i] || sw > hi[i])) ? 1.0 : 0.0;
+          v[1] = 0.0;
+        }, u2);
+        const double rr_new = dot(r, r, n);
+        if (u2[0] > 0.0) {
+          leave = true;
+          break;
+        }
+        if (std::sqrt(rr_new) <= tol) break;
+        const double beta = rr_new / rr;
+        map(n, [=] __device__(long long i) { p[i] = r[i] + beta * p[i]; });
+        rr = rr_new;
+      }
+      if (!leave) {
+        map(n, [=] __device__(long long i) {
+          s[i] += w[i];
+          Hs[i] += Hw[i];
+        });
+        break;
+      }
+      // projected search along w
+      double ms[2];
+      reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
+        v[0] = g[i] * s[i];
+        v[1] = s[i] * Hs[i];
+      }, ms);
+      const double m_s = ms[0] + 0.5 * ms[1];
+      double beta = 1.0;
+      bool accepted = false;
+      for (int bt = 0; bt <= P.cauchy_backtracks; ++bt) {
+        const double b = beta;
+        map(n, [=] __device__(long long i) { t1[i] = fmin(fmax(s[i] + b * w[i], lo[i]), hi[i]); });
+        Hlag(l, t1, t2);
+        double a[3];
+        reduce<3, OpSum>(n, [=] __device__(long long i, double(&v)[3]) {
+          v[0] = g[i] * t1[i];
+          v[1] = t1[i] * t2[i];
+          v[2] = (g[i] + Hs[i]) * (t1[i] - s[i]);
+        }, a);
+        if (a[0] + 0.5 * a[1] <= m_s + P.cauchy_c * a[2]) {
+          accepted = true;
+          break;
+        }
+        beta *= 0.5;
+      }
+      if (!accepted) break;
+      copy(s, t1, n);
+      copy(Hs, t2, n);
+    }
+    map(n, [=] __device__(long long i) { s[i] = fmin(fmax(s[i], lo[i]), hi[i]); });
+  }
+
+  // ---------------------------------------------------------------- TR method
+  void tr_box(int l, const double* x, double delta) {
+    LevelBuf& B = H->lv[l];
+    const double *lb = B.lb, *ub = B.ub;
+    double *lo = B.lo, *hi = B.hi;
+    map(B.n, [=] __device__(long long i) {
+      lo[i] = fmax(lb[i] - x[i], -delta);
+      hi[i] = fmin(ub[i] - x[i], delta);
+    });
+  }
+
+  void control(double rho, int l, double* x, double& delta) {
+    LevelBuf& B = H->lv[l];
+    if (rho > P.eta1) {
+      const double *s = B.s, *lb = B.lb, *ub = B.ub;
+      map(B.n, [=] __device__(long long i) { x[i] = fmin(fmax(x[i] + s[i], lb[i]), ub[i]); });
+    }
+    if (rho < P.eta1) delta = P.gamma1 * delta;
+    else if (rho > P.eta2) delta = std::min(P.gamma2 * delta, P.delta_max);
+  }
+
+  // Algorithm 2 on level l, iterate in B.x, `iters` TR steps.
+  void nonlinear_solve(int l, double& delta, int iters, int cg_max) {
+    LevelBuf& B = H->lv[l];
+    for (int it = 0; it < iters; ++it) {
+      grad_h(l, B.x, B.g);
+      tr_box(l, B.x, delta);
+      subproblem(l, delta, cg_max);
+      Hlag(l, B.s, B.t2);
+      double a[2];
+      const double *g = B.g, *s = B.s, *hs = B.t2;
+      reduce<2, OpSum>(B.n, [=] __device__(long long i, double(&v)[2]) {
+        v[0] = g[i] * s[i];
+        v[1] = s[i] * hs[i];
+      }, a);
+      const double pred = -(a[0] + 0.5 * a[1]);
+      S.tr_its += 1;
+      if (!(pred > 0.0)) break;
+      const double rho = -diff_h(l, B.x, B.s) / pred;
+      if (rho <= P.eta1) S.tr_rejected += 1;
+      control(rho, l, B.x, delta);
+    }
+  }
+
+  // Algorithm 1 on level l starting from B.x (B.xlag set by the caller).
+  void vcycle(int l, double& delta) {
+    LevelBuf& B = H->lv[l];
+    const int cg = finest(l) ? P.cg_fine : P.cg_smooth;
+    nonlinear_solve(l, delta, P.mu1, cg);
+    if (l == 0) return;
+    LevelBuf& C = H->lv[l - 1];
+    const Geom &gc = H->geo[l - 1], &gf = H->geo[l];
+    // fine correction bounds at x_mu1 -> coarse feasible set
+    tr_box(l, B.x, delta);
+    ck(xfer_bounds(gc, gf, F, B.lo, B.hi, C.lo, C.hi, st), "bounds");
+    S.launches += 1;
+    ck(xfer_restrict(gc, gf, F, B.x, C.x0, 0, true, st), "project");
+    S.launches += 1;
+    {
+      const double *x0 = C.x0, *lo = C.lo, *hi = C.hi;
+      double *lb = C.lb, *ub = C.ub, *xc = C.x;
+      map(C.n, [=] __device__(long long i) {
+        lb[i] = x0[i] + lo[i];
+        ub[i] = x0[i] + hi[i];
+        xc[i] = x0[i];
+      });
+    }
+    // dg = R grad h^l(x_mu1) - grad f~(x0)
+    grad_h(l, B.x, B.g);
+    ck(xfer_restrict(gc, gf, F, B.g, C.dg, 0, false, st), "restrict");
+    S.launches += 1;
+    gradient(l - 1, C.x0, C.t1);
+    {
+      double* dg = C.dg;
+      const double* t = C.t1;
+      map(C.n, [=] __device__(long long i) { dg[i] -= t[i]; });
+    }
+    set_lag(l - 1, C.x0);
+    double dc = delta;
+    if (l - 1 == 0) nonlinear_solve(0, dc, P.coarse_its, P.cg_coarse);
+    else vcycle(l - 1, dc);
+    // s = I (x* - x0), pred = h^{l-1}(x0) - h^{l-1}(x*)
+    {
+      const double* x0 = C.x0;
+      const double* xs = C.x;
+      double* d = C.t3;
+      map(C.n, [=] __device__(long long i) { d[i] = xs[i] - x0[i]; });
+    }
+    // C.t3 holds the coarse correction; diff_h uses C.t2/C.t3 as scratch, so
+    // keep a copy in C.w
+    copy(C.w, C.t3, C.n);
+    const double pred = -diff_h(l - 1, C.x0, C.w);
+    ck(xfer_prolong(gc, gf, F, C.w, B.s, 0, st), "prolong");
+    S.launches += 1;
+    if (pred > 0.0) {
+      const double rho = -diff_h(l, B.x, B.s) / pred;
+      if (rho <= P.eta1) S.coarse_rejected += 1;
+      control(rho, l, B.x, delta);
+    }
+    nonlinear_solve(l, delta, P.mu2, cg);
+  }
+
+  double pg_norm(const double* x) {
+    LevelBuf& B = H->lv[L - 1];
+    gradient(L - 1, x, B.g);
+    const double *g = B.g, *lb = B.lb, *ub = B.ub;
+    double r;
+    reduce<1, OpSum>(B.n, [=] __device__(long long i, double(&v)[1]) {
+      const double d = x[i] - fmin(fmax(x[i] - g[i], lb[i]), ub[i]);
+      v[0] = d * d;
+    }, &r);
+    return std::sqrt(r);
+  }
+
+  pf_status run(double* x_user) {
+    LevelBuf& B = H->lv[L - 1];
+    const Geom g = H->geo[L - 1];
+    const long long N = g.N;
+    const int dim = H->dim;
+    copy(B.x, x_user, B.n);
+    // c_prev := c ; finest bounds of eq. (space_pf), clamped displacement
+    copy(H->c_prev, B.x + dim * N, N);
+    {
+      double *lb = B.lb, *ub = B.ub, *x = B.x;
+      const double* cp = H->c_prev;
+      map(B.n, [=] __device__(long long i) {
+        const int f = int(i / N);
+        const long long k = i - f * N;
+        double l, u;
+        if (f == dim) {
+          l = cp[k];
+          u = 1.0;
+        } else if (on_boundary(g, k)) {
+          l = 0.0;
+          u = 0.0;
+        } else {
+          l = -INFINITY;
+          u = INFINITY;
+        }
+        lb[i] = l;
+        ub[i] = u;
+        x[i] = fmin(fmax(x[i], l), u);
+      });
+    }
+    const double pg0 = pg_norm(B.x);
+    if (!std::isfinite(pg0)) {
+      copy(x_user, B.x, B.n);
+      ck(cudaStreamSynchronize(st), "sync");
+      return PF_ENONFINITE;
+    }
+    double pg = pg0;
+    double delta = P.delta0;
+    int cycles = 0;
+    bool conv = pg0 <= P.atol;
+    while (!conv && cycles < P.max_cycles) {
+      set_lag(L - 1, B.x);
+      vcycle(L - 1, delta);
+      ++cycles;
+      pg = pg_norm(B.x);
+      if (!std::isfinite(pg)) break;
+      conv = pg <= std::max(P.rtol * pg0, P.atol);
+    }
+    S.cycles = cycles;
+    S.converged = conv ? 1 : 0;
+    S.pg0 = pg0;
+    S.pg = pg;
+    S.energy = energy(L - 1, B.x);
+    copy(x_user, B.x, B.n);
+    ck(cudaStreamSynchronize(st), "sync");
+    if (!std::isfinite(pg)) return PF_ENONFINITE;
+    return conv ? PF_OK : PF_ENOTCONV;
+  }
+};
+
+pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_params& P,
+                              pf_rmtr_stats* stats) {
+  pf_rmtr_stats S{};
+  const auto t0 = std::chrono::steady_clock::now();
+  pf_status rc;
+  try {
+    Solver solver(H, P, S);
+    rc = solver.run(x_dev);
+  } catch (const CudaFail& f) {
+    set_error(std::string("CUDA error in ") + f.where + ": " + cudaGetErrorString(f.e));
+    return PF_ECUDA;
+  }
+  S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rc == PF_ENOTCONV) set_error("rmtr_load_step: max_cycles reached before the tolerance");
+  if (rc == PF_ENONFINITE) set_error("rmtr_load_step: non-finite projected gradient");
+  if (stats) *stats = S;
+  return rc;
+}
+
+}  // namespace pf

@@ -1,0 +1,176 @@
+"""The device RMTR load step against the oracle (converged fields on the 2D
+65^2 workload, small 3D hierarchies, the 1D closed form) and its invariants
+at the 3D 129^3 workload size."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import pfinputs as PI
+from oracle import pf_oracle as O
+from tests.gpu_common import dev, host, pair, relinf, require_cuda
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+# converged-field parity (relative, per field, max norm) and energy parity
+FIELD_TOL = 1e-8
+ENERGY_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pf():
+    require_cuda()
+    import paper_2007_12908_gb300 as m
+    return m
+
+
+def _fields(x, dim, N):
+    return [x[f * N:(f + 1) * N] for f in range(dim + 1)]
+
+
+def _compare_fields(xg, xo, dim, N):
+    for f, (a, b) in enumerate(zip(_fields(xg, dim, N), _fields(xo, dim, N))):
+        scale = max(np.max(np.abs(b)), 1e-300)
+        assert np.max(np.abs(a - b)) <= FIELD_TOL * scale, (f, np.max(np.abs(a - b)) / scale)
+
+
+def _sneddon_setup(pf, model):
+    H, Ho = pair(2, (33, 33), 2, 1 / 32, p=1e-3)
+    import torch
+    g = Ho.fine
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    pf.fractures_set(H, pf.PF_LINE2D, PI.centred_crack_2d(), g.h, x)
+    xo = np.zeros(3 * g.N)
+    xo[2 * g.N:] = O.rasterize(g, O.LINE2D, PI.centred_crack_2d(), g.h)
+    return H, Ho, x, xo
+
+
+@pytest.fixture(scope="module")
+def sneddon_runs(pf):
+    out = {}
+    for model in (O.FIRST_ORDER, O.GALERKIN):
+        H, Ho, x, xo = _sneddon_setup(pf, model)
+        tr = O.TRParams(coarse_model=model, rtol=1e-13)
+        ro = O.rmtr_load_step(Ho, xo, tr, p=1e-3)
+        st = pf.rmtr_load_step(H, x, pf.default_params(coarse_model=model, rtol=1e-13))
+        out[model] = (H, Ho, host(x), ro, st)
+    return out
+
+
+@pytest.mark.parametrize("model", [O.FIRST_ORDER, O.GALERKIN])
+def test_2d_load_step_matches_oracle(sneddon_runs, model):
+    H, Ho, xg, ro, st = sneddon_runs[model]
+    assert st["converged"] == 1 and ro.converged
+    _compare_fields(xg, ro.x, 2, Ho.fine.N)
+    assert abs(st["energy"] - ro.energy) <= ENERGY_TOL * abs(ro.energy)
+
+
+def test_2d_sneddon_and_invariants(sneddon_runs):
+    gold = json.load(open(os.path.join(GOLD, "sneddon.json")))
+    H, Ho, xg, ro, st = sneddon_runs[O.FIRST_ORDER]
+    g = Ho.fine
+    uy = xg[g.N:2 * g.N].reshape(65, 65)
+    cod = uy[34, 32] - uy[30, 32]
+    assert cod > 0 and abs(cod / gold["w_centre"] - 1) < gold["rel_band"]
+    c = xg[2 * g.N:]
+    c0 = O.rasterize(g, O.LINE2D, PI.centred_crack_2d(), g.h)
+    assert np.all(c >= c0) and np.all(c <= 1.0)
+    bnd = g.boundary_nodes()
+    assert np.all(xg[:g.N][bnd] == 0) and np.all(xg[g.N:2 * g.N][bnd] == 0)
+
+
+def test_deterministic_and_host_entry(pf):
+    import torch
+    H, Ho, x1, _ = _sneddon_setup(pf, O.FIRST_ORDER)
+    x2 = x1.clone()
+    xh = host(x1).copy()
+    prm = pf.default_params(rtol=1e-8)
+    pf.rmtr_load_step(H, x1, prm)
+    pf.rmtr_load_step(H, x2, prm)
+    pf.rmtr_load_step_host(H, xh, prm)
+    assert torch.equal(x1, x2)
+    assert np.array_equal(host(x1), xh)
+
+
+def test_pure_phase_field_closed_form(pf):
+    import torch
+    H, Ho = pair(2, (17, 3), 2, 1 / 16, p=0.0)
+    g = Ho.fine
+    rows = np.array([[0.5 + 0.25 * g.h, 0.5, math.pi / 2, 10.0]])
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    pf.fractures_set(H, pf.PF_LINE2D, rows, g.h, x)
+    st = pf.rmtr_load_step(H, x, pf.default_params(rtol=1e-12))
+    assert st["converged"]
+    from tests.test_oracle_pins import _closed_form_profile
+    c = host(x)[2 * g.N:].reshape(g.n[1], g.n[0])
+    right, _ = _closed_form_profile(g.n[0] - 1 - 17, g.h, Ho.prm.ls)
+    left, _ = _closed_form_profile(16, g.h, Ho.prm.ls)
+    for row in c:
+        np.testing.assert_allclose(row[17:], right, rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(row[:17][::-1], left, rtol=1e-8, atol=1e-12)
+
+
+@pytest.mark.parametrize("model", [O.FIRST_ORDER, O.GALERKIN])
+def test_3d_small_load_steps_match_oracle(pf, model):
+    """Two load steps on a 3-level 3D hierarchy with discs (irreversibility
+    carries over between steps)."""
+    import torch
+    H, Ho = pair(3, (3, 3, 3), 3, 0.5, nu=0.25, p=0.0)
+    g = Ho.fine
+    rows = np.array([[0.5, 0.45, 0.52, 0.0, 0.6, 0.8, 0.3], [0.3, 0.6, 0.4, 1.0, 0.0, 0.0, 0.2]])
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    pf.fractures_set(H, pf.PF_DISC3D, rows, g.h, x)
+    xo = np.zeros(4 * g.N)
+    xo[3 * g.N:] = O.rasterize(g, O.DISC3D, rows, g.h)
+    assert np.array_equal(host(x), xo)
+    tr = O.TRParams(coarse_model=model, rtol=1e-13)
+    for p in (0.5, 1.0):
+        pf.pressure_set(H, p)
+        st = pf.rmtr_load_step(H, x, pf.default_params(coarse_model=model, rtol=1e-13))
+        ro = O.rmtr_load_step(Ho, xo, tr, p=p)
+        xo = ro.x
+        assert st["converged"] and ro.converged
+        _compare_fields(host(x), xo, 3, g.N)
+
+
+@pytest.mark.slow
+def test_3d_workload_load_step_properties(pf):
+    """One load step of the 129^3 four-level workload with 20 discs
+    (p = 5e-4): convergence, bounds, clamped boundary, energy decrease, and the
+    projected gradient re-evaluated by the oracle."""
+    import torch
+    H, Ho = pair(3, (17, 17, 17), 4, 1 / 16, nu=0.25, p=5e-4)
+    g = Ho.fine
+    rows = PI.disc_network_3d(PI.SEED_3D_PLAIN, 20)
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    pf.fractures_set(H, pf.PF_DISC3D, rows, g.h, x)
+    c0 = host(x)[3 * g.N:].copy()
+    e0 = pf.energy(H, 3, x)
+    st = pf.rmtr_load_step(H, x, pf.default_params())
+    assert st["converged"] == 1
+    xg = host(x)
+    assert st["energy"] < e0
+    c = xg[3 * g.N:]
+    assert np.all(c >= c0) and np.all(c <= 1.0)
+    bnd = g.boundary_nodes()
+    for f in range(3):
+        assert np.all(xg[f * g.N:(f + 1) * g.N][bnd] == 0.0)
+    # oracle re-check of first-order criticality at the returned point
+    Ho.c_prev = c0
+    lb, ub = Ho.fine_bounds()
+    gr = O.gradient(g, Ho.prm, xg)
+    pg = O.projected_gradient_norm(xg, gr, lb, ub)
+    assert pg <= 1e-9 * st["pg0"]
+    assert abs(O.energy(g, Ho.prm, xg) - st["energy"]) <= ENERGY_TOL * abs(st["energy"])
+
+
+def test_mixed_precision_reaches_fp64_energy(pf):
+    H, Ho, x, _ = _sneddon_setup(pf, O.FIRST_ORDER)
+    x2 = x.clone()
+    s64 = pf.rmtr_load_step(H, x, pf.default_params(rtol=1e-12))
+    s32 = pf.rmtr_load_step(H, x2, pf.default_params(rtol=1e-12, precision=pf.PF_FP32))
+    assert s32["converged"]
+    assert abs(s32["energy"] - s64["energy"]) <= 1e-8 * abs(s64["energy"])
