@@ -59,7 +59,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="also time the same K load steps in plain FP64")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="set up the workload state, launch the element kernels and exit")
+    ap.add_argument("--coarse-n", type=int, default=17,
+                    help="coarsest nodes per axis (17 = the 129^3 workload)")
     ap.add_argument("--coarse-model", choices=["first_order", "galerkin"], default="first_order")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -176,7 +182,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {k: WORKLOAD[k] for k in ("workload", "n_coarse", "levels", "fractures")},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                          "sample": ("one FP64 numpy oracle pass each of hessvec, gradient and energy "
                                     "difference on the full 129^3 state per step, scaled by the CUDA path's "
                                     f"finest-equivalent passes per load step {REF_WORK_MODEL}"),
@@ -188,6 +194,39 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+def kernels_only(pf, B, H, x, W):
+    """One launch each of the FP64 hessvec, FP32 hessvec and FP64 gradient
+    on the workload state (the launches an ncu capture takes), then their
+    event-timed averages."""
+    import torch
+    pf.pressure_set(H, W["dp"])
+    level = W["levels"] - 1
+    ndof = H.ndof()
+    v = torch.from_numpy(PI.random_direction(77, ndof, 1e-3)).cuda()
+    out = torch.empty_like(v)
+    x32, v32 = x.float(), v.float()
+    o32 = torch.empty_like(v32)
+    pf.hessvec(H, level, x, v, out)
+    pf.hessvec(H, level, x32, v32, o32)
+    pf.gradient(H, level, x, out)
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in (("hessvec_fp64", lambda: pf.hessvec(H, level, x, v, out)),
+                     ("hessvec_fp32", lambda: pf.hessvec(H, level, x32, v32, o32)),
+                     ("gradient_fp64", lambda: pf.gradient(H, level, x, out))):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 10 * 1e-3
+        res[name] = {"us": t * 1e6, "gdofs": ndof / t / 1e9}
+    print(json.dumps({"kernels": res, "dofs": ndof, "workload": W["workload"]}))
+    return 0
+
+
 def run_ours(args):
     import torch
     rank, world, local = rank_info()
@@ -201,7 +240,11 @@ def run_ours(args):
     import paper_2007_12908_gb300 as pf
     from paper_2007_12908_gb300 import _binding as B
 
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if args.coarse_n != 17:
+        W["n_coarse"] = [args.coarse_n] * 3
+        W["h_coarse"] = 1.0 / (args.coarse_n - 1)
+        W["workload"] = f"3d_{8 * (args.coarse_n - 1) + 1}^3_q1_4level_20discs_ramp"
     prm = pf.default_params(
         precision=pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64,
         coarse_model=pf.PF_GALERKIN if args.coarse_model == "galerkin" else pf.PF_FIRST_ORDER)
@@ -213,6 +256,9 @@ def run_ours(args):
     rows = PI.disc_network_3d(W["seed"], W["fractures"])
     pf.fractures_set(H, pf.PF_DISC3D, rows, g_h, x)
     stream = torch.cuda.current_stream()
+
+    if args.kernels_only:
+        return kernels_only(pf, B, H, x, W)
 
     def load_step(t, xx):
         pf.pressure_set(H, W["dp"] * t)
@@ -301,12 +347,33 @@ def run_ours(args):
         e2e = {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
                "d2h_bytes_per_step": 8 * ndof}
 
+    fp64_cmp = None
+    if args.compare_fp64 and args.precision != "fp64":
+        p64 = pf.default_params(precision=pf.PF_FP64, coarse_model=prm.coarse_model)
+        x64 = x_after_warmup.clone()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s64 = []
+        for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+            pf.pressure_set(H, W["dp"] * t)
+            s64.append(pf.rmtr_load_step(H, x64, p64, check=False))
+        b.record(stream)
+        torch.cuda.synchronize()
+        e64 = [s["energy"] for s in s64]
+        emx = [s["energy"] for s in stats]
+        fp64_cmp = {"value": a.elapsed_time(b) / args.steps / 1e3, "unit": UNIT,
+                    "speedup_of_headline": a.elapsed_time(b) / args.steps / ms,
+                    "energy_rel_diff": max(abs(p - q) / abs(q) for p, q in zip(emx, e64)),
+                    "cycles": [s["cycles"] for s in s64]}
+
     work = {k: statistics.mean(s[k] for s in stats) for k in ("fe_hessvec", "fe_gradient", "fe_energy")}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pass_s, _ = oracle_pass_seconds(budget_s=10.0)
         cpu = {"value": oracle_seconds_per_load_step(pass_s, work), "unit": UNIT,
-               "cores": 1, "kind": "oracle",
+               "cores": cpu_cores(), "kind": "oracle",
                "sample": ("FP64 numpy oracle: one hessvec, gradient and energy-difference pass on the "
                           "full 129^3 state (best of repeats within 10 s), scaled by this run's "
                           "finest-equivalent passes per load step"),
@@ -331,6 +398,7 @@ def run_ours(args):
             "roofline_other": roof32 if roofline is roof64 else roof64,
             "hessvec_gdofs": {"fp64": ndof / t64 / 1e9, "fp32": ndof / t32 / 1e9},
             "gradient_fp64_us": t_grad * 1e6,
+            "fp64_plain": fp64_cmp,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches,
