@@ -184,6 +184,31 @@ pf_status pf_rmtr_load_step_host(pf_hierarchy* h, double* x_host, const pf_rmtr_
 /* Copies the finest-level c_prev (FP64, N values) to c_prev_dev. */
 pf_status pf_get_c_prev(pf_hierarchy* h, double* c_prev_dev);
 
+/* Energy of pf_energy for callers that cannot allocate device memory.
+ * The paper has no counterpart: this exists for callers such as plug-ins
+ * that run inside a host application which owns the whole device memory
+ * budget, or real-time loops where cudaMalloc/cudaFree are not allowed
+ * because they can block and synchronise the device.  The call takes the
+ * grid and material directly (no pf_hierarchy, whose creation allocates),
+ * allocates nothing and frees nothing.
+ *   dim, n[0..dim): nodes per axis; h: spacing; E, nu, Gc, ls, k_res, p: as
+ *   in pf_mesh_desc / pf_pressure_set (ls is l_s itself); x_dev: (dim+1)
+ *   planes of prod(n) values in precision prec; E_dev: one device double
+ *   that receives the FP64 energy, written on `stream` (cudaStream_t, NULL =
+ *   legacy stream); the call does not synchronise.
+ * Scratch: a fixed 512 KiB + 256 B array in the library's device memory,
+ * loaded on every device that uses the library and held until the process
+ * exits.  It holds 65,536 block partials, so grids of more than 16,777,216
+ * elements are rejected with PF_EINVAL (use pf_energy for those).
+ * The first call on a device looks up that array's device address (with
+ * the device current), so make the first call on each device before any
+ * stream capture.  Every call shares the one array and clears its counter
+ * on entry; calls whose kernels overlap on the GPU (two streams, two host
+ * threads) race on it and must be serialised by the caller. */
+pf_status pf_energy_noalloc(int dim, const int n[3], double h, double E, double nu, double Gc,
+                            double ls, double k_res, double p, const void* x_dev, int prec,
+                            double* E_dev, void* stream);
+
 /* Measurement helper with no counterpart in the paper: runs a kernel of
  * independent fused multiply-adds in precision prec on the legacy stream
  * and writes the achieved rate (flop/s, an FMA counted as 2) to *flops_host.

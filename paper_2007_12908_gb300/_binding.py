@@ -27,7 +27,7 @@ EXPORTS = [
     "pf_mesh_hierarchy_destroy", "pf_level_info", "pf_fractures_set", "pf_pressure_set",
     "pf_energy", "pf_energy_diff", "pf_gradient", "pf_hessvec", "pf_prolong", "pf_restrict",
     "pf_project", "pf_coarse_bounds", "pf_rmtr_load_step", "pf_rmtr_load_step_host",
-    "pf_get_c_prev", "pf_probe_fma",
+    "pf_get_c_prev", "pf_probe_fma", "pf_energy_noalloc",
 ]
 
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_rmtr_load_step_host": (i, [vp, vp, C.POINTER(RmtrParams), C.POINTER(RmtrStats)]),
         "pf_get_c_prev": (i, [vp, vp]),
         "pf_probe_fma": (i, [i, C.POINTER(d)]),
+        "pf_energy_noalloc": (i, [i, C.POINTER(C.c_int), d, d, d, d, d, d, d, vp, i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -316,3 +317,15 @@ def probe_fma(prec: int) -> float:
     out = C.c_double()
     _check(lib().pf_probe_fma(prec, C.byref(out)))
     return out.value
+
+
+def energy_noalloc(dim, n, h, E, nu, Gc, ls, k_res, p, x, out, stream=None):
+    """pf_energy_noalloc: the energy written to the one-element float64 CUDA
+    tensor `out` on `stream`, with no device allocation inside the call."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    nn = (C.c_int * 3)(*[int(v) for v in list(n) + [1] * (3 - len(n))])
+    _check(lib().pf_energy_noalloc(dim, nn, h, E, nu, Gc, ls, k_res, p, _dev(x), _prec(x),
+                                   _dev(out, 1, torch.float64), C.c_void_p(stream.cuda_stream)))
+    return out

@@ -34,6 +34,11 @@ Mat<double> make_mat(const Geom& g, double E, double nu, double Gc, double ls, d
 // prec (0 = double, 1 = float).  Reductions write FP64 results to out_dev.
 cudaError_t elem_energy(const Geom& g, const Mat<double>& m, const void* x, int prec,
                         const Scratch& s, double* out_dev, cudaStream_t st);
+// The energy kernel launched with nblocks blocks of 256 threads, block
+// partials at partials[0 .. nblocks) (needs nblocks <= partials' length).
+cudaError_t elem_energy_blocks(const Geom& g, const Mat<double>& m, const void* x, int prec,
+                               double* partials, unsigned* counter, int nblocks, double* out,
+                               cudaStream_t st);
 cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x, const void* sv,
                              int prec, const Scratch& s, double* out_dev, cudaStream_t st);
 cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, void* y, int prec,

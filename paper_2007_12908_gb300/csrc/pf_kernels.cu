@@ -255,6 +255,26 @@ cudaError_t elem_energy(const Geom& g, const Mat<double>& m, const void* x, int 
               : launch_energy<2, double>(g, m, x, s, out, st);
 }
 
+// The energy kernel with one element per thread (nblocks = ceil(NE / 256))
+// and caller-provided partial sums (one per block) and counter.
+template <int D, class T>
+static cudaError_t launch_energy_blocks(const Geom& g, const Mat<double>& m, const void* x,
+                                        double* partials, unsigned* counter, int nblocks,
+                                        double* out, cudaStream_t st) {
+  k_energy<D, T><<<nblocks, 256, 0, st>>>(g, m, static_cast<const T*>(x), partials, counter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t elem_energy_blocks(const Geom& g, const Mat<double>& m, const void* x, int prec,
+                               double* partials, unsigned* counter, int nblocks, double* out,
+                               cudaStream_t st) {
+  if (g.dim == 3)
+    return prec ? launch_energy_blocks<3, float>(g, m, x, partials, counter, nblocks, out, st)
+                : launch_energy_blocks<3, double>(g, m, x, partials, counter, nblocks, out, st);
+  return prec ? launch_energy_blocks<2, float>(g, m, x, partials, counter, nblocks, out, st)
+              : launch_energy_blocks<2, double>(g, m, x, partials, counter, nblocks, out, st);
+}
+
 template <int D, class T>
 static cudaError_t launch_energy_diff(const Geom& g, const Mat<double>& m, const void* x,
                                       const void* sv, const Scratch& s, double* out,
