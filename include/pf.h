@@ -55,7 +55,7 @@ typedef struct pf_hierarchy pf_hierarchy;
 typedef struct {
   int dim;            /* 2 or 3                                              */
   int n_coarse[3];    /* nodes per axis on the coarsest level (>= 2)         */
-  int n_levels;       /* >= 1; level l has (n_coarse-1) 2^l + 1 nodes/axis   */
+  int n_levels;       /* 1 .. 8; level l has (n_coarse-1) 2^l + 1 nodes/axis */
   double h_coarse;    /* node spacing of the coarsest level                  */
   double E, nu;       /* Young's modulus, Poisson ratio (Lame via plane strain
                          in 2D)                                              */
@@ -84,6 +84,10 @@ typedef struct {
   int coarse_model;      /* PF_GALERKIN or PF_FIRST_ORDER                    */
   int precision;         /* PF_FP64, or PF_FP32 = mixed: FP32 hessvec and CG,
                             FP64 energy, gradient, rho, radius, norms        */
+  int precondition;      /* 1: Jacobi (Hessian-diagonal) preconditioned CG (1) */
+  double level_rtol;     /* a non-finest level stops its TR steps once its
+                            projected gradient fell by this factor (1e-3;
+                            0 = always take the full count)                  */
 } pf_rmtr_params;
 
 typedef struct {
@@ -102,6 +106,9 @@ typedef struct {
                             (a level-l call counts N_l / N_finest)           */
   double fe_gradient;    /* gradients, finest-level units                    */
   double fe_energy;      /* energy / energy-difference passes, finest units  */
+  long long cg_level[8]; /* CG iterations per level (index = level, <= 8)    */
+  long long tr_level[8]; /* TR iterations per level                          */
+  long long rej_level[8];/* rejected TR steps per level                      */
 } pf_rmtr_stats;
 
 /* Fills p with the defaults listed beside each field above. */

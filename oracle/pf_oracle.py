@@ -376,6 +376,31 @@ def hessvec(grid: Grid, prm: Params, x, v, elems=None) -> np.ndarray:
     return out
 
 
+def hess_diag(grid: Grid, prm: Params, x, elems=None) -> np.ndarray:
+    """Diagonal of the Hessian of E at x (the Jacobi preconditioner of the
+    subproblem CG): for a u_i dof of corner a,
+    g [lam (d_i phi_a)^2 + mu (|grad phi_a|^2 + (d_i phi_a)^2)]; for a c dof,
+    (g''(psi + p div u) + Gc/ls) phi_a^2 + Gc ls |grad phi_a|^2."""
+    U, C = _split(grid, x)
+    out = np.zeros_like(x)
+    lam, mu = lame(prm)
+    d = grid.dim
+    dn2 = grid.dNq ** 2  # (Q, A, d)
+    gn2 = np.sum(dn2, axis=-1)  # (Q, A)
+    for ch in _chunks(grid, elems):
+        conn = grid.element_connectivity(ch)
+        G, c, _ = _qp_state(grid, conn, U, C)
+        _, tr, psi, _ = _strain_terms(prm, G)
+        g, _, ddg = _degradation(prm, c)
+        cu = np.stack([grid.wq * np.einsum("eq,qa->ea", g, lam * dn2[:, :, i] + mu * (gn2 + dn2[:, :, i]),
+                                           optimize=True) for i in range(d)])
+        m = ddg * (psi + prm.p * tr) + prm.Gc / prm.ls
+        cc = grid.wq * (np.einsum("eq,qa->ea", m, grid.Nq ** 2, optimize=True)
+                        + prm.Gc * prm.ls * np.sum(gn2, axis=0)[None, :])
+        _scatter(grid, conn, cu, cc, out)
+    return out
+
+
 def dense_hessian(grid: Grid, prm: Params, x) -> np.ndarray:
     """Independent assembly of the full Hessian from element matrices built
     basis pair by basis pair (loops; tiny meshes only)."""
@@ -522,6 +547,9 @@ class TRParams:
     rtol: float = 1e-10
     atol: float = 0.0
     coarse_model: int = FIRST_ORDER
+    precondition: bool = True   # Jacobi-preconditioned subproblem CG
+    level_rtol: float = 1e-3    # non-finest levels stop their TR loop once the
+                                # level's projected gradient fell by this factor
 
 
 def proj_box(s, lo, hi):
@@ -544,7 +572,7 @@ def _model(g, s, Hs):
     return float(g @ s) + 0.5 * float(s @ Hs)
 
 
-def solve_subproblem(g, Hv, lo, hi, delta, cg_max, tr: TRParams, stats=None):
+def solve_subproblem(g, Hv, lo, hi, delta, cg_max, tr: TRParams, stats=None, minv=None):
     """Approximate minimiser of m(s) = g.s + 1/2 s.Hs over lo <= s <= hi
     (eq. model_qp: the TR box intersected with the level's feasible set),
     reaching the sufficient decrease the paper asks of its QP solvers:
@@ -558,6 +586,8 @@ def solve_subproblem(g, Hv, lo, hi, delta, cg_max, tr: TRParams, stats=None):
        s <- P(s + beta d), beta = 1, 1/2, ..., accepted on
        m(new) <= m(s) + c1 grad m(s).(new - s).  Repeated while CG was cut
        by the box and iterations remain.
+    minv: inverse diagonal preconditioner (0 where the diagonal is not
+    positive); None runs plain CG.
     """
     def H(v):
         if stats is not None:
@@ -601,10 +631,12 @@ def solve_subproblem(g, Hv, lo, hi, delta, cg_max, tr: TRParams, stats=None):
             tol = min(0.1, math.sqrt(r0)) * r0
         if math.sqrt(rr) <= tol or rr == 0.0:
             break
-        # CG on the free set from w = 0
+        # (preconditioned) CG on the free set from w = 0
         w = np.zeros_like(g)
         Hw = np.zeros_like(g)
-        p = r.copy()
+        z = r * minv if minv is not None else r
+        rz = float(r @ z)
+        p = z.copy()
         leave = False
         while used < cg_max:
             q = np.where(free, H(p), 0.0)
@@ -619,19 +651,21 @@ def solve_subproblem(g, Hv, lo, hi, delta, cg_max, tr: TRParams, stats=None):
                     Hw = Hw + amax * q
                 leave = True
                 break
-            alpha = rr / kappa
+            alpha = rz / kappa
             w = w + alpha * p
             Hw = Hw + alpha * q
             r = r - alpha * q
             rr_new = float(r @ r)
+            z = r * minv if minv is not None else r
+            rz_new = float(r @ z)
             sw = s + w
             if np.any(free & ((sw < lo) | (sw > hi))):
                 leave = True
                 break
             if math.sqrt(rr_new) <= tol:
                 break
-            p = r + (rr_new / rr) * p
-            rr = rr_new
+            p = z + (rz_new / rz) * p
+            rz = rz_new
         if not leave:
             s = s + w
             Hs = Hs + Hw
@@ -732,6 +766,16 @@ class LevelModel:
         T = self.H.transfers[self.level]
         return T.restrict(self.finer.Hlag(T.prolong(v)))
 
+    def minv(self):
+        """Inverse of the positive part of a Hessian diagonal (Jacobi): the
+        lagged Hessian's own diagonal on the finest level and for
+        FIRST_ORDER; the diagonal of Hess f~(x0) for GALERKIN levels."""
+        if not hasattr(self, "_minv"):
+            grid = self.H.grids[self.level]
+            dd = hess_diag(grid, self.H.prm, self.x_lag)
+            self._minv = np.where(dd > 0.0, 1.0 / np.where(dd > 0.0, dd, 1.0), 0.0)
+        return self._minv
+
     def dH(self, v):
         if self.finest or self.kind == FIRST_ORDER:
             return np.zeros_like(v)
@@ -772,22 +816,36 @@ def convergence_control(rho, x, s, delta, lb, ub, tr: TRParams):
 
 def nonlinear_solve(model: LevelModel, x0, lb, ub, delta0, iters, cg_max, tr: TRParams, stats):
     """Algorithm 2: `iters` trust-region iterations on h with the lagged
-    model Hessian, each solving eq. (model_qp) and testing eq. (rho_tr)."""
+    model Hessian, each solving eq. (model_qp) and testing eq. (rho_tr).
+    A non-finest level also stops once its projected gradient has fallen
+    by level_rtol (when level_rtol > 0)."""
     x = x0.copy()
     delta = delta0
+    minv = model.minv() if tr.precondition else None
+    chi0 = None
     for _ in range(iters):
         g = model.grad(x)
+        if tr.level_rtol > 0.0 and not model.finest:
+            chi = projected_gradient_norm(x, g, lb, ub)
+            if chi0 is None:
+                chi0 = chi
+            elif chi <= tr.level_rtol * chi0:
+                break
         lo = np.maximum(lb - x, -delta)
         hi = np.minimum(ub - x, delta)
-        s = solve_subproblem(g, model.Hlag, lo, hi, delta, cg_max, tr, stats)
+        s = solve_subproblem(g, model.Hlag, lo, hi, delta, cg_max, tr, stats, minv)
         pred = -(float(g @ s) + 0.5 * float(s @ model.Hlag(s)))
         stats["hessvecs"] += 1
         stats["tr_its"] += 1
+        lv = stats.setdefault("tr_level", {})
+        lv[model.level] = lv.get(model.level, 0) + 1
         if not pred > 0.0:
             break
         rho = -model.diff(x, s) / pred
         if rho <= tr.eta1:
             stats["tr_rejected"] += 1
+            rj = stats.setdefault("rej_level", {})
+            rj[model.level] = rj.get(model.level, 0) + 1
         x, delta = convergence_control(rho, x, s, delta, lb, ub, tr)
     return x, delta
 

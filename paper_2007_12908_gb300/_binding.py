@@ -45,7 +45,8 @@ class RmtrParams(C.Structure):
                 ("cg_fine", C.c_int), ("cg_smooth", C.c_int), ("cg_coarse", C.c_int),
                 ("cauchy_backtracks", C.c_int), ("cauchy_c", C.c_double),
                 ("max_cycles", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
-                ("coarse_model", C.c_int), ("precision", C.c_int)]
+                ("coarse_model", C.c_int), ("precision", C.c_int),
+                ("precondition", C.c_int), ("level_rtol", C.c_double)]
 
 
 class RmtrStats(C.Structure):
@@ -54,10 +55,16 @@ class RmtrStats(C.Structure):
                 ("cg", C.c_longlong), ("tr_its", C.c_longlong), ("tr_rejected", C.c_longlong),
                 ("coarse_rejected", C.c_longlong), ("seconds", C.c_double),
                 ("launches", C.c_longlong), ("fe_hessvec", C.c_double),
-                ("fe_gradient", C.c_double), ("fe_energy", C.c_double)]
+                ("fe_gradient", C.c_double), ("fe_energy", C.c_double),
+                ("cg_level", C.c_longlong * 8), ("tr_level", C.c_longlong * 8),
+                ("rej_level", C.c_longlong * 8)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if k.endswith("_level") else v
+        return out
 
 
 class PfError(RuntimeError):

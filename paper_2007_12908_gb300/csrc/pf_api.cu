@@ -68,6 +68,8 @@ void pf_rmtr_params_default(pf_rmtr_params* p) {
   p->atol = 0.0;
   p->coarse_model = PF_FIRST_ORDER;
   p->precision = PF_FP64;
+  p->precondition = 1;
+  p->level_rtol = 1e-3;
 }
 
 const char* pf_last_error(void) { return g_last_error.c_str(); }
@@ -88,6 +90,7 @@ pf_status pf_mesh_hierarchy_destroy(pf_hierarchy* h) {
   else cudaDeviceSynchronize();
   for (void* p : h->allocations) cudaFree(p);
   if (h->h_res) cudaFreeHost(h->h_res);
+  if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
   delete h;
   return PF_OK;
 }
@@ -96,7 +99,7 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
   if (!d || !out) return bad("mesh_hierarchy_create: null argument");
   *out = nullptr;
   if (d->dim != 2 && d->dim != 3) return bad("mesh_hierarchy_create: dim must be 2 or 3");
-  if (d->n_levels < 1 || d->n_levels > 12) return bad("mesh_hierarchy_create: n_levels out of range");
+  if (d->n_levels < 1 || d->n_levels > 8) return bad("mesh_hierarchy_create: n_levels must be 1 .. 8");
   for (int k = 0; k < d->dim; ++k)
     if (d->n_coarse[k] < 2) return bad("mesh_hierarchy_create: n_coarse must be >= 2");
   if (!(d->h_coarse > 0) || !(d->E > 0) || !(d->Gc > 0) || !(d->ls_over_h > 0) ||
@@ -130,11 +133,13 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
   if ((rc = alloc(h, (void**)&h->scratch.partials, sizeof(double) * kMaxSlots * kMaxBlocks)) ||
       (rc = alloc(h, (void**)&h->scratch.counter, sizeof(unsigned))) ||
       (rc = alloc(h, (void**)&h->d_res, sizeof(double) * kMaxSlots)) ||
-      (rc = alloc(h, (void**)&h->c_prev, sizeof(double) * h->geo.back().N))) {
+      (rc = alloc(h, (void**)&h->c_prev, sizeof(double) * h->geo.back().N)) ||
+      (rc = alloc(h, (void**)&h->ctrl, sizeof(CgCtrl)))) {
     pf_mesh_hierarchy_destroy(h);
     return rc;
   }
-  if (cudaMallocHost((void**)&h->h_res, sizeof(double) * kMaxSlots) != cudaSuccess) {
+  if (cudaMallocHost((void**)&h->h_res, sizeof(double) * kMaxSlots) != cudaSuccess ||
+      cudaMallocHost((void**)&h->h_ctrl, sizeof(CgCtrl)) != cudaSuccess) {
     pf_mesh_hierarchy_destroy(h);
     set_error("cudaMallocHost failed");
     return PF_ENOMEM;
@@ -148,13 +153,13 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
     const size_t bytes = sizeof(double) * B.n;
     double** vecs[] = {&B.x, &B.lb, &B.ub, &B.x0, &B.xlag, &B.dg, &B.g, &B.s, &B.lo, &B.hi,
                        &B.Hs, &B.r, &B.p, &B.q, &B.w, &B.Hw, &B.t1, &B.t2, &B.t3, &B.gin,
-                       &B.gout, &B.dh};
+                       &B.gout, &B.dh, &B.minv};
     for (double** v : vecs)
       if ((rc = alloc(h, (void**)v, bytes))) {
         pf_mesh_hierarchy_destroy(h);
         return rc;
       }
-    float** f32[] = {&B.xlag32, &B.v32, &B.hv32};
+    float** f32[] = {&B.xlag32};
     for (float** v : f32)
       if ((rc = alloc(h, (void**)v, sizeof(float) * B.n))) {
         pf_mesh_hierarchy_destroy(h);
@@ -327,7 +332,8 @@ static pf_status check_params(const pf_rmtr_params& P) {
       P.cauchy_backtracks < 0 || !(P.cauchy_c > 0 && P.cauchy_c < 1) || P.max_cycles < 0 ||
       !(P.rtol >= 0) || !(P.atol >= 0) ||
       (P.coarse_model != PF_GALERKIN && P.coarse_model != PF_FIRST_ORDER) ||
-      (P.precision != PF_FP64 && P.precision != PF_FP32))
+      (P.precision != PF_FP64 && P.precision != PF_FP32) ||
+      (P.precondition != 0 && P.precondition != 1) || !(P.level_rtol >= 0 && P.level_rtol < 1))
     return bad("rmtr_load_step: invalid parameters");
   return PF_OK;
 }

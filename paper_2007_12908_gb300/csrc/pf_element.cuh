@@ -414,4 +414,65 @@ __device__ __forceinline__ void elem_hessvec(const T (*xe)[1 << D], const T (*ve
   test<D, T>(s0, sc, out[D]);
 }
 
+// Diagonal of the Hessian (Jacobi preconditioner):
+//   u_i dof of corner a: sum_q w g [lam (d_i phi_a)^2 + mu (|grad phi_a|^2 + (d_i phi_a)^2)]
+//   c dof:              sum_q w [(g''(psi + p tr) + Gc/ls) phi_a^2 + Gc ls |grad phi_a|^2]
+template <int D, class T>
+__device__ __forceinline__ void elem_hessdiag(const T (*xe)[1 << D], const Mat<T>& m,
+                                              T (*out)[1 << D]) {
+  constexpr int NQ = 1 << D;
+  T gu[D][D][NQ], cv[NQ], gdummy[D][NQ], dummy[NQ];
+#pragma unroll
+  for (int i = 0; i < D; ++i) interp<D, T>(xe[i], dummy, gu[i]);
+  interp<D, T>(xe[D], cv, gdummy);
+  T gq[NQ], mq[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T G[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) G[i][k] = gu[i][k][q] * m.inv_h;
+    Strain<D, T> e;
+    e.set(G);
+    const T psi = T(0.5) * m.lam * e.tr * e.tr + m.mu * e.ddot(e);
+    const T omk = T(1) - m.k, omc = T(1) - cv[q];
+    gq[q] = m.w * (omk * omc * omc + m.k);
+    mq[q] = m.w * (T(2) * omk * (psi + m.p * e.tr) + m.Gc / m.ls);
+  }
+  const T h2 = m.inv_h * m.inv_h;
+#pragma unroll
+  for (int a = 0; a < NQ; ++a) {
+    T du[D], dc = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) du[i] = T(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      // 1D factors: N(q, a) = XI1 if q == a along the axis, else XI0
+      T n1[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) n1[k] = (((q >> k) & 1) == ((a >> k) & 1)) ? T(PF_XI1) : T(PF_XI0);
+      T phi = T(1);
+#pragma unroll
+      for (int k = 0; k < D; ++k) phi *= n1[k];
+      T d2[D], g2 = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        T t = T(1);
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+          if (j != k) t *= n1[j] * n1[j];
+        d2[k] = t * h2;
+        g2 += d2[k];
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) du[i] += gq[q] * (m.lam * d2[i] + m.mu * (g2 + d2[i]));
+      dc += mq[q] * phi * phi + m.w * m.Gc * m.ls * g2;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) out[i][a] = du[i];
+    out[D][a] = dc;
+  }
+}
+
 }  // namespace pf

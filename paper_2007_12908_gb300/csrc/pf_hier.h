@@ -19,8 +19,26 @@ struct LevelBuf {
   double *w = nullptr, *Hw = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
   double *gin = nullptr, *gout = nullptr;  // Galerkin recursion through this level
   double *dh = nullptr;                    // dH scratch
-  float *xlag32 = nullptr, *v32 = nullptr, *hv32 = nullptr;  // mixed-precision hessvec
+  double *minv = nullptr;                  // Jacobi preconditioner of the lagged Hessian
+  float* xlag32 = nullptr;  // FP32 copy of x_lag (mixed precision)
 };
+
+// Device-resident control block of one projected CG run: the scalars each
+// iteration needs and the reason it stopped, updated by the last block of
+// each reduction so the host only polls it.
+struct CgCtrl {
+  double rr;      // r.r of the current residual
+  double rz;      // r.M^-1 r (preconditioned CG)
+  double tol;     // forcing tolerance on ||r||
+  double alpha;   // step of the current iteration
+  double beta;    // direction update of the current iteration
+  double kappa;   // p.Hp of the current iteration
+  int done;       // 1 once the run has stopped; later launches are no-ops
+  int state;      // why it stopped (CG_*)
+  int used;       // Hessian-vector products spent by the CG loop
+  int cg_max;     // budget
+};
+enum { CG_RUNNING = 0, CG_NEGCURV = 1, CG_LEAVE = 2, CG_CONV = 3, CG_BUDGET = 4 };
 
 void set_error(const std::string& msg);
 
@@ -36,6 +54,8 @@ struct pf_hierarchy {
   double* d_res = nullptr;  // device result slots
   double* h_res = nullptr;  // pinned host mirror
   double* c_prev = nullptr; // finest N values
+  pf::CgCtrl* ctrl = nullptr;    // device CG control block
+  pf::CgCtrl* h_ctrl = nullptr;  // pinned host mirror
   bool have_fractures = false;
   std::vector<pf::LevelBuf> lv;
   std::vector<void*> allocations;

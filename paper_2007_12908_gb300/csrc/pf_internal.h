@@ -44,7 +44,15 @@ cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x,
 cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, void* y, int prec,
                           cudaStream_t st);
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
-                         void* y, int prec, cudaStream_t st);
+                         void* y, int prec, cudaStream_t st, const int* skip = nullptr);
+// Diagonal of the Hessian at x (precision prec), written as FP64.
+cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, int prec,
+                          double* y, cudaStream_t st);
+// FP32 Hessian at an FP32 copy of x applied to an FP64 v, written as FP64
+// (the mixed-precision solver's operator; conversions happen in registers).
+cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float* x32,
+                               const double* v, double* y, cudaStream_t st,
+                               const int* skip = nullptr);
 
 // Fracture band rasterisation into the c plane (FP64) of x and c_prev.
 // rows: device array of precomputed shape rows (see pf_kernels.cu).
@@ -53,9 +61,9 @@ cudaError_t rasterize(const Geom& g, int kind, int n, const double* rows_dev, do
 
 // Transfers between a coarse grid gc and its 2:1 refinement gf, nf planes.
 cudaError_t xfer_prolong(const Geom& gc, const Geom& gf, int nf, const void* in, void* out,
-                         int prec, cudaStream_t st);
+                         int prec, cudaStream_t st, const int* skip = nullptr);
 cudaError_t xfer_restrict(const Geom& gc, const Geom& gf, int nf, const void* in, void* out,
-                          int prec, bool normalise, cudaStream_t st);
+                          int prec, bool normalise, cudaStream_t st, const int* skip = nullptr);
 cudaError_t xfer_bounds(const Geom& gc, const Geom& gf, int nf, const double* lo_f,
                         const double* hi_f, double* lo_c, double* hi_c, cudaStream_t st);
 

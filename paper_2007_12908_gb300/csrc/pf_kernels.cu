@@ -150,19 +150,23 @@ struct Tile<2> {
   static constexpr int X = 32, Y = 8, Z = 1, THREADS = 128;
 };
 
-enum { OP_GRAD = 0, OP_HESS = 1 };
+enum { OP_GRAD = 0, OP_HESS = 1, OP_DIAG = 2 };
 
-template <int D, class T, int OP>
+// TC: compute precision (and that of x); TIO: precision of v and y.
+// skip: when non-null and *skip != 0 the launch does nothing (the solver's
+// device-side CG stops this way without a host round trip).
+template <int D, class TC, class TIO, int OP>
 __global__ void __launch_bounds__(Tile<D>::THREADS)
-    k_elem_scatter(Geom g, Mat<T> m, const T* __restrict__ x, const T* __restrict__ v,
-                   T* __restrict__ y) {
+    k_elem_scatter(Geom g, Mat<TC> m, const TC* __restrict__ x, const TIO* __restrict__ v,
+                   TIO* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   constexpr int F = D + 1, NC = 1 << D;
   constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
   constexpr int EX = TX + 1, EY = TY + 1, EZ = D == 3 ? TZ + 1 : 1;
   constexpr int NEL = EX * EY * EZ, NOWN = TX * TY * TZ, NT = Tile<D>::THREADS;
-  __shared__ T acc[F][NOWN];
+  __shared__ TC acc[F][NOWN];
   const int ox = blockIdx.x * TX, oy = blockIdx.y * TY, oz = D == 3 ? blockIdx.z * TZ : 0;
-  for (int i = threadIdx.x; i < F * NOWN; i += NT) (&acc[0][0])[i] = T(0);
+  for (int i = threadIdx.x; i < F * NOWN; i += NT) (&acc[0][0])[i] = TC(0);
   __syncthreads();
   for (int base = 0; base < NEL; base += NT) {
     const int e = base + threadIdx.x;
@@ -170,16 +174,23 @@ __global__ void __launch_bounds__(Tile<D>::THREADS)
     const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     bool valid = e < NEL && gx >= 0 && gx < g.ne[0] && gy >= 0 && gy < g.ne[1];
     if constexpr (D == 3) valid = valid && gz >= 0 && gz < g.ne[2];
-    T out[F][NC];
+    TC out[F][NC];
     if (valid) {
-      T xe[F][NC];
-      gather<D, T>(g, x, gx, gy, gz, xe);
+      TC xe[F][NC];
+      gather<D, TC>(g, x, gx, gy, gz, xe);
       if constexpr (OP == OP_HESS) {
-        T ve[F][NC];
-        gather<D, T>(g, v, gx, gy, gz, ve);
-        elem_hessvec<D, T>(xe, ve, m, out);
+        TC ve[F][NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          const long long idx = corner_node<D>(g, gx, gy, gz, a);
+#pragma unroll
+          for (int f = 0; f < F; ++f) ve[f][a] = TC(v[f * g.N + idx]);
+        }
+        elem_hessvec<D, TC>(xe, ve, m, out);
+      } else if constexpr (OP == OP_DIAG) {
+        elem_hessdiag<D, TC>(xe, m, out);
       } else {
-        elem_gradient<D, T>(xe, m, out);
+        elem_gradient<D, TC>(xe, m, out);
       }
     }
 #pragma unroll
@@ -201,7 +212,7 @@ __global__ void __launch_bounds__(Tile<D>::THREADS)
     if (gx < g.n[0] && gy < g.n[1] && gz < g.n[2]) {
       const long long idx = gx + g.n[0] * (gy + (long long)g.n[1] * gz);
 #pragma unroll
-      for (int f = 0; f < F; ++f) y[f * g.N + idx] = acc[f][i];
+      for (int f = 0; f < F; ++f) y[f * g.N + idx] = TIO(acc[f][i]);
     }
   }
 }
@@ -212,30 +223,46 @@ static dim3 scatter_grid(const Geom& g) {
               D == 3 ? (g.n[2] + Tile<D>::Z - 1) / Tile<D>::Z : 1);
 }
 
-template <int D, class T, int OP>
+template <int D, class TC, class TIO, int OP>
 static cudaError_t launch_scatter(const Geom& g, const Mat<double>& m, const void* x,
-                                  const void* v, void* y, cudaStream_t st) {
-  k_elem_scatter<D, T, OP><<<scatter_grid<D>(g), Tile<D>::THREADS, 0, st>>>(
-      g, cast_mat<T>(m), static_cast<const T*>(x), static_cast<const T*>(v), static_cast<T*>(y));
+                                  const void* v, void* y, const int* skip, cudaStream_t st) {
+  k_elem_scatter<D, TC, TIO, OP><<<scatter_grid<D>(g), Tile<D>::THREADS, 0, st>>>(
+      g, cast_mat<TC>(m), static_cast<const TC*>(x), static_cast<const TIO*>(v),
+      static_cast<TIO*>(y), skip);
   return cudaGetLastError();
 }
 
 cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, void* y, int prec,
                           cudaStream_t st) {
   if (g.dim == 3)
-    return prec ? launch_scatter<3, float, OP_GRAD>(g, m, x, nullptr, y, st)
-                : launch_scatter<3, double, OP_GRAD>(g, m, x, nullptr, y, st);
-  return prec ? launch_scatter<2, float, OP_GRAD>(g, m, x, nullptr, y, st)
-              : launch_scatter<2, double, OP_GRAD>(g, m, x, nullptr, y, st);
+    return prec ? launch_scatter<3, float, float, OP_GRAD>(g, m, x, nullptr, y, nullptr, st)
+                : launch_scatter<3, double, double, OP_GRAD>(g, m, x, nullptr, y, nullptr, st);
+  return prec ? launch_scatter<2, float, float, OP_GRAD>(g, m, x, nullptr, y, nullptr, st)
+              : launch_scatter<2, double, double, OP_GRAD>(g, m, x, nullptr, y, nullptr, st);
 }
 
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
-                         void* y, int prec, cudaStream_t st) {
+                         void* y, int prec, cudaStream_t st, const int* skip) {
   if (g.dim == 3)
-    return prec ? launch_scatter<3, float, OP_HESS>(g, m, x, v, y, st)
-                : launch_scatter<3, double, OP_HESS>(g, m, x, v, y, st);
-  return prec ? launch_scatter<2, float, OP_HESS>(g, m, x, v, y, st)
-              : launch_scatter<2, double, OP_HESS>(g, m, x, v, y, st);
+    return prec ? launch_scatter<3, float, float, OP_HESS>(g, m, x, v, y, skip, st)
+                : launch_scatter<3, double, double, OP_HESS>(g, m, x, v, y, skip, st);
+  return prec ? launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st)
+              : launch_scatter<2, double, double, OP_HESS>(g, m, x, v, y, skip, st);
+}
+
+cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, int prec,
+                          double* y, cudaStream_t st) {
+  if (g.dim == 3)
+    return prec ? launch_scatter<3, float, double, OP_DIAG>(g, m, x, nullptr, y, nullptr, st)
+                : launch_scatter<3, double, double, OP_DIAG>(g, m, x, nullptr, y, nullptr, st);
+  return prec ? launch_scatter<2, float, double, OP_DIAG>(g, m, x, nullptr, y, nullptr, st)
+              : launch_scatter<2, double, double, OP_DIAG>(g, m, x, nullptr, y, nullptr, st);
+}
+
+cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float* x32,
+                               const double* v, double* y, cudaStream_t st, const int* skip) {
+  if (g.dim == 3) return launch_scatter<3, float, double, OP_HESS>(g, m, x32, v, y, skip, st);
+  return launch_scatter<2, float, double, OP_HESS>(g, m, x32, v, y, skip, st);
 }
 
 template <int D, class T>
@@ -346,7 +373,9 @@ cudaError_t rasterize(const Geom& g, int kind, int n, const double* rows_dev, do
 // Q1 prolongation: a fine node on an even index coincides with a coarse
 // node; on an odd index it averages its two coarse neighbours (per axis).
 template <class T>
-__global__ void k_prolong(Geom gc, Geom gf, int nf, const T* __restrict__ in, T* __restrict__ out) {
+__global__ void k_prolong(Geom gc, Geom gf, int nf, const T* __restrict__ in, T* __restrict__ out,
+                          const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const long long total = gf.N * nf;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -379,7 +408,8 @@ __global__ void k_prolong(Geom gc, Geom gf, int nf, const T* __restrict__ in, T*
 // With normalise, the sum is divided by the sum of the weights (P).
 template <class T>
 __global__ void k_restrict(Geom gc, Geom gf, int nf, const T* __restrict__ in,
-                           T* __restrict__ out, bool normalise) {
+                           T* __restrict__ out, bool normalise, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const long long total = gc.N * nf;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -456,22 +486,22 @@ static int grid_for(long long n) {
 }
 
 cudaError_t xfer_prolong(const Geom& gc, const Geom& gf, int nf, const void* in, void* out,
-                         int prec, cudaStream_t st) {
+                         int prec, cudaStream_t st, const int* skip) {
   const int nb = grid_for(gf.N * nf);
   if (prec)
-    k_prolong<float><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const float*>(in), static_cast<float*>(out));
+    k_prolong<float><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const float*>(in), static_cast<float*>(out), skip);
   else
-    k_prolong<double><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const double*>(in), static_cast<double*>(out));
+    k_prolong<double><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const double*>(in), static_cast<double*>(out), skip);
   return cudaGetLastError();
 }
 
 cudaError_t xfer_restrict(const Geom& gc, const Geom& gf, int nf, const void* in, void* out,
-                          int prec, bool normalise, cudaStream_t st) {
+                          int prec, bool normalise, cudaStream_t st, const int* skip) {
   const int nb = grid_for(gc.N * nf);
   if (prec)
-    k_restrict<float><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const float*>(in), static_cast<float*>(out), normalise);
+    k_restrict<float><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const float*>(in), static_cast<float*>(out), normalise, skip);
   else
-    k_restrict<double><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const double*>(in), static_cast<double*>(out), normalise);
+    k_restrict<double><<<nb, 256, 0, st>>>(gc, gf, nf, static_cast<const double*>(in), static_cast<double*>(out), normalise, skip);
   return cudaGetLastError();
 }
 

@@ -77,6 +77,39 @@ __device__ __forceinline__ void grid_finish(double (&v)[K], double* partials, un
   }
 }
 
+// As grid_finish, but the last block's thread 0 hands the combined values to
+// fin(acc) instead of storing them (device-side control logic).
+template <int K, class Op, class Fin>
+__device__ __forceinline__ void grid_finish_fn(double (&v)[K], double* partials, unsigned* counter,
+                                               Fin& fin) {
+  __shared__ bool last;
+  block_reduce<K, Op>(v);
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) partials[k * kMaxBlocks + blockIdx.x] = v[k];
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    last = (t == unsigned(nb - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    acc[k] = Op::id();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      acc[k] = Op::op(acc[k], __ldcg(partials + k * kMaxBlocks + b));
+  }
+  block_reduce<K, Op>(acc);
+  if (threadIdx.x == 0) {
+    fin(acc);
+    __threadfence();
+    *counter = 0u;
+  }
+}
+
 inline int reduce_grid(long long n, int threads = 256) {
   long long b = (n + threads - 1) / threads;
   if (b > kMaxBlocks) b = kMaxBlocks;

@@ -32,6 +32,46 @@ __global__ void k_map(long long n, F f) {
     f(i);
 }
 
+template <class F>
+__global__ void k_map_skip(long long n, F f, const int* __restrict__ skip) {
+  if (*skip) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    f(i);
+}
+
+// Reduction whose last block passes the combined values to fin() on the
+// device; a no-op launch when *skip is set.
+template <int K, class Op, class F, class Fin>
+__global__ void __launch_bounds__(256) k_red_fin(long long n, F f, Fin fin, double* partials,
+                                                 unsigned* counter, const int* __restrict__ skip) {
+  if (*skip) return;
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = Op::id();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v[K];
+    f(i, v);
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = Op::op(acc[k], v[k]);
+  }
+  grid_finish_fn<K, Op>(acc, partials, counter, fin);
+}
+
+__global__ void k_ctrl_start(CgCtrl* c, double rr, double rz, double tol, int used, int cg_max) {
+  c->rr = rr;
+  c->rz = rz;
+  c->tol = tol;
+  c->alpha = 0.0;
+  c->beta = 0.0;
+  c->kappa = 0.0;
+  c->done = 0;
+  c->state = CG_RUNNING;
+  c->used = used;
+  c->cg_max = cg_max;
+}
+
 template <int K, class Op, class F>
 __global__ void __launch_bounds__(256) k_red(long long n, F f, double* partials, unsigned* counter,
                                              double* out) {
@@ -80,6 +120,21 @@ struct Solver {
   void map(long long n, Fn f) {
     k_map<<<map_grid(n), 256, 0, st>>>(n, f);
     ck(cudaGetLastError(), "map");
+    S.launches += 1;
+  }
+
+  template <class Fn>
+  void map_skip(long long n, Fn f, const int* skip) {
+    k_map_skip<<<map_grid(n), 256, 0, st>>>(n, f, skip);
+    ck(cudaGetLastError(), "map_skip");
+    S.launches += 1;
+  }
+
+  template <int K, class Op, class Fn, class Fin>
+  void red_fin(long long n, Fn f, Fin fin, const int* skip) {
+    k_red_fin<K, Op><<<reduce_grid(n), 256, 0, st>>>(n, f, fin, H->scratch.partials,
+                                                      H->scratch.counter, skip);
+    ck(cudaGetLastError(), "red_fin");
     S.launches += 1;
   }
 
@@ -141,46 +196,62 @@ struct Solver {
     return e;
   }
 
-  // FP32 Hessian at the lagged point (mixed precision): v and out stay FP64.
-  void hessvec_lag32(int l, const double* v, double* out) {
-    LevelBuf& B = H->lv[l];
-    float* v32 = B.v32;
-    float* h32 = B.hv32;
-    map(B.n, [=] __device__(long long i) { v32[i] = float(v[i]); });
-    ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, v32, h32, 1, st), "hessvec32");
-    S.hessvecs += 1;
-    S.fe_hessvec += frac(l);
-    S.launches += 1;
-    map(B.n, [=] __device__(long long i) { out[i] = double(h32[i]); });
-  }
-
   void set_lag(int l, const double* x) {
     LevelBuf& B = H->lv[l];
     copy(B.xlag, x, B.n);
-    if (mixed) {
+    if (mixed32(l)) {
       float* d = B.xlag32;
-      const double* s = B.xlag;
-      map(B.n, [=] __device__(long long i) { d[i] = float(s[i]); });
+      const double* src = B.xlag;
+      map(B.n, [=] __device__(long long i) { d[i] = float(src[i]); });
+    }
+    if (P.precondition) {
+      // Jacobi: inverse of the positive part of the lagged Hessian's diagonal
+      // (the level's own Hessian at x0 for GALERKIN levels)
+      const bool m32 = mixed32(l);
+      ck(elem_hessdiag(H->geo[l], H->mat[l], m32 ? (const void*)B.xlag32 : (const void*)B.xlag,
+                       m32 ? 1 : 0, B.minv, st),
+         "hessdiag");
+      S.launches += 1;
+      double* mi = B.minv;
+      map(B.n, [=] __device__(long long i) {
+        const double d = mi[i];
+        mi[i] = d > 0.0 ? 1.0 / d : 0.0;
+      });
     }
   }
 
   // ---------------------------------------------------------------- level model h^l
   bool finest(int l) const { return l == L - 1; }
   bool galerkin(int l) const { return !finest(l) && P.coarse_model == PF_GALERKIN; }
+  // mixed precision: FP32 Hessian on every level but the coarsest (which,
+  // like energy, rho and the radius, stays FP64)
+  bool mixed32(int l) const { return mixed && (l > 0 || L == 1); }
+
+  // finest-level units of one application of the lagged model Hessian
+  double hlag_units(int l) const { return galerkin(l) ? hlag_units(l + 1) : frac(l); }
 
   // Lagged model Hessian: finest / FIRST_ORDER: Hessian at x_lag of the level;
-  // GALERKIN: R H_{l+1} I.
-  void Hlag(int l, const double* v, double* out) {
+  // GALERKIN: R H_{l+1} I.  With skip, a no-op once *skip is set; count
+  // false leaves the work counters to the caller.
+  void Hlag(int l, const double* v, double* out, const int* skip = nullptr, bool count = true) {
     if (!galerkin(l)) {
-      if (mixed) hessvec_lag32(l, v, out);
-      else hessvec(l, H->lv[l].xlag, v, out);
+      LevelBuf& B = H->lv[l];
+      if (mixed32(l))
+        ck(elem_hessvec_mixed(H->geo[l], H->mat[l], B.xlag32, v, out, st, skip), "hessvec32");
+      else
+        ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag, v, out, 0, st, skip), "hessvec");
+      S.launches += 1;
+      if (count) {
+        S.hessvecs += 1;
+        S.fe_hessvec += frac(l);
+      }
       return;
     }
     LevelBuf& F1 = H->lv[l + 1];
-    ck(xfer_prolong(H->geo[l], H->geo[l + 1], F, v, F1.gin, 0, st), "prolong");
+    ck(xfer_prolong(H->geo[l], H->geo[l + 1], F, v, F1.gin, 0, st, skip), "prolong");
     S.launches += 1;
-    Hlag(l + 1, F1.gin, F1.gout);
-    ck(xfer_restrict(H->geo[l], H->geo[l + 1], F, F1.gout, out, 0, false, st), "restrict");
+    Hlag(l + 1, F1.gin, F1.gout, skip, count);
+    ck(xfer_restrict(H->geo[l], H->geo[l + 1], F, F1.gout, out, 0, false, st, skip), "restrict");
     S.launches += 1;
   }
 
@@ -279,77 +350,121 @@ struct Solver {
     }
     int used = 0;
     double tol = -1.0;
+    CgCtrl* c = H->ctrl;
+    const int* skip = &H->ctrl->done;
     while (used < cg_max) {
-      double rr;
-      reduce<1, OpSum>(n, [=] __device__(long long i, double(&v)[1]) {
+      double rr2[2];
+      const double* mi = B.minv;
+      const bool pc = P.precondition != 0;
+      reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
         const bool fr = lo[i] < s[i] && s[i] < hi[i];
         const double ri = fr ? -(g[i] + Hs[i]) : 0.0;
+        const double zi = pc ? mi[i] * ri : ri;
         r[i] = ri;
-        p[i] = ri;
+        p[i] = zi;
         w[i] = 0.0;
         Hw[i] = 0.0;
         v[0] = ri * ri;
-      }, &rr);
+        v[1] = ri * zi;
+      }, rr2);
+      const double rr = rr2[0];
       if (tol < 0.0) {
         const double r0 = std::sqrt(rr);
         tol = std::min(0.1, std::sqrt(r0)) * r0;
       }
       if (std::sqrt(rr) <= tol || rr == 0.0) break;
-      bool leave = false;
-      while (used < cg_max) {
-        Hlag(l, p, q);
-        double kappa;
-        reduce<1, OpSum>(n, [=] __device__(long long i, double(&v)[1]) {
-          const bool fr = lo[i] < s[i] && s[i] < hi[i];
-          const double qi = fr ? q[i] : 0.0;
-          q[i] = qi;
-          v[0] = p[i] * qi;
-        }, &kappa);
-        ++used;
-        S.cg += 1;
-        if (kappa <= 0.0) {
-          double amax;
-          reduce<1, OpMin>(n, [=] __device__(long long i, double(&v)[1]) {
+      // CG on the free set, driven on the device: each iteration is the
+      // model Hessian, a reduction for p.Hp (its last block sets alpha or
+      // flags non-positive curvature), an update reduction (its last block
+      // tests the box, the forcing term and the budget and sets beta) and
+      // the direction update.  The host polls the control block between
+      // chunks of iterations; launches after a stop are no-ops.
+      k_ctrl_start<<<1, 1, 0, st>>>(c, rr, rr2[1], tol, used, cg_max);
+      ck(cudaGetLastError(), "ctrl");
+      S.launches += 1;
+      int chunk = 2;
+      for (;;) {
+        for (int k = 0; k < chunk; ++k) {
+          Hlag(l, p, q, skip, false);
+          red_fin<1, OpSum>(n, [=] __device__(long long i, double(&v)[1]) {
             const bool fr = lo[i] < s[i] && s[i] < hi[i];
-            const double sw = s[i] + w[i];
-            double a = INFINITY;
-            if (fr && p[i] > 0.0) a = (hi[i] - sw) / p[i];
-            if (fr && p[i] < 0.0) a = (lo[i] - sw) / p[i];
-            v[0] = a;
-          }, &amax);
-          amax = std::max(amax, 0.0);
-          if (std::isfinite(amax)) {
-            const double am = amax;
-            map(n, [=] __device__(long long i) {
-              w[i] += am * p[i];
-              Hw[i] += am * q[i];
-            });
-          }
-          leave = true;
-          break;
+            const double qi = fr ? q[i] : 0.0;
+            q[i] = qi;
+            v[0] = p[i] * qi;
+          }, [=] __device__(double(&a)[1]) {
+            c->kappa = a[0];
+            c->used += 1;
+            if (a[0] <= 0.0) {
+              c->done = 1;
+              c->state = CG_NEGCURV;
+            } else {
+              c->alpha = c->rz / a[0];
+            }
+          }, skip);
+          red_fin<3, OpSum>(n, [=] __device__(long long i, double(&v)[3]) {
+            const double al = c->alpha;
+            const bool fr = lo[i] < s[i] && s[i] < hi[i];
+            const double wi = w[i] + al * p[i];
+            w[i] = wi;
+            Hw[i] += al * q[i];
+            const double ri = r[i] - al * q[i];
+            r[i] = ri;
+            const double sw = s[i] + wi;
+            v[0] = ri * ri;
+            v[1] = (fr && (sw < lo[i] || sw > hi[i])) ? 1.0 : 0.0;
+            v[2] = ri * (pc ? mi[i] * ri : ri);
+          }, [=] __device__(double(&a)[3]) {
+            if (a[1] > 0.0) {
+              c->done = 1;
+              c->state = CG_LEAVE;
+            } else if (sqrt(a[0]) <= c->tol) {
+              c->done = 1;
+              c->state = CG_CONV;
+            } else if (c->used >= c->cg_max) {
+              c->done = 1;
+              c->state = CG_BUDGET;
+            } else {
+              c->beta = a[2] / c->rz;
+              c->rr = a[0];
+              c->rz = a[2];
+            }
+          }, skip);
+          map_skip(n, [=] __device__(long long i) {
+            p[i] = (pc ? mi[i] * r[i] : r[i]) + c->beta * p[i];
+          }, skip);
         }
-        const double alpha = rr / kappa;
-        double u2[2];
-        reduce<2, OpMax>(n, [=] __device__(long long i, double(&v)[2]) {
+        ck(cudaMemcpyAsync(H->h_ctrl, c, sizeof(CgCtrl), cudaMemcpyDeviceToHost, st), "ctrl");
+        ck(cudaStreamSynchronize(st), "sync");
+        if (H->h_ctrl->done) break;
+        chunk = std::min(chunk * 2, 16);
+      }
+      const CgCtrl cs = *H->h_ctrl;
+      const int its = cs.used - used;
+      used = cs.used;
+      S.cg += its;
+      S.cg_level[std::min(l, 7)] += its;
+      S.hessvecs += its;
+      S.fe_hessvec += its * hlag_units(l);
+      bool leave = cs.state == CG_LEAVE;
+      if (cs.state == CG_NEGCURV) {
+        double amax;
+        reduce<1, OpMin>(n, [=] __device__(long long i, double(&v)[1]) {
           const bool fr = lo[i] < s[i] && s[i] < hi[i];
-          const double wi = w[i] + alpha * p[i];
-          w[i] = wi;
-          Hw[i] += alpha * q[i];
-          const double ri = r[i] - alpha * q[i];
-          r[i] = ri;
-          const double sw = s[i] + wi;
-          v[0] = (fr && (sw < lo[i] || sw > hi[i])) ? 1.0 : 0.0;
-          v[1] = 0.0;
-        }, u2);
-        const double rr_new = dot(r, r, n);
-        if (u2[0] > 0.0) {
-          leave = true;
-          break;
+          const double sw = s[i] + w[i];
+          double a = INFINITY;
+          if (fr && p[i] > 0.0) a = (hi[i] - sw) / p[i];
+          if (fr && p[i] < 0.0) a = (lo[i] - sw) / p[i];
+          v[0] = a;
+        }, &amax);
+        amax = std::max(amax, 0.0);
+        if (std::isfinite(amax)) {
+          const double am = amax;
+          map(n, [=] __device__(long long i) {
+            w[i] += am * p[i];
+            Hw[i] += am * q[i];
+          });
         }
-        if (std::sqrt(rr_new) <= tol) break;
-        const double beta = rr_new / rr;
-        map(n, [=] __device__(long long i) { p[i] = r[i] + beta * p[i]; });
-        rr = rr_new;
+        leave = true;
       }
       if (!leave) {
         map(n, [=] __device__(long long i) {
@@ -414,8 +529,15 @@ struct Solver {
   // Algorithm 2 on level l, iterate in B.x, `iters` TR steps.
   void nonlinear_solve(int l, double& delta, int iters, int cg_max) {
     LevelBuf& B = H->lv[l];
+    double chi0 = -1.0;
     for (int it = 0; it < iters; ++it) {
       grad_h(l, B.x, B.g);
+      if (P.level_rtol > 0.0 && !finest(l)) {
+        // stop once the level's projected gradient fell by level_rtol
+        const double chi = pg_norm_level(l);
+        if (chi0 < 0.0) chi0 = chi;
+        else if (chi <= P.level_rtol * chi0) break;
+      }
       tr_box(l, B.x, delta);
       subproblem(l, delta, cg_max);
       Hlag(l, B.s, B.t2);
@@ -427,9 +549,13 @@ struct Solver {
       }, a);
       const double pred = -(a[0] + 0.5 * a[1]);
       S.tr_its += 1;
+      S.tr_level[std::min(l, 7)] += 1;
       if (!(pred > 0.0)) break;
       const double rho = -diff_h(l, B.x, B.s) / pred;
-      if (rho <= P.eta1) S.tr_rejected += 1;
+      if (rho <= P.eta1) {
+        S.tr_rejected += 1;
+        S.rej_level[std::min(l, 7)] += 1;
+      }
       control(rho, l, B.x, delta);
     }
   }
@@ -490,6 +616,18 @@ struct Solver {
       control(rho, l, B.x, delta);
     }
     nonlinear_solve(l, delta, P.mu2, cg);
+  }
+
+  // || x - P_F(x - g) || on level l for the level's current x and g
+  double pg_norm_level(int l) {
+    LevelBuf& B = H->lv[l];
+    const double *x = B.x, *g = B.g, *lb = B.lb, *ub = B.ub;
+    double r;
+    reduce<1, OpSum>(B.n, [=] __device__(long long i, double(&v)[1]) {
+      const double d = x[i] - fmin(fmax(x[i] - g[i], lb[i]), ub[i]);
+      v[0] = d * d;
+    }, &r);
+    return std::sqrt(r);
   }
 
   double pg_norm(const double* x) {
