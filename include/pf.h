@@ -88,6 +88,8 @@ typedef struct {
   double level_rtol;     /* a non-finest level stops its TR steps once its
                             projected gradient fell by this factor (1e-3;
                             0 = always take the full count)                  */
+  int max_restarts;      /* CG restarts after a projected search, per
+                            subproblem (1000000 = unlimited)                 */
 } pf_rmtr_params;
 
 typedef struct {
@@ -109,6 +111,9 @@ typedef struct {
   long long cg_level[8]; /* CG iterations per level (index = level, <= 8)    */
   long long tr_level[8]; /* TR iterations per level                          */
   long long rej_level[8];/* rejected TR steps per level                      */
+  long long hv_cauchy;   /* Hessian applications in Cauchy-point searches    */
+  long long hv_search;   /* Hessian applications in projected searches       */
+  long long cg_restarts; /* CG runs restarted after a projected search       */
 } pf_rmtr_stats;
 
 /* Fills p with the defaults listed beside each field above. */
@@ -161,6 +166,17 @@ pf_status pf_gradient(pf_hierarchy* h, int level, const void* x_dev, void* g_dev
  * vectors in precision prec, computed in that precision. */
 pf_status pf_hessvec(pf_hierarchy* h, int level, const void* x_lin_dev, const void* v_dev,
                      void* Hv_dev, int prec);
+
+/* Hessian lagging (Sec. 4.2.1): pf_hessvec_lag_set fixes the lagged point
+ * x_lag of `level` (precision prec; FP64 precomputes the Gauss-point
+ * coefficients A = w g/h^2, B = w g'(sigma(u)+pI)/h, M = w(g''(psi+p tr)
+ * + Gc/l_s) and assembles the Hessian into a 3^d-point block stencil held
+ * by the hierarchy; FP32 keeps x_lag only); pf_hessvec_lagged then applies
+ * H(x_lag) to v (same precision) as many times as needed.  The pressure at
+ * lag_set time is used.  These share the level's lag buffers with
+ * pf_rmtr_load_step, which resets them. */
+pf_status pf_hessvec_lag_set(pf_hierarchy* h, int level, const void* x_lag_dev, int prec);
+pf_status pf_hessvec_lagged(pf_hierarchy* h, int level, const void* v_dev, void* Hv_dev, int prec);
 
 /* Transfers between level `coarse` and coarse+1 (Sec. 3), per plane:
  * prolong: Q1 interpolation I (fine = I coarse);

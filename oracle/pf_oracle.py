@@ -548,6 +548,7 @@ class TRParams:
     atol: float = 0.0
     coarse_model: int = FIRST_ORDER
     precondition: bool = True   # Jacobi-preconditioned subproblem CG
+    max_restarts: int = 1000000  # CG restarts after projected searches, per subproblem
     level_rtol: float = 1e-3    # non-finest levels stop their TR loop once the
                                 # level's projected gradient fell by this factor
 
@@ -621,6 +622,7 @@ def solve_subproblem(g, Hv, lo, hi, delta, cg_max, tr: TRParams, stats=None, min
 
     used = 0
     tol = None
+    restarts = 0
     while used < cg_max:
         free = (lo < s) & (s < hi)
         grad_m = g + Hs
@@ -684,6 +686,9 @@ def solve_subproblem(g, Hv, lo, hi, delta, cg_max, tr: TRParams, stats=None, min
         if not accepted:
             break
         s, Hs = s_new, Hs_new
+        restarts += 1
+        if restarts > tr.max_restarts:
+            break
     return proj_box(s, lo, hi)
 
 

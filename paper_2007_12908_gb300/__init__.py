@@ -8,6 +8,6 @@ device is present."""
 from ._binding import (  # noqa: F401
     PF_DISC3D, PF_FIRST_ORDER, PF_FP32, PF_FP64, PF_GALERKIN, PF_LINE2D, PfError,
     coarse_bounds, default_params, energy, energy_diff, fractures_set, get_c_prev, gradient,
-    hessvec, mesh_hierarchy_create, pressure_set, project, prolong, restrict, rmtr_load_step,
+    hessvec, hessvec_lag_set, hessvec_lagged, mesh_hierarchy_create, pressure_set, project, prolong, restrict, rmtr_load_step,
     rmtr_load_step_host,
 )

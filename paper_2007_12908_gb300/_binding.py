@@ -27,7 +27,8 @@ EXPORTS = [
     "pf_mesh_hierarchy_destroy", "pf_level_info", "pf_fractures_set", "pf_pressure_set",
     "pf_energy", "pf_energy_diff", "pf_gradient", "pf_hessvec", "pf_prolong", "pf_restrict",
     "pf_project", "pf_coarse_bounds", "pf_rmtr_load_step", "pf_rmtr_load_step_host",
-    "pf_get_c_prev", "pf_probe_fma", "pf_energy_noalloc",
+    "pf_get_c_prev", "pf_probe_fma", "pf_energy_noalloc", "pf_hessvec_lag_set",
+    "pf_hessvec_lagged",
 ]
 
 
@@ -46,7 +47,8 @@ class RmtrParams(C.Structure):
                 ("cauchy_backtracks", C.c_int), ("cauchy_c", C.c_double),
                 ("max_cycles", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
                 ("coarse_model", C.c_int), ("precision", C.c_int),
-                ("precondition", C.c_int), ("level_rtol", C.c_double)]
+                ("precondition", C.c_int), ("level_rtol", C.c_double),
+                ("max_restarts", C.c_int)]
 
 
 class RmtrStats(C.Structure):
@@ -57,7 +59,8 @@ class RmtrStats(C.Structure):
                 ("launches", C.c_longlong), ("fe_hessvec", C.c_double),
                 ("fe_gradient", C.c_double), ("fe_energy", C.c_double),
                 ("cg_level", C.c_longlong * 8), ("tr_level", C.c_longlong * 8),
-                ("rej_level", C.c_longlong * 8)]
+                ("rej_level", C.c_longlong * 8), ("hv_cauchy", C.c_longlong),
+                ("hv_search", C.c_longlong), ("cg_restarts", C.c_longlong)]
 
     def as_dict(self):
         out = {}
@@ -99,6 +102,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_get_c_prev": (i, [vp, vp]),
         "pf_probe_fma": (i, [i, C.POINTER(d)]),
         "pf_energy_noalloc": (i, [i, C.POINTER(C.c_int), d, d, d, d, d, d, d, vp, i, vp, vp]),
+        "pf_hessvec_lag_set": (i, [vp, i, vp, i]),
+        "pf_hessvec_lagged": (i, [vp, i, vp, vp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -253,6 +258,19 @@ def hessvec(H: Hierarchy, level: int, x_lin, v, out=None):
     n = H.ndof(level)
     _check(lib().pf_hessvec(H.handle, level, _dev(x_lin, n, v.dtype), _dev(v, n), _dev(out, n, v.dtype),
                             _prec(v)))
+    return out
+
+
+def hessvec_lag_set(H: Hierarchy, level: int, x_lag):
+    _check(lib().pf_hessvec_lag_set(H.handle, level, _dev(x_lag, H.ndof(level)), _prec(x_lag)))
+
+
+def hessvec_lagged(H: Hierarchy, level: int, v, out=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(v)
+    n = H.ndof(level)
+    _check(lib().pf_hessvec_lagged(H.handle, level, _dev(v, n), _dev(out, n, v.dtype), _prec(v)))
     return out
 
 

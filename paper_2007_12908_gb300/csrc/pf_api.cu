@@ -70,6 +70,7 @@ void pf_rmtr_params_default(pf_rmtr_params* p) {
   p->precision = PF_FP64;
   p->precondition = 1;
   p->level_rtol = 1e-3;
+  p->max_restarts = 1000000;
 }
 
 const char* pf_last_error(void) { return g_last_error.c_str(); }
@@ -165,6 +166,11 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
         pf_mesh_hierarchy_destroy(h);
         return rc;
       }
+    if ((rc = alloc(h, (void**)&B.coef, sizeof(double) * coef_count(h->geo[l]))) ||
+        (rc = alloc(h, (void**)&B.stencil, sizeof(double) * stencil_count(h->geo[l])))) {
+      pf_mesh_hierarchy_destroy(h);
+      return rc;
+    }
   }
   if (cudaStreamSynchronize(h->st) != cudaSuccess) {
     pf_mesh_hierarchy_destroy(h);
@@ -293,6 +299,36 @@ pf_status pf_hessvec(pf_hierarchy* h, int level, const void* x, const void* v, v
   return PF_OK;
 }
 
+pf_status pf_hessvec_lag_set(pf_hierarchy* h, int level, const void* x, int prec) {
+  if (!valid_level(h, level) || !x) return bad("hessvec_lag_set: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  LevelBuf& B = h->lv[level];
+  if (prec == PF_FP64) {
+    PF_TRY_CUDA(cudaMemcpyAsync(B.xlag, x, sizeof(double) * B.n, cudaMemcpyDeviceToDevice, h->st),
+                "hessvec_lag_set");
+    PF_TRY_CUDA(elem_hess_coef(h->geo[level], h->mat[level], B.xlag, B.coef, h->st), "hessvec_lag_set");
+    PF_TRY_CUDA(stencil_assemble(h->geo[level], h->mat[level], B.coef, B.stencil, h->st),
+                "hessvec_lag_set");
+  } else {
+    PF_TRY_CUDA(cudaMemcpyAsync(B.xlag32, x, sizeof(float) * B.n, cudaMemcpyDeviceToDevice, h->st),
+                "hessvec_lag_set");
+  }
+  return PF_OK;
+}
+
+pf_status pf_hessvec_lagged(pf_hierarchy* h, int level, const void* v, void* Hv, int prec) {
+  if (!valid_level(h, level) || !v || !Hv) return bad("hessvec_lagged: bad argument");
+  if (check_prec(prec)) return PF_EINVAL;
+  LevelBuf& B = h->lv[level];
+  if (prec == PF_FP64)
+    PF_TRY_CUDA(stencil_apply(h->geo[level], B.stencil, static_cast<const double*>(v),
+                              static_cast<double*>(Hv), h->st),
+                "hessvec_lagged");
+  else
+    PF_TRY_CUDA(elem_hessvec(h->geo[level], h->mat[level], B.xlag32, v, Hv, 1, h->st), "hessvec_lagged");
+  return PF_OK;
+}
+
 pf_status pf_prolong(pf_hierarchy* h, int coarse, const void* vc, void* vf, int prec) {
   if (!h || coarse < 0 || coarse + 1 >= h->L || !vc || !vf) return bad("prolong: bad argument");
   if (check_prec(prec)) return PF_EINVAL;
@@ -333,7 +369,8 @@ static pf_status check_params(const pf_rmtr_params& P) {
       !(P.rtol >= 0) || !(P.atol >= 0) ||
       (P.coarse_model != PF_GALERKIN && P.coarse_model != PF_FIRST_ORDER) ||
       (P.precision != PF_FP64 && P.precision != PF_FP32) ||
-      (P.precondition != 0 && P.precondition != 1) || !(P.level_rtol >= 0 && P.level_rtol < 1))
+      (P.precondition != 0 && P.precondition != 1) || !(P.level_rtol >= 0 && P.level_rtol < 1) ||
+      P.max_restarts < 0)
     return bad("rmtr_load_step: invalid parameters");
   return PF_OK;
 }

@@ -216,6 +216,23 @@ struct Strain {
   }
 };
 
+template <int D>
+struct NSym {
+  static constexpr int value = D * (D + 1) / 2;  // B stored 00, 11, (22), 01, (02, 12)
+};
+template <int D>
+struct NCoef {
+  static constexpr int value = NSym<D>::value + 2;  // A, M, B
+};
+
+template <int D>
+__device__ __forceinline__ constexpr int sym_index(int i, int k) {
+  if (i == k) return i;
+  if (D == 2) return 2;
+  const int lo = i < k ? i : k, hi = i < k ? k : i;
+  return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+
 // ---------------------------------------------------------------- element ops
 // Every op takes the element's nodal values xe[f][a] (f = field plane,
 // a = corner) and, for hessvec / energy_diff, a second vector ve[f][a].
@@ -252,6 +269,31 @@ __device__ __forceinline__ T elem_energy(const T (*xe)[1 << D], const Mat<T>& m)
   return m.w * e;
 }
 
+// Strain invariants of a displacement gradient G (physical units):
+// tr = div u, ee = eps : eps, and the symmetric off-diagonal sums
+// G_ik + G_ki (i < k) in sym order 01, (02, 12).
+template <int D, class T>
+struct StrainSym {
+  T tr, ee, off[D == 3 ? 3 : 1];
+  __device__ __forceinline__ void set(const T G[D][D]) {
+    tr = T(0);
+    ee = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      tr += G[i][i];
+      ee += G[i][i] * G[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = i + 1; k < D; ++k) {
+        const T sik = G[i][k] + G[k][i];
+        off[sym_index<D>(i, k) - D] = sik;
+        ee += T(0.5) * sik * sik;
+      }
+  }
+};
+
 // Quartic coefficients of E_e(x + t s) - E_e(x).
 template <int D, class T>
 __device__ __forceinline__ void elem_energy_diff(const T (*xe)[1 << D], const T (*se)[1 << D],
@@ -267,6 +309,7 @@ __device__ __forceinline__ void elem_energy_diff(const T (*xe)[1 << D], const T 
   interp<D, T>(xe[D], cv, gc);
   interp<D, T>(se[D], sc, gsc);
   T a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+  const T omk = T(1) - m.k;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     T G[D][D], Gs[D][D];
@@ -277,27 +320,33 @@ __device__ __forceinline__ void elem_energy_diff(const T (*xe)[1 << D], const T 
         G[i][k] = gu[i][k][q] * m.inv_h;
         Gs[i][k] = gs[i][k][q] * m.inv_h;
       }
-    Strain<D, T> e0, e1;
+    StrainSym<D, T> e0, e1;
     e0.set(G);
     e1.set(Gs);
-    const T psi0 = T(0.5) * m.lam * e0.tr * e0.tr + m.mu * e0.ddot(e0);
-    const T psi2 = T(0.5) * m.lam * e1.tr * e1.tr + m.mu * e1.ddot(e1);
-    const T psi1 = m.lam * e0.tr * e1.tr + T(2) * m.mu * e0.ddot(e1);
-    const T omk = T(1) - m.k, omc = T(1) - cv[q], s = sc[q];
+    T e01 = T(0);  // eps(u) : eps(s)
+#pragma unroll
+    for (int i = 0; i < D; ++i) e01 += G[i][i] * Gs[i][i];
+#pragma unroll
+    for (int j = 0; j < (D == 3 ? 3 : 1); ++j) e01 += T(0.5) * e0.off[j] * e1.off[j];
+    const T psi0 = T(0.5) * m.lam * e0.tr * e0.tr + m.mu * e0.ee;
+    const T psi2 = T(0.5) * m.lam * e1.tr * e1.tr + m.mu * e1.ee;
+    const T psi1 = m.lam * e0.tr * e1.tr + T(2) * m.mu * e01;
+    const T omc = T(1) - cv[q], s = sc[q];
     const T g0 = omk * omc * omc + m.k;
     const T g1 = T(-2) * omk * omc * s;
     const T g2 = omk * s * s;
     T cg = 0, gg = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const T u = gc[k][q] * m.inv_h, v = gsc[k][q] * m.inv_h;
+      const T u = gc[k][q], v = gsc[k][q];
       cg += u * v;
       gg += v * v;
     }
+    const T ih2 = m.inv_h * m.inv_h;
     a1 += g0 * psi1 + g1 * psi0 + m.p * (g0 * e1.tr + g1 * e0.tr) +
-          m.Gc * (cv[q] * s / m.ls + m.ls * cg);
+          m.Gc * (cv[q] * s / m.ls + m.ls * ih2 * cg);
     a2 += g0 * psi2 + g1 * psi1 + g2 * psi0 + m.p * (g1 * e1.tr + g2 * e0.tr) +
-          T(0.5) * m.Gc * (s * s / m.ls + m.ls * gg);
+          T(0.5) * m.Gc * (s * s / m.ls + m.ls * ih2 * gg);
     a3 += g1 * psi2 + g2 * psi1 + m.p * g2 * e1.tr;
     a4 += g2 * psi2;
   }
@@ -315,6 +364,8 @@ __device__ __forceinline__ void elem_gradient(const T (*xe)[1 << D], const Mat<T
   for (int i = 0; i < D; ++i) interp<D, T>(xe[i], dummy, gu[i]);
   interp<D, T>(xe[D], cv, gc);
   T su[D][D][NQ], s0[NQ], sc[D][NQ], zero[NQ];
+  const T omk = T(1) - m.k;
+  const T kc = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     zero[q] = T(0);
@@ -323,95 +374,144 @@ __device__ __forceinline__ void elem_gradient(const T (*xe)[1 << D], const Mat<T
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int k = 0; k < D; ++k) G[i][k] = gu[i][k][q] * m.inv_h;
-    Strain<D, T> s;
-    s.set(G);
-    const T psi = T(0.5) * m.lam * s.tr * s.tr + m.mu * s.ddot(s);
-    const T omk = T(1) - m.k, omc = T(1) - cv[q];
+    StrainSym<D, T> e;
+    e.set(G);
+    const T psi = T(0.5) * m.lam * e.tr * e.tr + m.mu * e.ee;
+    const T omc = T(1) - cv[q];
     const T g = omk * omc * omc + m.k;
     const T dg = T(-2) * omk * omc;
     // weight and 1/h of the test gradient folded into the coefficient
     const T wg = m.w * m.inv_h * g;
+    const T dia = m.lam * e.tr + m.p, wgm = wg * m.mu;
 #pragma unroll
-    for (int i = 0; i < D; ++i)
+    for (int i = 0; i < D; ++i) {
+      su[i][i][q] = wg * (dia + T(2) * m.mu * G[i][i]);
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        T sig = T(2) * m.mu * s.eps[i][k];
-        if (i == k) sig += m.lam * s.tr + m.p;
-        su[i][k][q] = wg * sig;
+      for (int k = i + 1; k < D; ++k) {
+        const T v = wgm * e.off[sym_index<D>(i, k) - D];
+        su[i][k][q] = v;
+        su[k][i][q] = v;
       }
-    s0[q] = m.w * (dg * (psi + m.p * s.tr) + m.Gc * cv[q] / m.ls);
-    const T f = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
+    }
+    s0[q] = m.w * (dg * (psi + m.p * e.tr) + m.Gc * cv[q] / m.ls);
 #pragma unroll
-    for (int k = 0; k < D; ++k) sc[k][q] = f * gc[k][q];
+    for (int k = 0; k < D; ++k) sc[k][q] = kc * gc[k][q];
   }
 #pragma unroll
   for (int i = 0; i < D; ++i) test<D, T>(zero, su[i], out[i]);
   test<D, T>(s0, sc, out[D]);
 }
 
-// Hessian at x applied to v:
+// ---------------------------------------------------------------- Hessian
+// The Hessian at x applied to v,
 //   u-rows  int [g sigma(v_u) + g' v_c (sigma(u) + p I)] : grad phi
 //   c-row   int [g' (sigma(u) + p I) : eps(v_u) + (g''(psi + p tr) + Gc/ls) v_c] phi
 //               + Gc ls grad v_c . grad phi
+// depends on x only through three Gauss-point coefficients (raw nodal
+// differences for the gradients, 1/h and the weight folded in):
+//   A = w g / h^2,   B = w g' (sigma(u) + p I) / h  (symmetric),
+//   M = w (g''(psi + p tr) + Gc/ls).
+// Under Hessian lagging they are computed once per lagged point and every
+// Hessian-vector product then needs only the v-part below.
+// cf[q][0] = A, cf[q][1] = M, cf[q][2 + s] = B_s
 template <int D, class T>
-__device__ __forceinline__ void elem_hessvec(const T (*xe)[1 << D], const T (*ve)[1 << D],
-                                             const Mat<T>& m, T (*out)[1 << D]) {
+__device__ __forceinline__ void hess_coef(const T (*xe)[1 << D], const Mat<T>& m,
+                                          T (*cf)[NCoef<D>::value]) {
+  constexpr int NQ = 1 << D;
+  T gu[D][D][NQ], cv[NQ], gdummy[D][NQ], dummy[NQ];
+#pragma unroll
+  for (int i = 0; i < D; ++i) interp<D, T>(xe[i], dummy, gu[i]);
+  interp<D, T>(xe[D], cv, gdummy);
+  const T omk = T(1) - m.k;
+  const T wh2 = m.w * m.inv_h * m.inv_h, wh = m.w * m.inv_h;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T G[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) G[i][k] = gu[i][k][q] * m.inv_h;
+    T tr = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) tr += G[i][i];
+    T ee = T(0);  // eps : eps
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      ee += G[i][i] * G[i][i];
+#pragma unroll
+      for (int k = i + 1; k < D; ++k) {
+        const T e = T(0.5) * (G[i][k] + G[k][i]);
+        ee += T(2) * e * e;
+      }
+    }
+    const T psi = T(0.5) * m.lam * tr * tr + m.mu * ee;
+    const T omc = T(1) - cv[q];
+    const T g = omk * omc * omc + m.k;
+    const T dgw = T(-2) * omk * omc * wh;
+    cf[q][0] = wh2 * g;
+    cf[q][1] = m.w * (T(2) * omk * (psi + m.p * tr) + m.Gc / m.ls);
+    const T diag = m.lam * tr + m.p;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      cf[q][2 + i] = dgw * (diag + T(2) * m.mu * G[i][i]);
+#pragma unroll
+      for (int k = i + 1; k < D; ++k) cf[q][2 + sym_index<D>(i, k)] = dgw * m.mu * (G[i][k] + G[k][i]);
+    }
+  }
+}
+
+// The v-part: out = H v from the coefficients of the element's Gauss points.
+template <int D, class T>
+__device__ __forceinline__ void hess_apply(const T (*ve)[1 << D], const T (*cf)[NCoef<D>::value],
+                                           const Mat<T>& m, T (*out)[1 << D]) {
   constexpr int NQ = 1 << D;
   T su[D][D][NQ], s0[NQ], sc[D][NQ], zero[NQ];
   {
-    T gu[D][D][NQ], cv[NQ], dummy[NQ], gdummy[D][NQ];
-    T gv[D][D][NQ], vc[NQ], gvc[D][NQ];
+    T gv[D][D][NQ], vc[NQ], gvc[D][NQ], dummy[NQ];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      interp<D, T>(xe[i], dummy, gu[i]);
-      interp<D, T>(ve[i], dummy, gv[i]);
-    }
-    interp<D, T>(xe[D], cv, gdummy);
+    for (int i = 0; i < D; ++i) interp<D, T>(ve[i], dummy, gv[i]);
     interp<D, T>(ve[D], vc, gvc);
+    const T kc = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       zero[q] = T(0);
-      T G[D][D], Gv[D][D];
+      const T A = cf[q][0], M = cf[q][1];
+      T trr = T(0);
 #pragma unroll
-      for (int i = 0; i < D; ++i)
+      for (int i = 0; i < D; ++i) trr += gv[i][i][q];
+      const T lt = m.lam * trr, am = A * m.mu;
+      T c0 = M * vc[q];
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          G[i][k] = gu[i][k][q] * m.inv_h;
-          Gv[i][k] = gv[i][k][q] * m.inv_h;
+      for (int i = 0; i < D; ++i) {
+        const T Bii = cf[q][2 + i];
+        su[i][i][q] = A * (lt + T(2) * m.mu * gv[i][i][q]) + vc[q] * Bii;
+        c0 += Bii * gv[i][i][q];
+#pragma unroll
+        for (int k = i + 1; k < D; ++k) {
+          const T Bik = cf[q][2 + sym_index<D>(i, k)];
+          const T sik = gv[i][k][q] + gv[k][i][q];
+          const T v = am * sik + vc[q] * Bik;
+          su[i][k][q] = v;
+          su[k][i][q] = v;
+          c0 += Bik * sik;
         }
-      Strain<D, T> e, ev;
-      e.set(G);
-      ev.set(Gv);
-      const T psi = T(0.5) * m.lam * e.tr * e.tr + m.mu * e.ddot(e);
-      const T omk = T(1) - m.k, omc = T(1) - cv[q];
-      const T g = omk * omc * omc + m.k;
-      const T dg = T(-2) * omk * omc;
-      const T ddg = T(2) * omk;
-      const T dgv = dg * vc[q];
-      const T wh = m.w * m.inv_h;
-      T Tev = T(0);  // (sigma(u) + p I) : eps(v)
+      }
+      s0[q] = c0;
 #pragma unroll
-      for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          T Tik = T(2) * m.mu * e.eps[i][k];
-          T Sv = T(2) * m.mu * ev.eps[i][k];
-          if (i == k) {
-            Tik += m.lam * e.tr + m.p;
-            Sv += m.lam * ev.tr;
-          }
-          Tev += Tik * ev.eps[i][k];
-          su[i][k][q] = wh * (g * Sv + dgv * Tik);
-        }
-      s0[q] = m.w * (dg * Tev + (ddg * (psi + m.p * e.tr) + m.Gc / m.ls) * vc[q]);
-      const T f = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
-#pragma unroll
-      for (int k = 0; k < D; ++k) sc[k][q] = f * gvc[k][q];
+      for (int k = 0; k < D; ++k) sc[k][q] = kc * gvc[k][q];
     }
   }
 #pragma unroll
   for (int i = 0; i < D; ++i) test<D, T>(zero, su[i], out[i]);
   test<D, T>(s0, sc, out[D]);
+}
+
+template <int D, class T>
+__device__ __forceinline__ void elem_hessvec(const T (*xe)[1 << D], const T (*ve)[1 << D],
+                                             const Mat<T>& m, T (*out)[1 << D]) {
+  T cf[1 << D][NCoef<D>::value];
+  hess_coef<D, T>(xe, m, cf);
+  hess_apply<D, T>(ve, cf, m, out);
 }
 
 // Diagonal of the Hessian (Jacobi preconditioner):

@@ -21,6 +21,8 @@ struct LevelBuf {
   double *dh = nullptr;                    // dH scratch
   double *minv = nullptr;                  // Jacobi preconditioner of the lagged Hessian
   float* xlag32 = nullptr;  // FP32 copy of x_lag (mixed precision)
+  double* coef = nullptr;   // lagged Gauss-point coefficients (FP64 Hessian)
+  double* stencil = nullptr;  // assembled lagged FP64 Hessian (3^d block stencil)
 };
 
 // Device-resident control block of one projected CG run: the scalars each

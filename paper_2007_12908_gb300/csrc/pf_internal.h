@@ -45,6 +45,24 @@ cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, vo
                           cudaStream_t st);
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
                          void* y, int prec, cudaStream_t st, const int* skip = nullptr);
+// FP64 lagged Hessian: Gauss-point coefficients of x (coef holds
+// NE * 2^d * (2 + d(d+1)/2) doubles), the input of the stencil assembly.
+cudaError_t elem_hess_coef(const Geom& g, const Mat<double>& m, const double* x, double* coef,
+                           cudaStream_t st);
+inline long long coef_count(const Geom& g) {
+  const int d = g.dim;
+  return g.NE * (1LL << d) * (2 + d * (d + 1) / 2);
+}
+// The lagged FP64 Hessian assembled into a 3^d-point block stencil (S holds
+// stencil_count(g) doubles) from the stored coefficients, and its product.
+inline long long stencil_count(const Geom& g) {
+  const int f = g.dim + 1;
+  return (g.dim == 3 ? 27LL : 9LL) * f * f * g.N;
+}
+cudaError_t stencil_assemble(const Geom& g, const Mat<double>& m, const double* coef, double* S,
+                             cudaStream_t st);
+cudaError_t stencil_apply(const Geom& g, const double* S, const double* v, double* y,
+                          cudaStream_t st, const int* skip = nullptr);
 // Diagonal of the Hessian at x (precision prec), written as FP64.
 cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, int prec,
                           double* y, cudaStream_t st);

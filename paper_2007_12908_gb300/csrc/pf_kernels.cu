@@ -7,6 +7,7 @@
 // corner a of every element; distinct elements hit distinct nodes within a
 // phase).  Each owned node therefore receives its element contributions in
 // a fixed order: results are bitwise reproducible, with no atomics.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -152,6 +153,28 @@ struct Tile<2> {
 
 enum { OP_GRAD = 0, OP_HESS = 1, OP_DIAG = 2 };
 
+// Lagged Gauss-point coefficients of the Hessian, one element per thread;
+// stored coef[(q * NCOEF + k) * NE + e] so that consecutive elements are
+// consecutive in memory.
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_hess_coef(Geom g, Mat<T> m, const T* __restrict__ x,
+                                                   T* __restrict__ coef) {
+  constexpr int NQ = 1 << D, NCF = NCoef<D>::value;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.NE;
+       e += (long long)gridDim.x * blockDim.x) {
+    int ex, ey, ez;
+    elem_coords<D>(g, e, ex, ey, ez);
+    T xe[D + 1][NQ];
+    gather<D, T>(g, x, ex, ey, ez, xe);
+    T cf[NQ][NCF];
+    hess_coef<D, T>(xe, m, cf);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int k = 0; k < NCF; ++k) coef[(q * NCF + k) * g.NE + e] = cf[q][k];
+  }
+}
+
 // TC: compute precision (and that of x); TIO: precision of v and y.
 // skip: when non-null and *skip != 0 the launch does nothing (the solver's
 // device-side CG stops this way without a host round trip).
@@ -248,6 +271,172 @@ cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, con
                 : launch_scatter<3, double, double, OP_HESS>(g, m, x, v, y, skip, st);
   return prec ? launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st)
               : launch_scatter<2, double, double, OP_HESS>(g, m, x, v, y, skip, st);
+}
+
+cudaError_t elem_hess_coef(const Geom& g, const Mat<double>& m, const double* x, double* coef,
+                           cudaStream_t st) {
+  const int nb = int(std::min<long long>((g.NE + 255) / 256, 8LL * 1216));
+  if (g.dim == 3)
+    k_hess_coef<3, double><<<nb, 256, 0, st>>>(g, cast_mat<double>(m), x, coef);
+  else
+    k_hess_coef<2, double><<<nb, 256, 0, st>>>(g, cast_mat<double>(m), x, coef);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ assembled Hessian
+// The lagged FP64 Hessian stored as a (3^d)-point block stencil: for node i,
+// offset o (component k of the offset = o_k - 1 in {-1, 0, 1}) and fields
+// f, g, the entry S[((o * F + f) * F + g) * N + i] couples dof (f, i) with
+// dof (g, i + offset).  Assembled from the stored Gauss-point coefficients
+// (A, M, B) of the up to 2^d elements around each node; each thread owns
+// one node's row, so the sums need no atomics.
+template <int D>
+__device__ __forceinline__ void shape_tables(int a, int q, double& na, double (&da)[D]) {
+  double n1[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) n1[k] = (((q >> k) & 1) == ((a >> k) & 1)) ? PF_XI1 : PF_XI0;
+  na = 1.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) na *= n1[k];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double t = ((a >> k) & 1) ? 1.0 : -1.0;  // raw derivative of the 1D factor
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+      if (j != k) t *= n1[j];
+    da[k] = t;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_assemble(Geom g, Mat<double> m,
+                                                  const double* __restrict__ coef,
+                                                  double* __restrict__ S) {
+  constexpr int F = D + 1, NC = 1 << D, NCF = NCoef<D>::value;
+  const double kc = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = int(i % g.n[0]);
+    const long long r = i / g.n[0];
+    const int iy = int(r % g.n[1]);
+    const int iz = int(r / g.n[1]);
+    const int ic[3] = {ix, iy, iz};
+    for (int a = 0; a < NC; ++a) {  // node i is corner a of element i - corner(a)
+      int ec[3] = {0, 0, 0};
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        ec[k] = ic[k] - ((a >> k) & 1);
+        ok = ok && ec[k] >= 0 && ec[k] < g.ne[k];
+      }
+      if (!ok) continue;
+      const long long e = ec[0] + (long long)g.ne[0] * (ec[1] + (long long)g.ne[1] * ec[2]);
+      for (int b = 0; b < NC; ++b) {
+        int o = 0, stride = 1;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          o += (((b >> k) & 1) - ((a >> k) & 1) + 1) * stride;
+          stride *= 3;
+        }
+        double blk[F][F];
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+#pragma unroll
+          for (int h = 0; h < F; ++h) blk[f][h] = 0.0;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          double na, nb, da[D], db[D];
+          shape_tables<D>(a, q, na, da);
+          shape_tables<D>(b, q, nb, db);
+          const double A = coef[(q * NCF + 0) * g.NE + e];
+          const double M = coef[(q * NCF + 1) * g.NE + e];
+          double B[D][D];
+#pragma unroll
+          for (int ii = 0; ii < D; ++ii)
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) B[ii][kk] = coef[(q * NCF + 2 + sym_index<D>(ii, kk)) * g.NE + e];
+          double dd = 0.0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) dd += da[k] * db[k];
+#pragma unroll
+          for (int ii = 0; ii < D; ++ii) {
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) {
+              double v = m.lam * da[ii] * db[jj] + m.mu * da[jj] * db[ii];
+              if (ii == jj) v += m.mu * dd;
+              blk[ii][jj] += A * v;
+            }
+            double bu = 0.0, bc = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              bu += B[ii][k] * da[k];
+              bc += B[ii][k] * db[k];
+            }
+            blk[ii][D] += bu * nb;  // u_i(a) - c(b)
+            blk[D][ii] += na * bc;  // c(a) - u_i(b)
+          }
+          blk[D][D] += M * na * nb + kc * dd;
+        }
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+#pragma unroll
+          for (int h = 0; h < F; ++h) S[((long long)(o * F + f) * F + h) * g.N + i] += blk[f][h];
+      }
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_stencil_apply(Geom g, const double* __restrict__ S,
+                                                       const double* __restrict__ v,
+                                                       double* __restrict__ y,
+                                                       const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int F = D + 1, NO = D == 3 ? 27 : 9;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = int(i % g.n[0]);
+    const long long r = i / g.n[0];
+    const int iy = int(r % g.n[1]);
+    const int iz = int(r / g.n[1]);
+    double acc[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = 0.0;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = D == 3 ? o / 9 - 1 : 0;
+      const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+      if (jx < 0 || jx >= g.n[0] || jy < 0 || jy >= g.n[1] || jz < 0 || jz >= g.n[2]) continue;
+      const long long j = jx + g.n[0] * (jy + (long long)g.n[1] * jz);
+      double vj[F];
+#pragma unroll
+      for (int h = 0; h < F; ++h) vj[h] = v[h * g.N + j];
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int h = 0; h < F; ++h) acc[f] += S[((long long)(o * F + f) * F + h) * g.N + i] * vj[h];
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) y[f * g.N + i] = acc[f];
+  }
+}
+
+cudaError_t stencil_assemble(const Geom& g, const Mat<double>& m, const double* coef, double* S,
+                             cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * stencil_count(g), st);
+  if (e != cudaSuccess) return e;
+  const int nb = int(std::min<long long>((g.N + 127) / 128, 16LL * 1216));
+  if (g.dim == 3) k_assemble<3><<<nb, 128, 0, st>>>(g, m, coef, S);
+  else k_assemble<2><<<nb, 128, 0, st>>>(g, m, coef, S);
+  return cudaGetLastError();
+}
+
+cudaError_t stencil_apply(const Geom& g, const double* S, const double* v, double* y,
+                          cudaStream_t st, const int* skip) {
+  const int nb = int(std::min<long long>((g.N + 255) / 256, 16LL * 1216));
+  if (g.dim == 3) k_stencil_apply<3><<<nb, 256, 0, st>>>(g, S, v, y, skip);
+  else k_stencil_apply<2><<<nb, 256, 0, st>>>(g, S, v, y, skip);
+  return cudaGetLastError();
 }
 
 cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, int prec,

@@ -168,12 +168,6 @@ struct Solver {
   }
 
   // ---------------------------------------------------------------- element ops
-  void hessvec(int l, const double* x, const double* v, double* out) {
-    ck(elem_hessvec(H->geo[l], H->mat[l], x, v, out, 0, st), "hessvec");
-    S.hessvecs += 1;
-    S.fe_hessvec += frac(l);
-    S.launches += 1;
-  }
   void gradient(int l, const double* x, double* out) {
     ck(elem_gradient(H->geo[l], H->mat[l], x, out, 0, st), "gradient");
     S.fe_gradient += frac(l);
@@ -203,6 +197,13 @@ struct Solver {
       float* d = B.xlag32;
       const double* src = B.xlag;
       map(B.n, [=] __device__(long long i) { d[i] = float(src[i]); });
+    }
+    if (!mixed32(l) || galerkin(l)) {
+      // FP64 Hessian of this level: Gauss-point coefficients, once per lag
+      ck(elem_hess_coef(H->geo[l], H->mat[l], B.xlag, B.coef, st), "hess_coef");
+      ck(stencil_assemble(H->geo[l], H->mat[l], B.coef, B.stencil, st), "assemble");
+      S.launches += 2;
+      S.fe_gradient += frac(l);
     }
     if (P.precondition) {
       // Jacobi: inverse of the positive part of the lagged Hessian's diagonal
@@ -239,7 +240,7 @@ struct Solver {
       if (mixed32(l))
         ck(elem_hessvec_mixed(H->geo[l], H->mat[l], B.xlag32, v, out, st, skip), "hessvec32");
       else
-        ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag, v, out, 0, st, skip), "hessvec");
+        ck(stencil_apply(H->geo[l], B.stencil, v, out, st, skip), "hessvec");
       S.launches += 1;
       if (count) {
         S.hessvecs += 1;
@@ -259,7 +260,11 @@ struct Solver {
   void dH(int l, const double* v, double* out) {
     LevelBuf& B = H->lv[l];
     Hlag(l, v, out);
-    hessvec(l, B.x0, v, B.dh);
+    // the level's own Hessian at x0 (= its lag point): the assembled stencil
+    ck(stencil_apply(H->geo[l], B.stencil, v, B.dh, st), "hessvec");
+    S.launches += 1;
+    S.hessvecs += 1;
+    S.fe_hessvec += frac(l);
     const double* t = B.dh;
     map(B.n, [=] __device__(long long i) { out[i] -= t[i]; });
   }
@@ -322,6 +327,7 @@ struct Solver {
       t1[i] = mv ? g[i] : 0.0;
     });
     Hlag(l, t1, t2);
+    S.hv_cauchy += 1;
     double cg2[2];
     reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
       v[0] = t1[i] * t2[i];
@@ -333,6 +339,7 @@ struct Solver {
       const double tt = t;
       map(n, [=] __device__(long long i) { s[i] = fmin(fmax(-tt * g[i], lo[i]), hi[i]); });
       Hlag(l, s, Hs);
+      S.hv_cauchy += 1;
       double a[2];
       reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
         v[0] = g[i] * s[i];
@@ -349,6 +356,7 @@ struct Solver {
       return;
     }
     int used = 0;
+    int restarts = 0;
     double tol = -1.0;
     CgCtrl* c = H->ctrl;
     const int* skip = &H->ctrl->done;
@@ -486,6 +494,7 @@ struct Solver {
         const double b = beta;
         map(n, [=] __device__(long long i) { t1[i] = fmin(fmax(s[i] + b * w[i], lo[i]), hi[i]); });
         Hlag(l, t1, t2);
+        S.hv_search += 1;
         double a[3];
         reduce<3, OpSum>(n, [=] __device__(long long i, double(&v)[3]) {
           v[0] = g[i] * t1[i];
@@ -501,6 +510,8 @@ struct Solver {
       if (!accepted) break;
       copy(s, t1, n);
       copy(Hs, t2, n);
+      S.cg_restarts += 1;
+      if (++restarts > P.max_restarts) break;
     }
     map(n, [=] __device__(long long i) { s[i] = fmin(fmax(s[i], lo[i]), hi[i]); });
   }

@@ -45,7 +45,12 @@ def test_energy_gradient_hessvec_fp64(pf, dim, nc, L, hc, k_res):
         eo = O.energy(g, Ho.prm, x)
         assert abs(e - eo) <= TOL64 * abs(eo)
         assert relinf(host(pf.gradient(H, level, xd)), O.gradient(g, Ho.prm, x)) <= TOL64
-        assert relinf(host(pf.hessvec(H, level, xd, vd)), O.hessvec(g, Ho.prm, x, v)) <= TOL64
+        ho = O.hessvec(g, Ho.prm, x, v)
+        assert relinf(host(pf.hessvec(H, level, xd, vd)), ho) <= TOL64
+        # Hessian lagging: stored Gauss-point coefficients, applied twice
+        pf.hessvec_lag_set(H, level, xd)
+        for _ in range(2):
+            assert relinf(host(pf.hessvec_lagged(H, level, vd)), ho) <= TOL64
         a = pf.energy_diff(H, level, xd, dev(0.1 * v))
         ao = O.energy_diff_coeffs(g, Ho.prm, x, 0.1 * v)
         assert np.max(np.abs(a - ao)) <= TOL64 * np.max(np.abs(ao))
@@ -60,7 +65,10 @@ def test_hessvec_fp32(pf, dim, nc, L, hc):
     v = PI.random_direction(8, x.size)
     hv = pf.hessvec(H, L - 1, dev(x, torch.float32), dev(v, torch.float32))
     assert hv.dtype == torch.float32
-    assert relinf(host(hv), O.hessvec(g, Ho.prm, x, v)) <= TOL32
+    ho = O.hessvec(g, Ho.prm, x, v)
+    assert relinf(host(hv), ho) <= TOL32
+    pf.hessvec_lag_set(H, L - 1, dev(x, torch.float32))
+    assert relinf(host(pf.hessvec_lagged(H, L - 1, dev(v, torch.float32))), ho) <= TOL32
     gr = pf.gradient(H, L - 1, dev(x, torch.float32))
     assert relinf(host(gr), O.gradient(g, Ho.prm, x)) <= TOL32
 
@@ -152,5 +160,7 @@ def test_full_size_sampled(pf, dim, nc, L, hc):
     ho = O.hessvec(g, Ho.prm, x, v, elems)[idx]
     assert relinf(host(pf.gradient(H, L - 1, xd))[idx], go) <= TOL64
     assert relinf(host(pf.hessvec(H, L - 1, xd, vd))[idx], ho) <= TOL64
+    pf.hessvec_lag_set(H, L - 1, xd)
+    assert relinf(host(pf.hessvec_lagged(H, L - 1, vd))[idx], ho) <= TOL64
     h32 = pf.hessvec(H, L - 1, xd.float(), vd.float())
     assert relinf(host(h32)[idx], ho) <= TOL32
