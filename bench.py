@@ -42,16 +42,12 @@ METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same G
 UNIT = "s/load-step"
 
 # Finest-level-equivalent element passes per load step of the CUDA path on
-# this workload (FP64, first-order coarse model), measured by this script's
-# GPU arm (printed as "work_model"); they scale the oracle's per-pass
-# seconds to seconds per load step for the CPU baseline and reference arm.
-REF_WORK_MODEL = {"fe_hessvec": 400.0, "fe_gradient": 10.0, "fe_energy": 30.0}
+# this workload (default configuration: mixed precision, extrapolated
+# start), measured by this script's GPU arm (printed as "work_model"); they
+# scale the oracle's per-pass seconds to seconds per load step for the
+# reference arm.
+REF_WORK_MODEL = {"fe_hessvec": 228.4, "fe_gradient": 9.18, "fe_energy": 8.17}
 
-# FP64 flops per element of the lagged Hessian-vector product as
-# implemented (sum-factorised interpolation of the 4 fields of v, 8
-# Gauss-point updates from the stored coefficients, 4 adjoint contractions;
-# an FMA counts 2): interpolation 4 x 90, Gauss points 8 x 62, test 4 x 90.
-HESSVEC_FP64_FLOPS_PER_ELEMENT = 1216.0
 
 
 def parse():
@@ -61,6 +57,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--start", choices=["plain", "extrapolate"], default="extrapolate",
+                    help="starting iterate of each load step (plain = x_{t-1})")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="also time the same K load steps in plain FP64")
     ap.add_argument("--kernels-only", action="store_true",
@@ -249,7 +247,8 @@ def run_ours(args):
         W["workload"] = f"3d_{8 * (args.coarse_n - 1) + 1}^3_q1_4level_20discs_ramp"
     prm = pf.default_params(
         precision=pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64,
-        coarse_model=pf.PF_GALERKIN if args.coarse_model == "galerkin" else pf.PF_FIRST_ORDER)
+        coarse_model=pf.PF_GALERKIN if args.coarse_model == "galerkin" else pf.PF_FIRST_ORDER,
+        start=pf.PF_START_EXTRAPOLATE if args.start == "extrapolate" else pf.PF_START_PLAIN)
     H = pf.mesh_hierarchy_create(3, W["n_coarse"], W["levels"], W["h_coarse"], E=W["E"],
                                  nu=W["nu"], Gc=W["Gc"], ls_over_h=W["ls_over_h"])
     g_n, g_h, N = H.levels[-1]
@@ -313,7 +312,6 @@ def run_ours(args):
     o32 = torch.empty_like(v32)
     t32 = time_kernel(lambda: pf.hessvec(H, level, x32, v32, o32))
     t_grad = time_kernel(lambda: pf.gradient(H, level, x, out))
-    n_elem = (g_n[0] - 1) * (g_n[1] - 1) * (g_n[2] - 1)
     fma64 = B.probe_fma(pf.PF_FP64)
     hbm = None
     try:
@@ -321,19 +319,58 @@ def run_ours(args):
         hbm_src = "measured"
     except (OSError, KeyError, ValueError):
         hbm, hbm_src = 6800.0, "fallback"
-    bytes64 = 24.0 * ndof
+    # FP64 lagged Hessian = the assembled 27-point block stencil: it reads the
+    # stencil (27 x 4 x 4 doubles per node) and v, and writes Hv
+    bytes64 = (27 * 16 * 8 + 2 * 4 * 8) * N
     bytes32 = 12.0 * ndof
-    flops64 = HESSVEC_FP64_FLOPS_PER_ELEMENT * n_elem
-    roof64 = {"kernel": "hessvec_fp64", "bound": "alu", "achieved": flops64 / t64 / 1e12,
-              "peak": fma64 / 1e12, "unit": "TFLOP/s", "frac": flops64 / t64 / fma64,
-              "traffic": None, "peak_source": "measured FP64 FMA probe (pf_probe_fma)",
-              "hbm_gbs": bytes64 / t64 / 1e9, "hbm_frac": bytes64 / t64 / 1e9 / hbm,
+    roof64 = {"kernel": "hessvec_fp64 (assembled stencil apply)", "bound": "hbm",
+              "achieved": bytes64 / t64 / 1e9, "peak": hbm, "unit": "GB/s",
+              "frac": bytes64 / t64 / 1e9 / hbm, "traffic": None,
+              "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+              "flop_per_node": 864, "fp64_fma_peak_tflops": fma64 / 1e12,
               "gdofs": ndof / t64 / 1e9, "us_per_launch": t64 * 1e6}
     roof32 = {"kernel": "hessvec_fp32", "bound": "hbm", "achieved": bytes32 / t32 / 1e9,
               "peak": hbm, "unit": "GB/s", "frac": bytes32 / t32 / 1e9 / hbm, "traffic": None,
               "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
               "gdofs": ndof / t32 / 1e9, "us_per_launch": t32 * 1e6}
     roofline = roof64 if args.precision == "fp64" else roof32
+
+    def with_p_prev(p_src, t):
+        """Parameters of timed step t: the first one names the warm-up's last
+        pressure so an extrapolated start scales as in the timed run."""
+        q = pf.default_params(**{k: getattr(p_src, k) for k, _ in p_src._fields_})
+        if t == args.warmup + 1:
+            q.p_prev = W["dp"] * args.warmup
+        return q
+
+    def compare(p_cmp):
+        """The same K timed load steps from the same warmed-up state with
+        other parameters."""
+        xc = x_after_warmup.clone()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sc = []
+        for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+            pf.pressure_set(H, W["dp"] * t)
+            sc.append(pf.rmtr_load_step(H, xc, with_p_prev(p_cmp, t), check=False))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ec = [s["energy"] for s in sc]
+        eh = [s["energy"] for s in stats]
+        return {"value": a.elapsed_time(b) / args.steps / 1e3, "unit": UNIT,
+                "speedup_of_headline": a.elapsed_time(b) / args.steps / ms,
+                "energy_rel_diff": max(abs(p - q) / abs(q) for p, q in zip(eh, ec)),
+                "cycles": [s["cycles"] for s in sc], "status": [s["status"] for s in sc]}
+
+    fp64_cmp = mixed_plain = None
+    if args.compare_fp64:
+        fp64_cmp = compare(pf.default_params(precision=pf.PF_FP64, coarse_model=prm.coarse_model,
+                                             start=pf.PF_START_PLAIN))
+        if args.precision == "mixed" and args.start != "plain":
+            mixed_plain = compare(pf.default_params(precision=pf.PF_FP32, coarse_model=prm.coarse_model,
+                                                    start=pf.PF_START_PLAIN))
 
     # ---- end to end through the host-buffer entry point
     e2e = None
@@ -345,31 +382,10 @@ def run_ours(args):
         t0 = time.perf_counter()
         for t in range(args.warmup + 1, args.warmup + args.steps + 1):
             pf.pressure_set(H, W["dp"] * t)
-            pf.rmtr_load_step_host(H, xn, prm, check=False)
+            pf.rmtr_load_step_host(H, xn, with_p_prev(prm, t), check=False)
         e2e_s = (time.perf_counter() - t0) / args.steps
         e2e = {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
                "d2h_bytes_per_step": 8 * ndof}
-
-    fp64_cmp = None
-    if args.compare_fp64 and args.precision != "fp64":
-        p64 = pf.default_params(precision=pf.PF_FP64, coarse_model=prm.coarse_model)
-        x64 = x_after_warmup.clone()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        s64 = []
-        for t in range(args.warmup + 1, args.warmup + args.steps + 1):
-            pf.pressure_set(H, W["dp"] * t)
-            s64.append(pf.rmtr_load_step(H, x64, p64, check=False))
-        b.record(stream)
-        torch.cuda.synchronize()
-        e64 = [s["energy"] for s in s64]
-        emx = [s["energy"] for s in stats]
-        fp64_cmp = {"value": a.elapsed_time(b) / args.steps / 1e3, "unit": UNIT,
-                    "speedup_of_headline": a.elapsed_time(b) / args.steps / ms,
-                    "energy_rel_diff": max(abs(p - q) / abs(q) for p, q in zip(emx, e64)),
-                    "cycles": [s["cycles"] for s in s64]}
 
     work = {k: statistics.mean(s[k] for s in stats) for k in ("fe_hessvec", "fe_gradient", "fe_energy")}
     cpu = None
@@ -395,6 +411,7 @@ def run_ours(args):
                        "dofs": ndof, "fractures": W["fractures"], "pressure_steps": [
                            W["dp"] * t for t in range(args.warmup + 1, args.warmup + args.steps + 1)],
                        "precision": args.precision, "coarse_model": args.coarse_model,
+                       "start": args.start,
                        "parallelism": f"replicas{world}",
                        "l2": "working set > L2 (FP64 vectors 69 MB each, >20 resident)"},
             "roofline": roofline,
@@ -402,6 +419,7 @@ def run_ours(args):
             "hessvec_gdofs": {"fp64": ndof / t64 / 1e9, "fp32": ndof / t32 / 1e9},
             "gradient_fp64_us": t_grad * 1e6,
             "fp64_plain": fp64_cmp,
+            "mixed_plain_start": mixed_plain,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches,

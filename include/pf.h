@@ -90,7 +90,23 @@ typedef struct {
                             0 = always take the full count)                  */
   int max_restarts;      /* CG restarts after a projected search, per
                             subproblem (1000000 = unlimited)                 */
+  int keep_c_prev;       /* 0: c_prev := c of x on entry; 1: keep the
+                            hierarchy's c_prev (set by pf_learned_propose)   */
+  double pg_ref;         /* > 0: the stopping test is relative to this value
+                            instead of the start's own projected gradient,
+                            so that every starting point stops at the same
+                            accuracy (see pf_projected_gradient); 0 = start  */
+  int start;             /* PF_START_PLAIN: iterate from x as given;
+                            PF_START_EXTRAPOLATE: scale u by p / p_last (the
+                            pressure of the last converged step), c kept,
+                            with the stopping test relative to the plain
+                            start (pg_ref taken at x as given)               */
+  double p_prev;         /* > 0: the previous pressure for
+                            PF_START_EXTRAPOLATE instead of p_last           */
 } pf_rmtr_params;
+
+#define PF_START_PLAIN 0
+#define PF_START_EXTRAPOLATE 1
 
 typedef struct {
   int cycles;            /* V-cycles taken                                   */
@@ -204,6 +220,12 @@ pf_status pf_rmtr_load_step(pf_hierarchy* h, void* x_dev, const pf_rmtr_params* 
 pf_status pf_rmtr_load_step_host(pf_hierarchy* h, double* x_host, const pf_rmtr_params* params,
                                  pf_rmtr_stats* stats);
 
+/* || x - P_F(x - grad E(x)) ||_2 on the finest level at the current
+ * pressure, with the feasible set a load step starting from x would use
+ * (c(x) <= c <= 1, clamped u): the reference for pf_rmtr_params.pg_ref.
+ * Synchronises the stream. */
+pf_status pf_projected_gradient(pf_hierarchy* h, const double* x_dev, double* pg_host);
+
 /* Copies the finest-level c_prev (FP64, N values) to c_prev_dev. */
 pf_status pf_get_c_prev(pf_hierarchy* h, double* c_prev_dev);
 
@@ -237,6 +259,71 @@ pf_status pf_energy_noalloc(int dim, const int n[3], double h, double E, double 
  * and writes the achieved rate (flop/s, an FMA counted as 2) to *flops_host.
  * Used as the ALU roofline denominator of the element kernels. */
 pf_status pf_probe_fma(int prec, double* flops_host);
+
+/* ------------------------------------------------------------------------
+ * Learned initial iterate (no counterpart in the paper; the network, its
+ * features and its acceptance test are this library's extension).  A 2D
+ * U-Net proposes each load step's change of state; the proposal is
+ * accepted only through the trust-region ratio (eq. rho_tr) of the FP64
+ * energy, otherwise the plain iterate is kept.
+ * ---------------------------------------------------------------------- */
+typedef struct pf_unet pf_unet;
+
+/* Network on an H x W grid (multiples of 8): 4 levels with channels[0..3],
+ * two 3x3 convolutions + ReLU per level, 2x2 average pooling, nearest 2x
+ * upsampling with skip concatenation [up, skip], 1x1 head; n_in input and
+ * n_out output planes.  BF16 weights/activations, FP32 arithmetic, FP32
+ * master weights.  Parameter vector layout: for every layer in the order
+ * enc0a enc0b ... enc3a enc3b dec2a dec2b dec1a dec1b dec0a dec0b head,
+ * its weights [c_out][c_in][k][k] then its biases [c_out]. */
+pf_status pf_unet_create(int height, int width, int n_in, int n_out, const int channels[4],
+                         void* stream, pf_unet** out);
+pf_status pf_unet_destroy(pf_unet* u);
+pf_status pf_unet_num_params(const pf_unet* u, long long* n);
+/* host FP32 parameter vectors; set also clears the Adam moments and the
+ * accumulated gradient */
+pf_status pf_unet_set_params(pf_unet* u, const float* params_host);
+pf_status pf_unet_get_params(pf_unet* u, float* params_host);
+pf_status pf_unet_get_grads(pf_unet* u, float* grads_host);
+/* y = net(x): x_dev n_in x H x W FP32 planes, y_dev n_out x H x W FP32;
+ * keeps the activations for pf_unet_backward. */
+pf_status pf_unet_forward(pf_unet* u, const float* x_dev, float* y_dev);
+/* adds dL/dparams for dL/dy (FP32, n_out x H x W) at the last forward */
+pf_status pf_unet_backward(pf_unet* u, const float* dy_dev);
+/* masked mean-squared error L = sum mask (y - t)^2 / (2 n_out n_valid);
+ * writes dL/dy to dy_dev and L to *loss_host (mask_dev: H x W, NULL = all
+ * pixels, n_valid its number of ones). */
+pf_status pf_unet_mse(pf_unet* u, const float* y_dev, const float* t_dev, const float* mask_dev,
+                      double n_valid, float* dy_dev, double* loss_host);
+/* one Adam step (Kingma & Ba) with the accumulated gradient times
+ * grad_scale, then clears the gradient */
+pf_status pf_unet_adam(pf_unet* u, float lr, float beta1, float beta2, float eps, float grad_scale);
+
+/* Network input planes (H x W, zero outside the finest 2D grid) from the
+ * previous converged state x_prev (pressure p_prev > 0), the phase field
+ * c_before of the step before it (NULL = c of x_prev) and the new pressure:
+ * [u_x E/p_prev, u_y E/p_prev, c, p_new/p_prev, c - c_before]. */
+pf_status pf_learned_features(pf_hierarchy* h, const double* x_prev_dev, const double* c_before_dev,
+                              double p_prev, double p_new, int H, int W, float* feat_dev);
+/* Training target planes from two converged states: the change beyond the
+ * linear extrapolation r = p_new/p_prev of the displacement,
+ * [(u_new - r u_prev) E/dp (2 planes), (c_new - c_prev)/dp],
+ * dp = p_new - p_prev (p_prev > 0). */
+pf_status pf_learned_target(pf_hierarchy* h, const double* x_prev_dev, const double* x_new_dev,
+                            double p_prev, double p_new, int H, int W, float* target_dev);
+/* Proposal from the network output y (the target's scaling inverted):
+ * xhat = [r u_prev + dp/E y_u, c_prev + dp y_c]; y = 0 gives the linear
+ * extrapolation of the displacement. */
+pf_status pf_learned_apply(pf_hierarchy* h, const double* x_prev_dev, const float* y_dev,
+                           double p_prev, double p_new, int H, int W, double* xhat_dev);
+/* Acceptance test at the current pressure: c_prev := c of x (kept for the
+ * next load step, which must run with keep_c_prev = 1); xhat is projected
+ * onto the feasible set; s = xhat - x; rho = (E(x) - E(x + s)) /
+ * (-(grad E(x).s + s.H(x)s/2)) with FP64 energy difference, gradient and
+ * Hessian; x := x + s when rho > eta and E decreases.  Writes rho and
+ * accepted (0/1). */
+pf_status pf_learned_propose(pf_hierarchy* h, double* x_dev, const double* xhat_dev, double eta,
+                             double* rho_host, int* accepted_host);
 
 #ifdef __cplusplus
 }

@@ -549,6 +549,7 @@ class TRParams:
     coarse_model: int = FIRST_ORDER
     precondition: bool = True   # Jacobi-preconditioned subproblem CG
     max_restarts: int = 1000000  # CG restarts after projected searches, per subproblem
+    pg_ref: float = 0.0         # > 0: stopping test relative to this instead of the start
     level_rtol: float = 1e-3    # non-finest levels stop their TR loop once the
                                 # level's projected gradient fell by this factor
 
@@ -923,11 +924,13 @@ def rmtr_load_step(H: Hierarchy, x, tr: TRParams = None, p=None) -> LoadStepResu
     pg = pg0
     delta = tr.delta0
     cycles = 0
-    converged = pg0 <= tr.atol
+    ref = tr.pg_ref if tr.pg_ref > 0 else pg0
+    target = max(tr.rtol * ref, tr.atol)
+    converged = pg0 <= (target if tr.pg_ref > 0 else tr.atol)
     while not converged and cycles < tr.max_cycles:
         model = LevelModel(H, H.L - 1, x)
         x, delta = vcycle(H, H.L - 1, model, x, lb, ub, delta, tr, stats)
         cycles += 1
         pg = projected_gradient_norm(x, H.df(H.L - 1, x), lb, ub)
-        converged = pg <= max(tr.rtol * pg0, tr.atol)
+        converged = pg <= target
     return LoadStepResult(x, cycles, converged, H.f(H.L - 1, x), pg0, pg, stats)

@@ -17,6 +17,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ENOTCONV, PF_ETIMEOUT, 
 PF_FP64, PF_FP32 = 0, 1
 PF_GALERKIN, PF_FIRST_ORDER = 0, 1
 PF_LINE2D, PF_DISC3D = 0, 1
+PF_START_PLAIN, PF_START_EXTRAPOLATE = 0, 1
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ENONFINITE",
                 5: "PF_ENOTCONV", 6: "PF_ETIMEOUT", 7: "PF_ESTATE"}
@@ -28,7 +29,10 @@ EXPORTS = [
     "pf_energy", "pf_energy_diff", "pf_gradient", "pf_hessvec", "pf_prolong", "pf_restrict",
     "pf_project", "pf_coarse_bounds", "pf_rmtr_load_step", "pf_rmtr_load_step_host",
     "pf_get_c_prev", "pf_probe_fma", "pf_energy_noalloc", "pf_hessvec_lag_set",
-    "pf_hessvec_lagged",
+    "pf_hessvec_lagged", "pf_unet_create", "pf_unet_destroy", "pf_unet_num_params",
+    "pf_unet_set_params", "pf_unet_get_params", "pf_unet_get_grads", "pf_unet_forward",
+    "pf_unet_backward", "pf_unet_mse", "pf_unet_adam", "pf_learned_features", "pf_learned_target",
+    "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient",
 ]
 
 
@@ -48,7 +52,8 @@ class RmtrParams(C.Structure):
                 ("max_cycles", C.c_int), ("rtol", C.c_double), ("atol", C.c_double),
                 ("coarse_model", C.c_int), ("precision", C.c_int),
                 ("precondition", C.c_int), ("level_rtol", C.c_double),
-                ("max_restarts", C.c_int)]
+                ("max_restarts", C.c_int), ("keep_c_prev", C.c_int), ("pg_ref", C.c_double),
+                ("start", C.c_int), ("p_prev", C.c_double)]
 
 
 class RmtrStats(C.Structure):
@@ -104,6 +109,21 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_energy_noalloc": (i, [i, C.POINTER(C.c_int), d, d, d, d, d, d, d, vp, i, vp, vp]),
         "pf_hessvec_lag_set": (i, [vp, i, vp, i]),
         "pf_hessvec_lagged": (i, [vp, i, vp, vp, i]),
+        "pf_unet_create": (i, [i, i, i, i, C.POINTER(C.c_int), vp, C.POINTER(vp)]),
+        "pf_unet_destroy": (i, [vp]),
+        "pf_unet_num_params": (i, [vp, C.POINTER(C.c_longlong)]),
+        "pf_unet_set_params": (i, [vp, vp]),
+        "pf_unet_get_params": (i, [vp, vp]),
+        "pf_unet_get_grads": (i, [vp, vp]),
+        "pf_unet_forward": (i, [vp, vp, vp]),
+        "pf_unet_backward": (i, [vp, vp]),
+        "pf_unet_mse": (i, [vp, vp, vp, vp, d, vp, C.POINTER(d)]),
+        "pf_unet_adam": (i, [vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
+        "pf_learned_features": (i, [vp, vp, vp, d, d, i, i, vp]),
+        "pf_learned_target": (i, [vp, vp, vp, d, d, i, i, vp]),
+        "pf_learned_apply": (i, [vp, vp, vp, d, d, i, i, vp]),
+        "pf_learned_propose": (i, [vp, vp, vp, d, C.POINTER(d), C.POINTER(C.c_int)]),
+        "pf_projected_gradient": (i, [vp, vp, C.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -330,6 +350,13 @@ def rmtr_load_step_host(H: Hierarchy, x: np.ndarray, params: RmtrParams | None =
     return d
 
 
+def projected_gradient(H: Hierarchy, x) -> float:
+    import torch
+    out = C.c_double()
+    _check(lib().pf_projected_gradient(H.handle, _dev(x, H.ndof(), torch.float64), C.byref(out)))
+    return out.value
+
+
 def get_c_prev(H: Hierarchy):
     import torch
     out = torch.empty(H.nodes(), dtype=torch.float64, device="cuda")
@@ -354,3 +381,114 @@ def energy_noalloc(dim, n, h, E, nu, Gc, ls, k_res, p, x, out, stream=None):
     _check(lib().pf_energy_noalloc(dim, nn, h, E, nu, Gc, ls, k_res, p, _dev(x), _prec(x),
                                    _dev(out, 1, torch.float64), C.c_void_p(stream.cuda_stream)))
     return out
+
+
+# ------------------------------------------------------------------ learned iterate
+class Unet:
+    """Owns a pf_unet* (the learned initial-iterate network)."""
+
+    def __init__(self, height, width, n_in=5, n_out=3, channels=(16, 32, 64, 128), stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.H, self.W, self.n_in, self.n_out = height, width, n_in, n_out
+        ch = (C.c_int * 4)(*channels)
+        h = C.c_void_p()
+        _check(lib().pf_unet_create(height, width, n_in, n_out, ch, C.c_void_p(stream.cuda_stream),
+                                    C.byref(h)))
+        self.handle = h
+        n = C.c_longlong()
+        _check(lib().pf_unet_num_params(h, C.byref(n)))
+        self.n_params = n.value
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        if flat.size != self.n_params:
+            raise ValueError("parameter vector has the wrong size")
+        _check(lib().pf_unet_set_params(self.handle, flat.ctypes.data_as(C.c_void_p)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().pf_unet_get_params(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def get_grads(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().pf_unet_get_grads(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def forward(self, x, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.n_out, self.H, self.W), dtype=torch.float32, device="cuda")
+        _check(lib().pf_unet_forward(self.handle, _dev(x, self.n_in * self.H * self.W, torch.float32),
+                                     _dev(out, self.n_out * self.H * self.W, torch.float32)))
+        return out
+
+    def backward(self, dy):
+        import torch
+        _check(lib().pf_unet_backward(self.handle, _dev(dy, self.n_out * self.H * self.W, torch.float32)))
+
+    def mse(self, y, t, mask=None, n_valid=None, dy=None):
+        import torch
+        if dy is None:
+            dy = torch.empty_like(y)
+        loss = C.c_double()
+        m = _dev(mask, self.H * self.W, torch.float32) if mask is not None else None
+        nv = float(n_valid) if mask is not None else 1.0
+        _check(lib().pf_unet_mse(self.handle, _dev(y), _dev(t), m, nv, _dev(dy), C.byref(loss)))
+        return loss.value, dy
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0):
+        _check(lib().pf_unet_adam(self.handle, lr, beta1, beta2, eps, grad_scale))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pf_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def learned_features(H: Hierarchy, x_prev, c_before, p_prev, p_new, height, width, out=None):
+    import torch
+    if out is None:
+        out = torch.empty((5, height, width), dtype=torch.float32, device="cuda")
+    cb = _dev(c_before, H.nodes(), torch.float64) if c_before is not None else None
+    _check(lib().pf_learned_features(H.handle, _dev(x_prev, H.ndof(), torch.float64), cb, p_prev, p_new,
+                                     height, width, _dev(out, 5 * height * width, torch.float32)))
+    return out
+
+
+def learned_target(H: Hierarchy, x_prev, x_new, p_prev, p_new, height, width, out=None):
+    import torch
+    if out is None:
+        out = torch.empty((3, height, width), dtype=torch.float32, device="cuda")
+    _check(lib().pf_learned_target(H.handle, _dev(x_prev, H.ndof(), torch.float64),
+                                   _dev(x_new, H.ndof(), torch.float64), p_prev, p_new, height, width,
+                                   _dev(out, 3 * height * width, torch.float32)))
+    return out
+
+
+def learned_apply(H: Hierarchy, x_prev, y, p_prev, p_new, out=None):
+    import torch
+    if out is None:
+        out = torch.empty_like(x_prev)
+    _check(lib().pf_learned_apply(H.handle, _dev(x_prev, H.ndof(), torch.float64),
+                                  _dev(y, None, torch.float32), p_prev, p_new, y.shape[1], y.shape[2],
+                                  _dev(out, H.ndof(), torch.float64)))
+    return out
+
+
+def learned_propose(H: Hierarchy, x, xhat, eta=0.1):
+    import torch
+    rho = C.c_double()
+    acc = C.c_int()
+    _check(lib().pf_learned_propose(H.handle, _dev(x, H.ndof(), torch.float64),
+                                    _dev(xhat, H.ndof(), torch.float64), eta, C.byref(rho), C.byref(acc)))
+    return rho.value, bool(acc.value)

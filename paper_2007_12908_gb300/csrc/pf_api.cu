@@ -71,6 +71,10 @@ void pf_rmtr_params_default(pf_rmtr_params* p) {
   p->precondition = 1;
   p->level_rtol = 1e-3;
   p->max_restarts = 1000000;
+  p->keep_c_prev = 0;
+  p->pg_ref = 0.0;
+  p->start = PF_START_PLAIN;
+  p->p_prev = 0.0;
 }
 
 const char* pf_last_error(void) { return g_last_error.c_str(); }
@@ -240,6 +244,7 @@ pf_status pf_fractures_set(pf_hierarchy* h, int kind, int n, const double* rows,
     return PF_ECUDA;
   }
   h->have_fractures = true;
+  h->p_last = 0.0;
   return PF_OK;
 }
 
@@ -370,7 +375,8 @@ static pf_status check_params(const pf_rmtr_params& P) {
       (P.coarse_model != PF_GALERKIN && P.coarse_model != PF_FIRST_ORDER) ||
       (P.precision != PF_FP64 && P.precision != PF_FP32) ||
       (P.precondition != 0 && P.precondition != 1) || !(P.level_rtol >= 0 && P.level_rtol < 1) ||
-      P.max_restarts < 0)
+      P.max_restarts < 0 || (P.keep_c_prev != 0 && P.keep_c_prev != 1) || !(P.pg_ref >= 0) ||
+      (P.start != PF_START_PLAIN && P.start != PF_START_EXTRAPOLATE) || !(P.p_prev >= 0))
     return bad("rmtr_load_step: invalid parameters");
   return PF_OK;
 }
@@ -403,6 +409,11 @@ pf_status pf_rmtr_load_step_host(pf_hierarchy* h, double* x_host, const pf_rmtr_
               "rmtr_load_step_host");
   PF_TRY_CUDA(cudaStreamSynchronize(h->st), "rmtr_load_step_host");
   return rc;
+}
+
+pf_status pf_projected_gradient(pf_hierarchy* h, const double* x, double* pg) {
+  if (!h || !x || !pg) return bad("projected_gradient: null argument");
+  return projected_gradient_impl(h, x, pg);
 }
 
 pf_status pf_get_c_prev(pf_hierarchy* h, double* out) {

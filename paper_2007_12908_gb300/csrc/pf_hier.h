@@ -51,6 +51,7 @@ struct pf_hierarchy {
   std::vector<pf::Geom> geo;
   std::vector<pf::Mat<double>> mat;  // per level (ls = ls_over_h * h_finest)
   double E = 1, nu = 0.3, Gc = 1, ls = 0, k_res = 0, p = 0;
+  double p_last = 0;  // pressure of the last converged load step (0 = none)
   cudaStream_t st = nullptr;
   pf::Scratch scratch{nullptr, nullptr};
   double* d_res = nullptr;  // device result slots
@@ -66,5 +67,6 @@ struct pf_hierarchy {
 namespace pf {
 pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_params& P,
                               pf_rmtr_stats* stats);
+pf_status projected_gradient_impl(pf_hierarchy* H, const double* x_dev, double* out);
 void refresh_pressure(pf_hierarchy* H);
 }  // namespace pf

@@ -111,6 +111,9 @@ struct Solver {
   cudaStream_t st;
   int L, F;
   bool mixed;
+  // the finest level's B.g holds grad f at its current B.x (set by pg_norm,
+  // cleared whenever that x or the gradient buffer changes)
+  bool fine_grad_valid = false;
 
   Solver(pf_hierarchy* h, const pf_rmtr_params& p, pf_rmtr_stats& s)
       : H(h), P(p), S(s), st(h->st), L(h->L), F(h->dim + 1), mixed(p.precision == PF_FP32) {}
@@ -542,7 +545,8 @@ struct Solver {
     LevelBuf& B = H->lv[l];
     double chi0 = -1.0;
     for (int it = 0; it < iters; ++it) {
-      grad_h(l, B.x, B.g);
+      if (!(finest(l) && fine_grad_valid)) grad_h(l, B.x, B.g);
+      fine_grad_valid = false;
       if (P.level_rtol > 0.0 && !finest(l)) {
         // stop once the level's projected gradient fell by level_rtol
         const double chi = pg_norm_level(l);
@@ -644,6 +648,7 @@ struct Solver {
   double pg_norm(const double* x) {
     LevelBuf& B = H->lv[L - 1];
     gradient(L - 1, x, B.g);
+    fine_grad_valid = (x == B.x);
     const double *g = B.g, *lb = B.lb, *ub = B.ub;
     double r;
     reduce<1, OpSum>(B.n, [=] __device__(long long i, double(&v)[1]) {
@@ -653,14 +658,56 @@ struct Solver {
     return std::sqrt(r);
   }
 
+  // projected gradient at x for the feasible set c(x) <= c <= 1, clamped u
+  double pg_at(const double* x_user) {
+    LevelBuf& B = H->lv[L - 1];
+    const Geom g = H->geo[L - 1];
+    const long long N = g.N;
+    const int dim = H->dim;
+    copy(B.t3, x_user, B.n);
+    {
+      double *lb = B.lb, *ub = B.ub;
+      const double* x = B.t3;
+      map(B.n, [=] __device__(long long i) {
+        const int f = int(i / N);
+        const long long k = i - f * N;
+        double l, u;
+        if (f == dim) {
+          l = x[dim * N + k];
+          u = 1.0;
+        } else if (on_boundary(g, k)) {
+          l = 0.0;
+          u = 0.0;
+        } else {
+          l = -INFINITY;
+          u = INFINITY;
+        }
+        lb[i] = l;
+        ub[i] = u;
+      });
+    }
+    return pg_norm(B.t3);
+  }
+
   pf_status run(double* x_user) {
     LevelBuf& B = H->lv[L - 1];
     const Geom g = H->geo[L - 1];
     const long long N = g.N;
     const int dim = H->dim;
+    double pg_ref = P.pg_ref;
+    const double p_before = P.p_prev > 0.0 ? P.p_prev : H->p_last;
+    if (P.start == PF_START_EXTRAPOLATE && p_before > 0.0 && H->p != p_before) {
+      // the displacement is nearly linear in p: start from u p / p_last, c
+      // unchanged, and stop at the accuracy of the plain start
+      if (!(pg_ref > 0.0)) pg_ref = pg_at(x_user);
+      const double r = H->p / p_before;
+      double* xu = x_user;
+      map((long long)dim * N, [=] __device__(long long i) { xu[i] *= r; });
+    }
     copy(B.x, x_user, B.n);
-    // c_prev := c ; finest bounds of eq. (space_pf), clamped displacement
-    copy(H->c_prev, B.x + dim * N, N);
+    // c_prev := c (unless kept from an accepted proposal); finest bounds of
+    // eq. (space_pf), clamped displacement
+    if (!P.keep_c_prev) copy(H->c_prev, B.x + dim * N, N);
     {
       double *lb = B.lb, *ub = B.ub, *x = B.x;
       const double* cp = H->c_prev;
@@ -692,14 +739,16 @@ struct Solver {
     double pg = pg0;
     double delta = P.delta0;
     int cycles = 0;
-    bool conv = pg0 <= P.atol;
+    const double ref = pg_ref > 0.0 ? pg_ref : pg0;
+    const double target = std::max(P.rtol * ref, P.atol);
+    bool conv = pg0 <= (pg_ref > 0.0 ? target : P.atol);
     while (!conv && cycles < P.max_cycles) {
       set_lag(L - 1, B.x);
       vcycle(L - 1, delta);
       ++cycles;
       pg = pg_norm(B.x);
       if (!std::isfinite(pg)) break;
-      conv = pg <= std::max(P.rtol * pg0, P.atol);
+      conv = pg <= target;
     }
     S.cycles = cycles;
     S.converged = conv ? 1 : 0;
@@ -709,9 +758,24 @@ struct Solver {
     copy(x_user, B.x, B.n);
     ck(cudaStreamSynchronize(st), "sync");
     if (!std::isfinite(pg)) return PF_ENONFINITE;
+    if (conv) H->p_last = H->p;
     return conv ? PF_OK : PF_ENOTCONV;
   }
 };
+
+pf_status projected_gradient_impl(pf_hierarchy* H, const double* x_dev, double* out) {
+  pf_rmtr_stats S{};
+  pf_rmtr_params P;
+  pf_rmtr_params_default(&P);
+  try {
+    Solver solver(H, P, S);
+    *out = solver.pg_at(x_dev);
+  } catch (const CudaFail& f) {
+    set_error(std::string("CUDA error in ") + f.where + ": " + cudaGetErrorString(f.e));
+    return PF_ECUDA;
+  }
+  return std::isfinite(*out) ? PF_OK : PF_ENONFINITE;
+}
 
 pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_params& P,
                               pf_rmtr_stats* stats) {
