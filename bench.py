@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--coarse-n", type=int, default=17,
                     help="coarsest nodes per axis (17 = the 129^3 workload)")
     ap.add_argument("--coarse-model", choices=["first_order", "galerkin"], default="first_order")
+    ap.add_argument("--batched", action="store_true",
+                    help="the uneven 2D batch (64 instances, 129^2 .. 1025^2) instead of the 3D workload")
+    ap.add_argument("--batch-threads", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -434,10 +437,74 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Load steps of 64 uneven 2D instances (16 each of 129^2, 257^2, 513^2,
+    1025^2 nodes; 10-1000 line fractures, +-30 deg families) run
+    concurrently, each on its own stream, by the library's host workers."""
+    import torch
+    from paper_2007_12908_gb300 import build
+    build.build()
+    import paper_2007_12908_gb300 as pf
+    sizes, counts = PI.batched_grid_draw(PI.SEED_2D_BATCHED, 64)
+    prm = pf.default_params(precision=pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64,
+                            start=pf.PF_START_EXTRAPOLATE if args.start == "extrapolate" else pf.PF_START_PLAIN)
+    Hs, xs = [], []
+    for i, (n, nf) in enumerate(zip(sizes, counts)):
+        levels = int(round(np.log2((n - 1) / 16))) + 1
+        st = torch.cuda.Stream()
+        H = pf.mesh_hierarchy_create(2, (17, 17), levels, 1 / 16, E=1.0, nu=0.3, Gc=1.0, stream=st)
+        x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        pf.fractures_set(H, pf.PF_LINE2D, PI.line_network_2d(PI.SEED_2D_BATCHED + 1 + i, nf),
+                         H.levels[-1][1], x)
+        Hs.append(H)
+        xs.append(x)
+    dofs = sum(H.ndof() for H in Hs)
+
+    def step(t, threads):
+        for H in Hs:
+            pf.pressure_set(H, 1e-3 * t)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = pf.rmtr_load_step_batch(Hs, xs, prm, n_threads=threads, check=False)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    for t in range(1, args.warmup + 1):
+        step(t, args.batch_threads)
+    clocks = Clocks(0)
+    clocks.start()
+    times, outs = [], []
+    for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+        dt, out = step(t, args.batch_threads)
+        times.append(dt)
+        outs.append(out)
+    clk = clocks.stop()
+    sec = statistics.mean(times)
+    line = {
+        "metric": "batched RMTR load steps: GDoF/s over 64 uneven 2D instances",
+        "value": dofs / sec / 1e9, "unit": "GDoF/s (load steps)", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "config": {"workload": "2d_batched_64_uneven_129-1025", "instances": len(Hs), "dofs": dofs,
+                   "sizes": sizes, "fractures": counts, "precision": args.precision,
+                   "start": args.start, "threads": args.batch_threads or len(Hs)},
+        "instances_per_s": len(Hs) / sec,
+        "converged": [sum(o["converged"] for o in out) for out in outs],
+        "cycles_mean": [statistics.mean(o["cycles"] for o in out) for out in outs],
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched:
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -226,6 +226,18 @@ pf_status pf_rmtr_load_step_host(pf_hierarchy* h, double* x_host, const pf_rmtr_
  * Synchronises the stream. */
 pf_status pf_projected_gradient(pf_hierarchy* h, const double* x_dev, double* pg_host);
 
+/* Batched load steps: one load step of each of n independent instances
+ * (hierarchies of any sizes, each with its own stream; hierarchies sharing a
+ * stream serialise), run concurrently by n_threads host workers of the
+ * library (<= 0: one per instance, at most 64), largest instances first.
+ * xs[i] is the finest FP64 state of hs[i] (device).  params (NULL =
+ * defaults) apply to every instance; stats[i] and status[i] (either may be
+ * NULL) receive each instance's outcome.  Returns PF_OK if every instance
+ * converged, else the first non-OK status in instance order. */
+pf_status pf_rmtr_load_step_batch(int n, pf_hierarchy* const* hs, double* const* xs,
+                                  const pf_rmtr_params* params, int n_threads,
+                                  pf_rmtr_stats* stats, pf_status* status);
+
 /* Copies the finest-level c_prev (FP64, N values) to c_prev_dev. */
 pf_status pf_get_c_prev(pf_hierarchy* h, double* c_prev_dev);
 

@@ -32,7 +32,7 @@ EXPORTS = [
     "pf_hessvec_lagged", "pf_unet_create", "pf_unet_destroy", "pf_unet_num_params",
     "pf_unet_set_params", "pf_unet_get_params", "pf_unet_get_grads", "pf_unet_forward",
     "pf_unet_backward", "pf_unet_mse", "pf_unet_adam", "pf_learned_features", "pf_learned_target",
-    "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient",
+    "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient", "pf_rmtr_load_step_batch",
 ]
 
 
@@ -124,6 +124,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_learned_apply": (i, [vp, vp, vp, d, d, i, i, vp]),
         "pf_learned_propose": (i, [vp, vp, vp, d, C.POINTER(d), C.POINTER(C.c_int)]),
         "pf_projected_gradient": (i, [vp, vp, C.POINTER(d)]),
+        "pf_rmtr_load_step_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(RmtrParams), i,
+                                        C.POINTER(RmtrStats), C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -355,6 +357,27 @@ def projected_gradient(H: Hierarchy, x) -> float:
     out = C.c_double()
     _check(lib().pf_projected_gradient(H.handle, _dev(x, H.ndof(), torch.float64), C.byref(out)))
     return out.value
+
+
+def rmtr_load_step_batch(Hs, xs, params: RmtrParams | None = None, n_threads=0, check=True):
+    """One load step of every (hierarchy, state) pair, run concurrently by the
+    library's host workers; each hierarchy should own its stream."""
+    import torch
+    n = len(Hs)
+    hv = (C.c_void_p * n)(*[H.handle for H in Hs])
+    xv = (C.c_void_p * n)(*[_dev(x, H.ndof(), torch.float64).value for H, x in zip(Hs, xs)])
+    st = (RmtrStats * n)()
+    status = (C.c_int * n)()
+    p = params if params is not None else default_params()
+    rc = lib().pf_rmtr_load_step_batch(n, hv, xv, C.byref(p), n_threads, st, status)
+    if check and rc != PF_OK:
+        _check(rc)
+    out = []
+    for i in range(n):
+        d = st[i].as_dict()
+        d["status"] = status[i]
+        out.append(d)
+    return out
 
 
 def get_c_prev(H: Hierarchy):

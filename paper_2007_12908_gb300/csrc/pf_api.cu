@@ -1,7 +1,12 @@
 // C-ABI of libpf: argument checks, hierarchy set-up and dispatch to kernels.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <numeric>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "pf_hier.h"
 
@@ -408,6 +413,55 @@ pf_status pf_rmtr_load_step_host(pf_hierarchy* h, double* x_host, const pf_rmtr_
   PF_TRY_CUDA(cudaMemcpyAsync(x_host, stage, sizeof(double) * B.n, cudaMemcpyDeviceToHost, h->st),
               "rmtr_load_step_host");
   PF_TRY_CUDA(cudaStreamSynchronize(h->st), "rmtr_load_step_host");
+  return rc;
+}
+
+pf_status pf_rmtr_load_step_batch(int n, pf_hierarchy* const* hs, double* const* xs,
+                                  const pf_rmtr_params* params, int n_threads,
+                                  pf_rmtr_stats* stats, pf_status* status) {
+  if (n < 0 || (n > 0 && (!hs || !xs))) return bad("rmtr_load_step_batch: bad argument");
+  for (int i = 0; i < n; ++i)
+    if (!hs[i] || !xs[i]) return bad("rmtr_load_step_batch: null instance");
+  pf_rmtr_params P;
+  if (params) P = *params;
+  else pf_rmtr_params_default(&P);
+  if (check_params(P)) return PF_EINVAL;
+  if (n == 0) return PF_OK;
+  int dev = 0;
+  PF_TRY_CUDA(cudaGetDevice(&dev), "rmtr_load_step_batch");
+  // largest instances first (longest-processing-time order)
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return hs[a]->lv.back().n > hs[b]->lv.back().n;
+  });
+  std::vector<pf_status> st(n, PF_OK);
+  std::vector<pf_rmtr_stats> ss(n);
+  std::vector<std::string> errs(n);
+  std::atomic<int> next{0};
+  const int nt = std::max(1, std::min(n_threads > 0 ? n_threads : n, std::min(n, 64)));
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n) break;
+      const int i = order[k];
+      st[i] = rmtr_load_step_impl(hs[i], xs[i], P, &ss[i]);
+      if (st[i] != PF_OK) errs[i] = pf_last_error();
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  pf_status rc = PF_OK;
+  for (int i = 0; i < n; ++i) {
+    if (stats) stats[i] = ss[i];
+    if (status) status[i] = st[i];
+    if (rc == PF_OK && st[i] != PF_OK) {
+      rc = st[i];
+      set_error("rmtr_load_step_batch: instance " + std::to_string(i) + ": " + errs[i]);
+    }
+  }
   return rc;
 }
 

@@ -102,3 +102,11 @@ def test_defaults_and_validation_on_host(lib):
     assert lib.pf_hessvec(None, 0, None, None, None, 0) == B.PF_EINVAL
     assert lib.pf_rmtr_load_step(None, None, None, None) == B.PF_EINVAL
     assert lib.pf_mesh_hierarchy_destroy(None) == B.PF_OK
+
+
+def test_batch_validation_on_host(lib):
+    assert lib.pf_rmtr_load_step_batch(-1, None, None, None, 0, None, None) == B.PF_EINVAL
+    hv = (C.c_void_p * 1)(None)
+    xv = (C.c_void_p * 1)(None)
+    assert lib.pf_rmtr_load_step_batch(1, hv, xv, None, 0, None, None) == B.PF_EINVAL
+    assert lib.pf_rmtr_load_step_batch(0, None, None, None, 0, None, None) == B.PF_OK
