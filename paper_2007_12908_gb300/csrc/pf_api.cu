@@ -298,7 +298,12 @@ pf_status pf_energy_diff(pf_hierarchy* h, int level, const void* x, const void* 
 pf_status pf_gradient(pf_hierarchy* h, int level, const void* x, void* g, int prec) {
   if (!valid_level(h, level) || !x || !g) return bad("gradient: bad argument");
   if (check_prec(prec)) return PF_EINVAL;
-  PF_TRY_CUDA(elem_gradient(h->geo[level], h->mat[level], x, g, prec, h->st), "gradient");
+  if (prec == PF_FP64)
+    PF_TRY_CUDA(elem_gradient_fp64(h->geo[level], h->mat[level], static_cast<const double*>(x),
+                                   static_cast<double*>(g), h->lv[level].coef, h->st),
+                "gradient");
+  else
+    PF_TRY_CUDA(elem_gradient(h->geo[level], h->mat[level], x, g, prec, h->st), "gradient");
   return PF_OK;
 }
 

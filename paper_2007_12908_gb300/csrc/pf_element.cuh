@@ -81,9 +81,10 @@ __device__ __forceinline__ void interp3(const T f[8], T val[8], T gx[8], T gy[8]
 }
 
 // r[a] = sum_q s0[q] N_a(q) + sx[q] Dx_a(q) + sy[q] Dy_a(q) + sz[q] Dz_a(q)
-// (raw derivatives), the adjoint of interp3.
+// (raw derivatives), the adjoint of interp3.  s0 == nullptr drops the value
+// term (IEEE arithmetic cannot fold multiplications by a zero term away).
 template <class T>
-__device__ __forceinline__ void test3(const T s0[8], const T sx[8], const T sy[8], const T sz[8],
+__device__ __forceinline__ void test3(const T* s0, const T sx[8], const T sy[8], const T sz[8],
                                       T r[8]) {
   const T x0 = T(PF_XI0), x1 = T(PF_XI1);
   T XYb[2][2][2], DXYb[2][2], DYb[2][2];
@@ -93,8 +94,13 @@ __device__ __forceinline__ void test3(const T s0[8], const T sx[8], const T sy[8
     for (int qx = 0; qx < 2; ++qx) {
       const int q = qx + 2 * qy;
       const T zs = sz[q] + sz[q + 4];
-      XYb[qx][qy][0] = x1 * s0[q] + x0 * s0[q + 4] - zs;
-      XYb[qx][qy][1] = x0 * s0[q] + x1 * s0[q + 4] + zs;
+      if (s0) {
+        XYb[qx][qy][0] = x1 * s0[q] + x0 * s0[q + 4] - zs;
+        XYb[qx][qy][1] = x0 * s0[q] + x1 * s0[q + 4] + zs;
+      } else {
+        XYb[qx][qy][0] = -zs;
+        XYb[qx][qy][1] = zs;
+      }
     }
 #pragma unroll
   for (int qy = 0; qy < 2; ++qy) {
@@ -154,14 +160,19 @@ __device__ __forceinline__ void interp2(const T f[4], T val[4], T gx[4], T gy[4]
 }
 
 template <class T>
-__device__ __forceinline__ void test2(const T s0[4], const T sx[4], const T sy[4], T r[4]) {
+__device__ __forceinline__ void test2(const T* s0, const T sx[4], const T sy[4], T r[4]) {
   const T x0 = T(PF_XI0), x1 = T(PF_XI1);
   T Xb[2][2];
 #pragma unroll
   for (int qx = 0; qx < 2; ++qx) {
     const T ys = sy[qx] + sy[qx + 2];
-    Xb[qx][0] = x1 * s0[qx] + x0 * s0[qx + 2] - ys;
-    Xb[qx][1] = x0 * s0[qx] + x1 * s0[qx + 2] + ys;
+    if (s0) {
+      Xb[qx][0] = x1 * s0[qx] + x0 * s0[qx + 2] - ys;
+      Xb[qx][1] = x0 * s0[qx] + x1 * s0[qx + 2] + ys;
+    } else {
+      Xb[qx][0] = -ys;
+      Xb[qx][1] = ys;
+    }
   }
   const T a = sx[0] + sx[1], b = sx[2] + sx[3];
   const T DXb0 = x1 * a + x0 * b, DXb1 = x0 * a + x1 * b;
@@ -294,7 +305,8 @@ struct StrainSym {
   }
 };
 
-// Quartic coefficients of E_e(x + t s) - E_e(x).
+// Quartic coefficients of E_e(x + t s) - E_e(x).  Gradients stay raw nodal
+// differences; 1/h and 1/h^2 are folded into the constants.
 template <int D, class T>
 __device__ __forceinline__ void elem_energy_diff(const T (*xe)[1 << D], const T (*se)[1 << D],
                                                  const Mat<T>& m, T a[4]) {
@@ -310,6 +322,9 @@ __device__ __forceinline__ void elem_energy_diff(const T (*xe)[1 << D], const T 
   interp<D, T>(se[D], sc, gsc);
   T a1 = 0, a2 = 0, a3 = 0, a4 = 0;
   const T omk = T(1) - m.k;
+  const T ih2 = m.inv_h * m.inv_h;
+  const T hl = T(0.5) * m.lam * ih2, lam2 = m.lam * ih2, mu2 = m.mu * ih2, ph = m.p * m.inv_h;
+  const T gls = m.Gc * m.ls * ih2, hgls = T(0.5) * gls, gcl = m.Gc / m.ls, hgcl = T(0.5) * gcl;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     T G[D][D], Gs[D][D];
@@ -317,20 +332,20 @@ __device__ __forceinline__ void elem_energy_diff(const T (*xe)[1 << D], const T 
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        G[i][k] = gu[i][k][q] * m.inv_h;
-        Gs[i][k] = gs[i][k][q] * m.inv_h;
+        G[i][k] = gu[i][k][q];
+        Gs[i][k] = gs[i][k][q];
       }
     StrainSym<D, T> e0, e1;
     e0.set(G);
     e1.set(Gs);
-    T e01 = T(0);  // eps(u) : eps(s)
+    T e01 = T(0);  // eps(u) : eps(s), raw
 #pragma unroll
     for (int i = 0; i < D; ++i) e01 += G[i][i] * Gs[i][i];
 #pragma unroll
     for (int j = 0; j < (D == 3 ? 3 : 1); ++j) e01 += T(0.5) * e0.off[j] * e1.off[j];
-    const T psi0 = T(0.5) * m.lam * e0.tr * e0.tr + m.mu * e0.ee;
-    const T psi2 = T(0.5) * m.lam * e1.tr * e1.tr + m.mu * e1.ee;
-    const T psi1 = m.lam * e0.tr * e1.tr + T(2) * m.mu * e01;
+    const T psi0 = hl * e0.tr * e0.tr + mu2 * e0.ee;
+    const T psi2 = hl * e1.tr * e1.tr + mu2 * e1.ee;
+    const T psi1 = lam2 * e0.tr * e1.tr + T(2) * mu2 * e01;
     const T omc = T(1) - cv[q], s = sc[q];
     const T g0 = omk * omc * omc + m.k;
     const T g1 = T(-2) * omk * omc * s;
@@ -342,12 +357,10 @@ __device__ __forceinline__ void elem_energy_diff(const T (*xe)[1 << D], const T 
       cg += u * v;
       gg += v * v;
     }
-    const T ih2 = m.inv_h * m.inv_h;
-    a1 += g0 * psi1 + g1 * psi0 + m.p * (g0 * e1.tr + g1 * e0.tr) +
-          m.Gc * (cv[q] * s / m.ls + m.ls * ih2 * cg);
-    a2 += g0 * psi2 + g1 * psi1 + g2 * psi0 + m.p * (g1 * e1.tr + g2 * e0.tr) +
-          T(0.5) * m.Gc * (s * s / m.ls + m.ls * ih2 * gg);
-    a3 += g1 * psi2 + g2 * psi1 + m.p * g2 * e1.tr;
+    const T t0 = ph * e0.tr, t1 = ph * e1.tr;
+    a1 += g0 * psi1 + g1 * psi0 + (g0 * t1 + g1 * t0) + gcl * cv[q] * s + gls * cg;
+    a2 += g0 * psi2 + g1 * psi1 + g2 * psi0 + (g1 * t1 + g2 * t0) + hgcl * s * s + hgls * gg;
+    a3 += g1 * psi2 + g2 * psi1 + g2 * t1;
     a4 += g2 * psi2;
   }
   a[0] = m.w * a1; a[1] = m.w * a2; a[2] = m.w * a3; a[3] = m.w * a4;
@@ -363,12 +376,11 @@ __device__ __forceinline__ void elem_gradient(const T (*xe)[1 << D], const Mat<T
 #pragma unroll
   for (int i = 0; i < D; ++i) interp<D, T>(xe[i], dummy, gu[i]);
   interp<D, T>(xe[D], cv, gc);
-  T su[D][D][NQ], s0[NQ], sc[D][NQ], zero[NQ];
+  T su[D][D][NQ], s0[NQ], sc[D][NQ];
   const T omk = T(1) - m.k;
   const T kc = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    zero[q] = T(0);
     T G[D][D];
 #pragma unroll
     for (int i = 0; i < D; ++i)
@@ -398,7 +410,7 @@ __device__ __forceinline__ void elem_gradient(const T (*xe)[1 << D], const Mat<T
     for (int k = 0; k < D; ++k) sc[k][q] = kc * gc[k][q];
   }
 #pragma unroll
-  for (int i = 0; i < D; ++i) test<D, T>(zero, su[i], out[i]);
+  for (int i = 0; i < D; ++i) test<D, T>(nullptr, su[i], out[i]);
   test<D, T>(s0, sc, out[D]);
 }
 
@@ -465,7 +477,7 @@ template <int D, class T>
 __device__ __forceinline__ void hess_apply(const T (*ve)[1 << D], const T (*cf)[NCoef<D>::value],
                                            const Mat<T>& m, T (*out)[1 << D]) {
   constexpr int NQ = 1 << D;
-  T su[D][D][NQ], s0[NQ], sc[D][NQ], zero[NQ];
+  T su[D][D][NQ], s0[NQ], sc[D][NQ];
   {
     T gv[D][D][NQ], vc[NQ], gvc[D][NQ], dummy[NQ];
 #pragma unroll
@@ -474,8 +486,7 @@ __device__ __forceinline__ void hess_apply(const T (*ve)[1 << D], const T (*cf)[
     const T kc = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      zero[q] = T(0);
-      const T A = cf[q][0], M = cf[q][1];
+        const T A = cf[q][0], M = cf[q][1];
       T trr = T(0);
 #pragma unroll
       for (int i = 0; i < D; ++i) trr += gv[i][i][q];
@@ -502,7 +513,7 @@ __device__ __forceinline__ void hess_apply(const T (*ve)[1 << D], const T (*cf)[
     }
   }
 #pragma unroll
-  for (int i = 0; i < D; ++i) test<D, T>(zero, su[i], out[i]);
+  for (int i = 0; i < D; ++i) test<D, T>(nullptr, su[i], out[i]);
   test<D, T>(s0, sc, out[D]);
 }
 

@@ -43,6 +43,11 @@ cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x,
                              int prec, const Scratch& s, double* out_dev, cudaStream_t st);
 cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, void* y, int prec,
                           cudaStream_t st);
+// FP64 gradient evaluating every element once: corner contributions go to
+// scratch (NE * 2^d * (d+1) doubles, e.g. a level's coefficient buffer),
+// then each node sums its elements' in a fixed order.
+cudaError_t elem_gradient_fp64(const Geom& g, const Mat<double>& m, const double* x, double* y,
+                               double* scratch, cudaStream_t st);
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
                          void* y, int prec, cudaStream_t st, const int* skip = nullptr);
 // FP64 lagged Hessian: Gauss-point coefficients of x (coef holds

@@ -8,9 +8,11 @@
 // phase).  Each owned node therefore receives its element contributions in
 // a fixed order: results are bitwise reproducible, with no atomics.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 
+#include "pf_element_f2.cuh"
 #include "pf_internal.h"
 #include "pf_reduce.cuh"
 
@@ -178,8 +180,10 @@ __global__ void __launch_bounds__(256) k_hess_coef(Geom g, Mat<T> m, const T* __
 // TC: compute precision (and that of x); TIO: precision of v and y.
 // skip: when non-null and *skip != 0 the launch does nothing (the solver's
 // device-side CG stops this way without a host round trip).
+// FP32 instances are limited to 128 registers so that two CTAs (16 warps)
+// share an SM and hide the gather and barrier latency.
 template <int D, class TC, class TIO, int OP>
-__global__ void __launch_bounds__(Tile<D>::THREADS)
+__global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
     k_elem_scatter(Geom g, Mat<TC> m, const TC* __restrict__ x, const TIO* __restrict__ v,
                    TIO* __restrict__ y, const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -209,7 +213,10 @@ __global__ void __launch_bounds__(Tile<D>::THREADS)
 #pragma unroll
           for (int f = 0; f < F; ++f) ve[f][a] = TC(v[f * g.N + idx]);
         }
-        elem_hessvec<D, TC>(xe, ve, m, out);
+        if constexpr (D == 3 && std::is_same<TC, float>::value)
+          p2::elem_hessvec(xe, ve, m, out);  // paired FP32 (FFMA2) arithmetic
+        else
+          elem_hessvec<D, TC>(xe, ve, m, out);
       } else if constexpr (OP == OP_DIAG) {
         elem_hessdiag<D, TC>(xe, m, out);
       } else {
@@ -280,6 +287,76 @@ cudaError_t elem_hess_coef(const Geom& g, const Mat<double>& m, const double* x,
     k_hess_coef<3, double><<<nb, 256, 0, st>>>(g, cast_mat<double>(m), x, coef);
   else
     k_hess_coef<2, double><<<nb, 256, 0, st>>>(g, cast_mat<double>(m), x, coef);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ FP64 gradient, two passes
+// Element-parallel: every element is evaluated once (no halo) and writes its
+// corner contributions to scratch[(f * 2^d + a) * NE + e]; then every node
+// sums the contributions of its up to 2^d elements in corner order, so the
+// result is deterministic.
+template <int D>
+__global__ void __launch_bounds__(128) k_grad_elem(Geom g, Mat<double> m, const double* __restrict__ x,
+                                                   double* __restrict__ scratch) {
+  constexpr int F = D + 1, NC = 1 << D;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.NE;
+       e += (long long)gridDim.x * blockDim.x) {
+    int ex, ey, ez;
+    elem_coords<D>(g, e, ex, ey, ez);
+    double xe[F][NC], out[F][NC];
+    gather<D, double>(g, x, ex, ey, ez, xe);
+    elem_gradient<D, double>(xe, m, out);
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int a = 0; a < NC; ++a) scratch[(f * NC + a) * g.NE + e] = out[f][a];
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_grad_gather(Geom g, const double* __restrict__ scratch,
+                                                     double* __restrict__ y) {
+  constexpr int F = D + 1, NC = 1 << D;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = int(i % g.n[0]);
+    const long long r = i / g.n[0];
+    const int iy = int(r % g.n[1]);
+    const int iz = int(r / g.n[1]);
+    const int ic[3] = {ix, iy, iz};
+    double acc[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = 0.0;
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+      int ec[3] = {0, 0, 0};
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        ec[k] = ic[k] - ((a >> k) & 1);
+        ok = ok && ec[k] >= 0 && ec[k] < g.ne[k];
+      }
+      if (!ok) continue;
+      const long long e = ec[0] + (long long)g.ne[0] * (ec[1] + (long long)g.ne[1] * ec[2]);
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f] += scratch[(f * NC + a) * g.NE + e];
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) y[f * g.N + i] = acc[f];
+  }
+}
+
+cudaError_t elem_gradient_fp64(const Geom& g, const Mat<double>& m, const double* x, double* y,
+                               double* scratch, cudaStream_t st) {
+  const int nb = int(std::min<long long>((g.NE + 127) / 128, 32LL * 1216));
+  const int nn = int(std::min<long long>((g.N + 255) / 256, 16LL * 1216));
+  if (g.dim == 3) {
+    k_grad_elem<3><<<nb, 128, 0, st>>>(g, m, x, scratch);
+    k_grad_gather<3><<<nn, 256, 0, st>>>(g, scratch, y);
+  } else {
+    k_grad_elem<2><<<nb, 128, 0, st>>>(g, m, x, scratch);
+    k_grad_gather<2><<<nn, 256, 0, st>>>(g, scratch, y);
+  }
   return cudaGetLastError();
 }
 

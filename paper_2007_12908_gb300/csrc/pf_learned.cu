@@ -201,7 +201,7 @@ pf_status pf_learned_propose(pf_hierarchy* h, double* x, const double* xhat, dou
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return cuda_status(e, "learned_propose");
   const double actual = -(h->h_res[0] + h->h_res[1] + h->h_res[2] + h->h_res[3]);
-  e = elem_gradient(g, h->mat[L - 1], x, gr, 0, h->st);
+  e = elem_gradient_fp64(g, h->mat[L - 1], x, gr, B.coef, h->st);
   if (e == cudaSuccess) e = elem_hessvec(g, h->mat[L - 1], x, s, hs, 0, h->st);
   if (e == cudaSuccess) {
     k_dots<<<reduce_grid(n), 256, 0, h->st>>>(n, gr, s, hs, h->scratch.partials, h->scratch.counter, h->d_res);

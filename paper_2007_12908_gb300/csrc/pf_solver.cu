@@ -172,9 +172,11 @@ struct Solver {
 
   // ---------------------------------------------------------------- element ops
   void gradient(int l, const double* x, double* out) {
-    ck(elem_gradient(H->geo[l], H->mat[l], x, out, 0, st), "gradient");
+    // FP64, elements evaluated once; the level's coefficient buffer is free
+    // scratch outside the assembly in set_lag
+    ck(elem_gradient_fp64(H->geo[l], H->mat[l], x, out, H->lv[l].coef, st), "gradient");
     S.fe_gradient += frac(l);
-    S.launches += 1;
+    S.launches += 2;
   }
   double ediff(int l, const double* x, const double* s) {
     ck(elem_energy_diff(H->geo[l], H->mat[l], x, s, 0, H->scratch, H->d_res, st), "ediff");
