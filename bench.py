@@ -39,6 +39,12 @@ WORKLOAD = {
     "fractures": 20, "seed": PI.SEED_3D_PLAIN, "dp": 5e-4,
 }
 METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same GB300"
+
+# DRAM bytes (read + write) per launch of the roofline kernels on this
+# workload from one ncu capture (profiles/elem_kernels_3d_129cubed_ncu.md);
+# to be re-captured whenever those kernels change.
+TRAFFIC_HESSVEC_FP32 = 68.730e6 + 13.118e6
+TRAFFIC_HESSVEC_FP64 = 7595.291e6 + 86.475e6
 UNIT = "s/load-step"
 
 # Finest-level-equivalent element passes per load step of the CUDA path on
@@ -330,12 +336,16 @@ def run_ours(args):
     bytes32 = 12.0 * ndof
     roof64 = {"kernel": "hessvec_fp64 (assembled stencil apply)", "bound": "hbm",
               "achieved": bytes64 / t64 / 1e9, "peak": hbm, "unit": "GB/s",
-              "frac": bytes64 / t64 / 1e9 / hbm, "traffic": None,
+              "frac": bytes64 / t64 / 1e9 / hbm, "traffic": TRAFFIC_HESSVEC_FP64,
+              "fp64_pipe_active": 0.984,
               "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
               "flop_per_node": 864, "fp64_fma_peak_tflops": fma64 / 1e12,
               "gdofs": ndof / t64 / 1e9, "us_per_launch": t64 * 1e6}
     roof32 = {"kernel": "hessvec_fp32", "bound": "hbm", "achieved": bytes32 / t32 / 1e9,
-              "peak": hbm, "unit": "GB/s", "frac": bytes32 / t32 / 1e9 / hbm, "traffic": None,
+              "peak": hbm, "unit": "GB/s", "frac": bytes32 / t32 / 1e9 / hbm,
+              # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
+              # this kernel (profiles/elem_kernels_3d_129cubed_ncu.md), per launch
+              "traffic": TRAFFIC_HESSVEC_FP32,
               "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
               "gdofs": ndof / t32 / 1e9, "us_per_launch": t32 * 1e6}
     roofline = roof64 if args.precision == "fp64" else roof32
