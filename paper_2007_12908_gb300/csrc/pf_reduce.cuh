@@ -9,17 +9,22 @@
 
 namespace pf {
 
+// FP32 overloads serve per-thread partial results of FP32 vectors; blocks
+// and the grid always combine in FP64.
 struct OpSum {
   static __device__ __forceinline__ double id() { return 0.0; }
   static __device__ __forceinline__ double op(double a, double b) { return a + b; }
+  static __device__ __forceinline__ float op(float a, float b) { return a + b; }
 };
 struct OpMax {
   static __device__ __forceinline__ double id() { return -INFINITY; }
   static __device__ __forceinline__ double op(double a, double b) { return fmax(a, b); }
+  static __device__ __forceinline__ float op(float a, float b) { return fmaxf(a, b); }
 };
 struct OpMin {
   static __device__ __forceinline__ double id() { return INFINITY; }
   static __device__ __forceinline__ double op(double a, double b) { return fmin(a, b); }
+  static __device__ __forceinline__ float op(float a, float b) { return fminf(a, b); }
 };
 
 template <int K, class Op>

@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <string>
+#include <type_traits>
 
 #include "pf_hier.h"
 #include "pf_reduce.cuh"
@@ -40,22 +41,33 @@ __global__ void k_map_skip(long long n, F f, const int* __restrict__ skip) {
     f(i);
 }
 
-// Reduction whose last block passes the combined values to fin() on the
-// device; a no-op launch when *skip is set.
-template <int K, class Op, class F, class Fin>
-__global__ void __launch_bounds__(256) k_red_fin(long long n, F f, Fin fin, double* partials,
-                                                 unsigned* counter, const int* __restrict__ skip) {
-  if (*skip) return;
-  double acc[K];
+// Each thread combines its elements in precision A (FP32 for FP32 vectors,
+// whose dot products then cost no FP64 instructions per element); blocks
+// and the grid combine in FP64.
+template <int K, class Op, class A, class F>
+__device__ __forceinline__ void thread_part(long long n, F& f, double (&out)[K]) {
+  A acc[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = Op::id();
+  for (int k = 0; k < K; ++k) acc[k] = A(Op::id());
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double v[K];
+    A v[K];
     f(i, v);
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = Op::op(acc[k], v[k]);
   }
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = double(acc[k]);
+}
+
+// Reduction whose last block passes the combined values to fin() on the
+// device; a no-op launch when *skip is set.
+template <int K, class Op, class A, class F, class Fin>
+__global__ void __launch_bounds__(256) k_red_fin(long long n, F f, Fin fin, double* partials,
+                                                 unsigned* counter, const int* __restrict__ skip) {
+  if (*skip) return;
+  double acc[K];
+  thread_part<K, Op, A>(n, f, acc);
   grid_finish_fn<K, Op>(acc, partials, counter, fin);
 }
 
@@ -72,19 +84,11 @@ __global__ void k_ctrl_start(CgCtrl* c, double rr, double rz, double tol, int us
   c->cg_max = cg_max;
 }
 
-template <int K, class Op, class F>
+template <int K, class Op, class A, class F>
 __global__ void __launch_bounds__(256) k_red(long long n, F f, double* partials, unsigned* counter,
                                              double* out) {
   double acc[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = Op::id();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    double v[K];
-    f(i, v);
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = Op::op(acc[k], v[k]);
-  }
+  thread_part<K, Op, A>(n, f, acc);
   grid_finish<K, Op>(acc, partials, counter, out);
 }
 
@@ -102,6 +106,13 @@ __device__ __forceinline__ bool on_boundary(const Geom& g, long long i) {
   bool b = ix == 0 || ix == g.n[0] - 1 || iy == 0 || iy == g.n[1] - 1;
   if (g.dim == 3) b = b || iz == 0 || iz == g.n[2] - 1;
   return b;
+}
+
+__device__ __forceinline__ double clampv(double x, double lo, double hi) {
+  return fmin(fmax(x, lo), hi);
+}
+__device__ __forceinline__ float clampv(float x, float lo, float hi) {
+  return fminf(fmaxf(x, lo), hi);
 }
 
 struct Solver {
@@ -133,18 +144,18 @@ struct Solver {
     S.launches += 1;
   }
 
-  template <int K, class Op, class Fn, class Fin>
+  template <int K, class Op, class A = double, class Fn, class Fin>
   void red_fin(long long n, Fn f, Fin fin, const int* skip) {
-    k_red_fin<K, Op><<<reduce_grid(n), 256, 0, st>>>(n, f, fin, H->scratch.partials,
-                                                      H->scratch.counter, skip);
+    k_red_fin<K, Op, A><<<reduce_grid(n), 256, 0, st>>>(n, f, fin, H->scratch.partials,
+                                                         H->scratch.counter, skip);
     ck(cudaGetLastError(), "red_fin");
     S.launches += 1;
   }
 
-  template <int K, class Op, class Fn>
+  template <int K, class Op, class A = double, class Fn>
   void reduce(long long n, Fn f, double* out) {
-    k_red<K, Op><<<reduce_grid(n), 256, 0, st>>>(n, f, H->scratch.partials, H->scratch.counter,
-                                                  H->d_res);
+    k_red<K, Op, A><<<reduce_grid(n), 256, 0, st>>>(n, f, H->scratch.partials, H->scratch.counter,
+                                                     H->d_res);
     ck(cudaGetLastError(), "reduce");
     S.launches += 1;
     fetch(K, out);
@@ -159,10 +170,12 @@ struct Solver {
   long long nd(int l) const { return H->lv[l].n; }
   double frac(int l) const { return double(H->geo[l].N) / double(H->geo[L - 1].N); }
 
-  void copy(double* dst, const double* src, long long n) {
-    ck(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+  template <class V>
+  void copy(V* dst, const V* src, long long n) {
+    ck(cudaMemcpyAsync(dst, src, sizeof(V) * n, cudaMemcpyDeviceToDevice, st), "copy");
   }
-  void zero(double* a, long long n) { ck(cudaMemsetAsync(a, 0, sizeof(double) * n, st), "zero"); }
+  template <class V>
+  void zero(V* a, long long n) { ck(cudaMemsetAsync(a, 0, sizeof(V) * n, st), "zero"); }
 
   double dot(const double* a, const double* b, long long n) {
     double r;
@@ -212,17 +225,28 @@ struct Solver {
     }
     if (P.precondition) {
       // Jacobi: inverse of the positive part of the lagged Hessian's diagonal
-      // (the level's own Hessian at x0 for GALERKIN levels)
+      // (the level's own Hessian at x0 for GALERKIN levels); FP32 on levels
+      // whose subproblem runs on FP32 vectors (the diagonal goes through B.Hw,
+      // free outside the subproblem)
       const bool m32 = mixed32(l);
+      double* d = sub32(l) ? B.Hw : B.minv;
       ck(elem_hessdiag(H->geo[l], H->mat[l], m32 ? (const void*)B.xlag32 : (const void*)B.xlag,
-                       m32 ? 1 : 0, B.minv, st),
+                       m32 ? 1 : 0, d, st),
          "hessdiag");
       S.launches += 1;
-      double* mi = B.minv;
-      map(B.n, [=] __device__(long long i) {
-        const double d = mi[i];
-        mi[i] = d > 0.0 ? 1.0 / d : 0.0;
-      });
+      if (sub32(l)) {
+        float* mi = reinterpret_cast<float*>(B.minv);
+        map(B.n, [=] __device__(long long i) {
+          const double di = d[i];
+          mi[i] = di > 0.0 ? float(1.0 / di) : 0.0f;
+        });
+      } else {
+        double* mi = B.minv;
+        map(B.n, [=] __device__(long long i) {
+          const double di = mi[i];
+          mi[i] = di > 0.0 ? 1.0 / di : 0.0;
+        });
+      }
     }
   }
 
@@ -310,45 +334,109 @@ struct Solver {
   }
 
   // ---------------------------------------------------------------- subproblem
-  // Projected-search truncated CG for min g.s + 1/2 s.Hs over lo <= s <= hi.
-  // Uses B.s (result), B.Hs, B.r, B.p, B.q, B.w, B.Hw, B.t1 (s_new), B.t2.
+  // Levels whose subproblem runs on FP32 vectors: the FP32-Hessian levels of
+  // the mixed mode (GALERKIN levels apply their operator through FP64
+  // transfers and keep FP64 vectors).
+  bool sub32(int l) const { return mixed32(l) && !galerkin(l); }
+
+  // The lagged model Hessian on vectors of precision V.
+  template <class V>
+  void hv(int l, const V* v, V* out, const int* skip = nullptr, bool count = true) {
+    if constexpr (std::is_same<V, double>::value) {
+      Hlag(l, v, out, skip, count);
+    } else {
+      ck(elem_hessvec(H->geo[l], H->mat[l], H->lv[l].xlag32, v, out, 1, st, skip), "hessvec32");
+      S.launches += 1;
+      if (count) {
+        S.hessvecs += 1;
+        S.fe_hessvec += frac(l);
+      }
+    }
+  }
+
+  // Vectors of one subproblem solve in precision V.  a and b hold the free
+  // gaps lo - s < 0 < hi - s of the current s on its free set and 0 elsewhere,
+  // so a[i] < 0 is the free-set test and w outside [a, b] leaves the box.
+  template <class V>
+  struct SubVecs {
+    const V *g, *lo, *hi, *mi;
+    V *s, *Hs, *r, *p, *q, *w, *a, *b, *t1, *t2;
+  };
+
+  // Projected-search truncated CG for min g.s + 1/2 s.Hs over lo <= s <= hi
+  // (eq. model_qp); the step is left in B.s (FP64).  On sub32 levels the
+  // solve runs on FP32 copies of g and of the box, rounded towards zero so
+  // that the FP32 box lies inside the FP64 one, in FP32 halves of the FP64
+  // work buffers.  Uses B.s, B.Hs, B.r, B.p, B.q, B.w, B.Hw, B.t1, B.t2, B.t3.
   void subproblem(int l, double delta, int cg_max) {
     LevelBuf& B = H->lv[l];
     const long long n = B.n;
-    const double *g = B.g, *lo = B.lo, *hi = B.hi;
-    double *s = B.s, *Hs = B.Hs, *r = B.r, *p = B.p, *q = B.q, *w = B.w, *Hw = B.Hw;
-    double *t1 = B.t1, *t2 = B.t2;
+    if (!sub32(l)) {
+      subproblem_t<double>(l, delta, cg_max,
+                           {B.g, B.lo, B.hi, B.minv, B.s, B.Hs, B.r, B.p, B.q, B.w, B.Hw, B.t3,
+                            B.t1, B.t2});
+      return;
+    }
+    auto half = [n](double* d, int k) { return reinterpret_cast<float*>(d) + k * n; };
+    float *g32 = half(B.t3, 0), *lo32 = half(B.t3, 1), *hi32 = half(B.Hw, 0);
+    {
+      const double *g = B.g, *lo = B.lo, *hi = B.hi;
+      map(n, [=] __device__(long long i) {
+        g32[i] = __double2float_rn(g[i]);
+        lo32[i] = __double2float_ru(lo[i]);  // lo <= 0 <= hi
+        hi32[i] = __double2float_rd(hi[i]);
+      });
+    }
+    const SubVecs<float> v{g32, lo32, hi32, reinterpret_cast<const float*>(B.minv),
+                           half(B.Hw, 1), half(B.Hs, 0), half(B.Hs, 1), half(B.p, 0),
+                           half(B.p, 1), half(B.w, 0), half(B.w, 1), half(B.r, 0),
+                           half(B.r, 1), half(B.q, 0)};
+    subproblem_t<float>(l, delta, cg_max, v);
+    const float* s32 = v.s;
+    double* s = B.s;
+    map(n, [=] __device__(long long i) { s[i] = double(s32[i]); });
+  }
+
+  template <class V>
+  void subproblem_t(int l, double delta, int cg_max, const SubVecs<V>& vec) {
+    const long long n = H->lv[l].n;
+    const V *g = vec.g, *lo = vec.lo, *hi = vec.hi, *mi = vec.mi;
+    V *s = vec.s, *Hs = vec.Hs, *r = vec.r, *p = vec.p, *q = vec.q, *w = vec.w;
+    V *ga = vec.a, *gb = vec.b, *t1 = vec.t1, *t2 = vec.t2;
+    const V Z = V(0);
     double gmax;
-    reduce<1, OpMax>(n, [=] __device__(long long i, double(&v)[1]) {
-      const bool mv = (g[i] < 0.0 && hi[i] > 0.0) || (g[i] > 0.0 && lo[i] < 0.0);
-      v[0] = mv ? fabs(g[i]) : 0.0;
+    reduce<1, OpMax, V>(n, [=] __device__(long long i, V(&o)[1]) {
+      const V gi = g[i];
+      const bool mv = (gi < Z && hi[i] > Z) || (gi > Z && lo[i] < Z);
+      o[0] = mv ? (gi < Z ? -gi : gi) : Z;
     }, &gmax);
     zero(s, n);
     if (!(gmax > 0.0)) return;
     double t = delta / gmax;
     // exact minimiser of the model along the movable part of -g
     map(n, [=] __device__(long long i) {
-      const bool mv = (g[i] < 0.0 && hi[i] > 0.0) || (g[i] > 0.0 && lo[i] < 0.0);
-      t1[i] = mv ? g[i] : 0.0;
+      const V gi = g[i];
+      const bool mv = (gi < Z && hi[i] > Z) || (gi > Z && lo[i] < Z);
+      t1[i] = mv ? gi : Z;
     });
-    Hlag(l, t1, t2);
+    hv<V>(l, t1, t2);
     S.hv_cauchy += 1;
     double cg2[2];
-    reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
-      v[0] = t1[i] * t2[i];
-      v[1] = t1[i] * t1[i];
+    reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
+      o[0] = t1[i] * t2[i];
+      o[1] = t1[i] * t1[i];
     }, cg2);
     if (cg2[0] > 0.0) t = std::min(t, cg2[1] / cg2[0]);
     bool ok = false;
     for (int bt = 0; bt <= P.cauchy_backtracks; ++bt) {
-      const double tt = t;
-      map(n, [=] __device__(long long i) { s[i] = fmin(fmax(-tt * g[i], lo[i]), hi[i]); });
-      Hlag(l, s, Hs);
+      const V tt = V(t);
+      map(n, [=] __device__(long long i) { s[i] = clampv(-tt * g[i], lo[i], hi[i]); });
+      hv<V>(l, s, Hs);
       S.hv_cauchy += 1;
       double a[2];
-      reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
-        v[0] = g[i] * s[i];
-        v[1] = s[i] * Hs[i];
+      reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
+        o[0] = g[i] * s[i];
+        o[1] = s[i] * Hs[i];
       }, a);
       if (a[0] + 0.5 * a[1] <= P.cauchy_c * a[0]) {
         ok = true;
@@ -365,20 +453,22 @@ struct Solver {
     double tol = -1.0;
     CgCtrl* c = H->ctrl;
     const int* skip = &H->ctrl->done;
+    const bool pc = P.precondition != 0;
     while (used < cg_max) {
       double rr2[2];
-      const double* mi = B.minv;
-      const bool pc = P.precondition != 0;
-      reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
-        const bool fr = lo[i] < s[i] && s[i] < hi[i];
-        const double ri = fr ? -(g[i] + Hs[i]) : 0.0;
-        const double zi = pc ? mi[i] * ri : ri;
+      // residual of the model on the free set of s, its gaps, p = M^-1 r
+      reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
+        const V a = lo[i] - s[i], b = hi[i] - s[i];
+        const bool fr = a < Z && Z < b;
+        const V ri = fr ? -(g[i] + Hs[i]) : Z;
+        const V zi = pc ? mi[i] * ri : ri;
         r[i] = ri;
         p[i] = zi;
-        w[i] = 0.0;
-        Hw[i] = 0.0;
-        v[0] = ri * ri;
-        v[1] = ri * zi;
+        w[i] = Z;
+        ga[i] = fr ? a : Z;
+        gb[i] = fr ? b : Z;
+        o[0] = ri * ri;
+        o[1] = ri * zi;
       }, rr2);
       const double rr = rr2[0];
       if (tol < 0.0) {
@@ -388,9 +478,10 @@ struct Solver {
       if (std::sqrt(rr) <= tol || rr == 0.0) break;
       // CG on the free set, driven on the device: each iteration is the
       // model Hessian, a reduction for p.Hp (its last block sets alpha or
-      // flags non-positive curvature), an update reduction (its last block
-      // tests the box, the forcing term and the budget and sets beta) and
-      // the direction update.  The host polls the control block between
+      // flags non-positive curvature; p vanishes off the free set, so the
+      // unmasked product is the masked one), an update reduction (its last
+      // block tests the box, the forcing term and the budget and sets beta)
+      // and the direction update.  The host polls the control block between
       // chunks of iterations; launches after a stop are no-ops.
       k_ctrl_start<<<1, 1, 0, st>>>(c, rr, rr2[1], tol, used, cg_max);
       ck(cudaGetLastError(), "ctrl");
@@ -398,13 +489,9 @@ struct Solver {
       int chunk = 2;
       for (;;) {
         for (int k = 0; k < chunk; ++k) {
-          Hlag(l, p, q, skip, false);
-          red_fin<1, OpSum>(n, [=] __device__(long long i, double(&v)[1]) {
-            const bool fr = lo[i] < s[i] && s[i] < hi[i];
-            const double qi = fr ? q[i] : 0.0;
-            q[i] = qi;
-            v[0] = p[i] * qi;
-          }, [=] __device__(double(&a)[1]) {
+          hv<V>(l, p, q, skip, false);
+          red_fin<1, OpSum, V>(n, [=] __device__(long long i, V(&o)[1]) { o[0] = p[i] * q[i]; },
+                               [=] __device__(double(&a)[1]) {
             c->kappa = a[0];
             c->used += 1;
             if (a[0] <= 0.0) {
@@ -414,18 +501,17 @@ struct Solver {
               c->alpha = c->rz / a[0];
             }
           }, skip);
-          red_fin<3, OpSum>(n, [=] __device__(long long i, double(&v)[3]) {
-            const double al = c->alpha;
-            const bool fr = lo[i] < s[i] && s[i] < hi[i];
-            const double wi = w[i] + al * p[i];
+          red_fin<3, OpSum, V>(n, [=] __device__(long long i, V(&o)[3]) {
+            const V al = V(c->alpha);
+            const V a = ga[i];
+            const V qi = a < Z ? q[i] : Z;
+            const V wi = w[i] + al * p[i];
             w[i] = wi;
-            Hw[i] += al * q[i];
-            const double ri = r[i] - al * q[i];
+            const V ri = r[i] - al * qi;
             r[i] = ri;
-            const double sw = s[i] + wi;
-            v[0] = ri * ri;
-            v[1] = (fr && (sw < lo[i] || sw > hi[i])) ? 1.0 : 0.0;
-            v[2] = ri * (pc ? mi[i] * ri : ri);
+            o[0] = ri * ri;
+            o[1] = (wi < a || wi > gb[i]) ? V(1) : Z;
+            o[2] = ri * (pc ? mi[i] * ri : ri);
           }, [=] __device__(double(&a)[3]) {
             if (a[1] > 0.0) {
               c->done = 1;
@@ -443,7 +529,7 @@ struct Solver {
             }
           }, skip);
           map_skip(n, [=] __device__(long long i) {
-            p[i] = (pc ? mi[i] * r[i] : r[i]) + c->beta * p[i];
+            p[i] = (pc ? mi[i] * r[i] : r[i]) + V(c->beta) * p[i];
           }, skip);
         }
         ck(cudaMemcpyAsync(H->h_ctrl, c, sizeof(CgCtrl), cudaMemcpyDeviceToHost, st), "ctrl");
@@ -460,51 +546,45 @@ struct Solver {
       S.fe_hessvec += its * hlag_units(l);
       bool leave = cs.state == CG_LEAVE;
       if (cs.state == CG_NEGCURV) {
+        // to the box along p
         double amax;
-        reduce<1, OpMin>(n, [=] __device__(long long i, double(&v)[1]) {
-          const bool fr = lo[i] < s[i] && s[i] < hi[i];
-          const double sw = s[i] + w[i];
-          double a = INFINITY;
-          if (fr && p[i] > 0.0) a = (hi[i] - sw) / p[i];
-          if (fr && p[i] < 0.0) a = (lo[i] - sw) / p[i];
-          v[0] = a;
+        reduce<1, OpMin, V>(n, [=] __device__(long long i, V(&o)[1]) {
+          const V pi = p[i];
+          V a = V(INFINITY);
+          if (pi > Z) a = (gb[i] - w[i]) / pi;
+          if (pi < Z) a = (ga[i] - w[i]) / pi;
+          o[0] = a;
         }, &amax);
         amax = std::max(amax, 0.0);
         if (std::isfinite(amax)) {
-          const double am = amax;
-          map(n, [=] __device__(long long i) {
-            w[i] += am * p[i];
-            Hw[i] += am * q[i];
-          });
+          const V am = V(amax);
+          map(n, [=] __device__(long long i) { w[i] += am * p[i]; });
         }
         leave = true;
       }
       if (!leave) {
-        map(n, [=] __device__(long long i) {
-          s[i] += w[i];
-          Hs[i] += Hw[i];
-        });
+        map(n, [=] __device__(long long i) { s[i] += w[i]; });
         break;
       }
       // projected search along w
       double ms[2];
-      reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
-        v[0] = g[i] * s[i];
-        v[1] = s[i] * Hs[i];
+      reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
+        o[0] = g[i] * s[i];
+        o[1] = s[i] * Hs[i];
       }, ms);
       const double m_s = ms[0] + 0.5 * ms[1];
       double beta = 1.0;
       bool accepted = false;
       for (int bt = 0; bt <= P.cauchy_backtracks; ++bt) {
-        const double b = beta;
-        map(n, [=] __device__(long long i) { t1[i] = fmin(fmax(s[i] + b * w[i], lo[i]), hi[i]); });
-        Hlag(l, t1, t2);
+        const V bb = V(beta);
+        map(n, [=] __device__(long long i) { t1[i] = clampv(s[i] + bb * w[i], lo[i], hi[i]); });
+        hv<V>(l, t1, t2);
         S.hv_search += 1;
         double a[3];
-        reduce<3, OpSum>(n, [=] __device__(long long i, double(&v)[3]) {
-          v[0] = g[i] * t1[i];
-          v[1] = t1[i] * t2[i];
-          v[2] = (g[i] + Hs[i]) * (t1[i] - s[i]);
+        reduce<3, OpSum, V>(n, [=] __device__(long long i, V(&o)[3]) {
+          o[0] = g[i] * t1[i];
+          o[1] = t1[i] * t2[i];
+          o[2] = (g[i] + Hs[i]) * (t1[i] - s[i]);
         }, a);
         if (a[0] + 0.5 * a[1] <= m_s + P.cauchy_c * a[2]) {
           accepted = true;
@@ -518,7 +598,7 @@ struct Solver {
       S.cg_restarts += 1;
       if (++restarts > P.max_restarts) break;
     }
-    map(n, [=] __device__(long long i) { s[i] = fmin(fmax(s[i], lo[i]), hi[i]); });
+    map(n, [=] __device__(long long i) { s[i] = clampv(s[i], lo[i], hi[i]); });
   }
 
   // ---------------------------------------------------------------- TR method
