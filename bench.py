@@ -441,7 +441,11 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "work_model": work,
             "solver": {k: [s[k] for s in stats] for k in ("cycles", "converged", "cg", "tr_its",
-                                                          "tr_rejected", "coarse_rejected", "status")},
+                                                          "tr_rejected", "coarse_rejected", "status",
+                                                          "hv_cauchy", "hv_search", "cg_restarts",
+                                                          "fe_hessvec", "fe_gradient", "fe_energy")},
+            "solver_levels": {k: [list(s[k])[:W["levels"]] for s in stats]
+                              for k in ("cg_level", "tr_level", "rej_level")},
         }
         print(json.dumps(line))
     if dist:

@@ -163,7 +163,7 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
     const size_t bytes = sizeof(double) * B.n;
     double** vecs[] = {&B.x, &B.lb, &B.ub, &B.x0, &B.xlag, &B.dg, &B.g, &B.s, &B.lo, &B.hi,
                        &B.Hs, &B.r, &B.p, &B.q, &B.w, &B.Hw, &B.t1, &B.t2, &B.t3, &B.gin,
-                       &B.gout, &B.dh, &B.minv};
+                       &B.gout, &B.dh, &B.minv, &B.g0};
     for (double** v : vecs)
       if ((rc = alloc(h, (void**)v, bytes))) {
         pf_mesh_hierarchy_destroy(h);

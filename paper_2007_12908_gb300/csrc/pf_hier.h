@@ -14,6 +14,7 @@ struct LevelBuf {
   long long n = 0;  // dofs
   double *x = nullptr, *lb = nullptr, *ub = nullptr;  // iterate and feasible set
   double *x0 = nullptr, *xlag = nullptr, *dg = nullptr;  // level model
+  double* g0 = nullptr;  // gradient of the level model at x0 (R of the finer gradient)
   double *g = nullptr, *s = nullptr, *lo = nullptr, *hi = nullptr;  // TR step
   double *Hs = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;    // CG
   double *w = nullptr, *Hw = nullptr, *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;

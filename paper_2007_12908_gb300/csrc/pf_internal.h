@@ -41,6 +41,12 @@ cudaError_t elem_energy_blocks(const Geom& g, const Mat<double>& m, const void* 
                                cudaStream_t st);
 cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x, const void* sv,
                              int prec, const Scratch& s, double* out_dev, cudaStream_t st);
+// (gx . s, a2, a3, a4) to out_dev[0..4): the higher-order coefficients of
+// E(x + t s) - E(x) in FP32 arithmetic from FP64 x and s, and the FP64 dot
+// product of gx (skipped when null) with s.
+cudaError_t elem_energy_diff_hi(const Geom& g, const Mat<double>& m, const double* x,
+                                const double* sv, const double* gx, const Scratch& s,
+                                double* out_dev, cudaStream_t st);
 cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, void* y, int prec,
                           cudaStream_t st);
 // FP64 gradient evaluating every element once: corner contributions go to

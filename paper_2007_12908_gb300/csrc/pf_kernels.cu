@@ -141,6 +141,47 @@ __global__ void __launch_bounds__(256) k_energy_diff(Geom g, Mat<double> m,
   grid_finish<4, OpSum>(acc, partials, counter, out);
 }
 
+// Second- to fourth-order coefficients a2..a4 of E(x + t s) - E(x) from FP64
+// x and s in FP32 arithmetic (each a sum of terms of order two and higher in
+// s, free of the cancellation of energy totals), plus the FP64 dot product
+// gx . s over the n dofs when gx is given (the first-order coefficient when
+// gx is the gradient at x).  out = (gx . s, a2, a3, a4).
+template <int D>
+__global__ void __launch_bounds__(256) k_energy_diff_hi(Geom g, Mat<float> m,
+                                                        const double* __restrict__ x,
+                                                        const double* __restrict__ s,
+                                                        const double* __restrict__ gx,
+                                                        long long n, double* partials,
+                                                        unsigned* counter, double* out) {
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.NE;
+       e += (long long)gridDim.x * blockDim.x) {
+    int ex, ey, ez;
+    elem_coords<D>(g, e, ex, ey, ez);
+    double xt[D + 1][1 << D], st[D + 1][1 << D];
+    gather<D, double>(g, x, ex, ey, ez, xt);
+    gather<D, double>(g, s, ex, ey, ez, st);
+    float xe[D + 1][1 << D], se[D + 1][1 << D];
+#pragma unroll
+    for (int f = 0; f <= D; ++f)
+#pragma unroll
+      for (int a = 0; a < (1 << D); ++a) {
+        xe[f][a] = float(xt[f][a]);
+        se[f][a] = float(st[f][a]);
+      }
+    float a4[4];
+    elem_energy_diff<D, float>(xe, se, m, a4);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] += a4[k + 1];
+  }
+  double d[4] = {0.0, double(acc[0]), double(acc[1]), double(acc[2])};
+  if (gx)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+      d[0] += gx[i] * s[i];
+  grid_finish<4, OpSum>(d, partials, counter, out);
+}
+
 // ------------------------------------------------------------ scatter ops
 template <int D>
 struct Tile;
@@ -585,6 +626,20 @@ cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x,
                 : launch_energy_diff<3, double>(g, m, x, sv, s, out, st);
   return prec ? launch_energy_diff<2, float>(g, m, x, sv, s, out, st)
               : launch_energy_diff<2, double>(g, m, x, sv, s, out, st);
+}
+
+cudaError_t elem_energy_diff_hi(const Geom& g, const Mat<double>& m, const double* x,
+                                const double* sv, const double* gx, const Scratch& s,
+                                double* out, cudaStream_t st) {
+  const int nb = reduce_grid(g.NE, 256);
+  const long long n = (long long)(g.dim + 1) * g.N;
+  if (g.dim == 3)
+    k_energy_diff_hi<3><<<nb, 256, 0, st>>>(g, cast_mat<float>(m), x, sv, gx, n, s.partials,
+                                            s.counter, out);
+  else
+    k_energy_diff_hi<2><<<nb, 256, 0, st>>>(g, cast_mat<float>(m), x, sv, gx, n, s.partials,
+                                            s.counter, out);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ rasterisation

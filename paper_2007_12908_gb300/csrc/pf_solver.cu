@@ -316,8 +316,27 @@ struct Solver {
     map(B.n, [=] __device__(long long i) { out[i] += dg[i] + e[i]; });
   }
 
-  // h(x + s) - h(x) without subtracting totals
-  double diff_h(int l, const double* x, const double* s) {
+  // h(x + s) - h(x) without subtracting totals; gx = grad h(x) (FP64).
+  // h(x + t s) - h(x) is a quartic in t whose first-order coefficient is
+  // gx . s, so the FP32-Hessian levels of the mixed mode take that term in
+  // FP64 from gx and only the higher-order terms of f~ from an FP32 pass
+  // (GALERKIN adds 1/2 s.dH s; dg and dH (x - x0) are inside gx).
+  double diff_h(int l, const double* x, const double* s, const double* gx) {
+    if (mixed32(l)) {
+      LevelBuf& B = H->lv[l];
+      ck(elem_energy_diff_hi(H->geo[l], H->mat[l], x, s, gx, H->scratch, H->d_res, st),
+         "ediff_hi");
+      S.fe_energy += frac(l);
+      S.launches += 1;
+      double a[4];
+      fetch(4, a);
+      double d = a[0] + a[1] + a[2] + a[3];
+      if (galerkin(l)) {
+        dH(l, s, B.t2);
+        d += 0.5 * dot(s, B.t2, B.n);
+      }
+      return d;
+    }
     double d = ediff(l, x, s);
     if (finest(l)) return d;
     LevelBuf& B = H->lv[l];
@@ -648,7 +667,7 @@ struct Solver {
       S.tr_its += 1;
       S.tr_level[std::min(l, 7)] += 1;
       if (!(pred > 0.0)) break;
-      const double rho = -diff_h(l, B.x, B.s) / pred;
+      const double rho = -diff_h(l, B.x, B.s, B.g) / pred;
       if (rho <= P.eta1) {
         S.tr_rejected += 1;
         S.rej_level[std::min(l, 7)] += 1;
@@ -680,15 +699,16 @@ struct Solver {
         xc[i] = x0[i];
       });
     }
-    // dg = R grad h^l(x_mu1) - grad f~(x0)
+    // dg = R grad h^l(x_mu1) - grad f~(x0); g0 = R grad h^l(x_mu1) is the
+    // coarse model's gradient at x0 (first-order coherence)
     grad_h(l, B.x, B.g);
-    ck(xfer_restrict(gc, gf, F, B.g, C.dg, 0, false, st), "restrict");
+    ck(xfer_restrict(gc, gf, F, B.g, C.g0, 0, false, st), "restrict");
     S.launches += 1;
     gradient(l - 1, C.x0, C.t1);
     {
       double* dg = C.dg;
-      const double* t = C.t1;
-      map(C.n, [=] __device__(long long i) { dg[i] -= t[i]; });
+      const double *t = C.t1, *g0 = C.g0;
+      map(C.n, [=] __device__(long long i) { dg[i] = g0[i] - t[i]; });
     }
     set_lag(l - 1, C.x0);
     double dc = delta;
@@ -704,11 +724,11 @@ struct Solver {
     // C.t3 holds the coarse correction; diff_h uses C.t2/C.t3 as scratch, so
     // keep a copy in C.w
     copy(C.w, C.t3, C.n);
-    const double pred = -diff_h(l - 1, C.x0, C.w);
+    const double pred = -diff_h(l - 1, C.x0, C.w, C.g0);
     ck(xfer_prolong(gc, gf, F, C.w, B.s, 0, st), "prolong");
     S.launches += 1;
     if (pred > 0.0) {
-      const double rho = -diff_h(l, B.x, B.s) / pred;
+      const double rho = -diff_h(l, B.x, B.s, B.g) / pred;
       if (rho <= P.eta1) S.coarse_rejected += 1;
       control(rho, l, B.x, delta);
     }
