@@ -173,9 +173,28 @@ pf_status pf_energy(pf_hierarchy* h, int level, const void* x_dev, int prec, dou
 pf_status pf_energy_diff(pf_hierarchy* h, int level, const void* x_dev, const void* s_dev,
                          int prec, double* a_host);
 
+/* Mixed-precision form of pf_energy_diff used by the FP32 levels of the
+ * solver: a_host[0] = g . s over all dofs in FP64 (the first-order
+ * coefficient a1 when g_dev is grad E(x)), a_host[1..3] = a2, a3, a4 in FP32
+ * arithmetic from the FP64 x_dev and s_dev (each a sum of terms of order two
+ * and higher in s, so their error is relative to their own size).  All
+ * vectors FP64 device arrays of (dim+1)*N values. */
+pf_status pf_energy_diff_mixed(pf_hierarchy* h, int level, const double* x_dev,
+                               const double* s_dev, const double* g_dev, double* a_host);
+
 /* Gradient of the energy at x_dev written to g_dev (same precision, same
  * layout), all dofs, no boundary masking. */
 pf_status pf_gradient(pf_hierarchy* h, int level, const void* x_dev, void* g_dev, int prec);
+
+/* Gradient step: g_dev += grad E(x_dev) - grad E(x_dev - s_dev), so that
+ * g_dev = grad E(x - s) on entry leaves grad E(x).  FP64 vectors; the
+ * difference is evaluated in FP32 arithmetic as a sum of terms of order one
+ * and higher in s (no two gradients are subtracted), so its error is
+ * relative to the size of the change.  The mixed-precision solver updates
+ * its model gradient this way after an accepted step (Algorithm 2); every
+ * stopping test still evaluates the FP64 gradient. */
+pf_status pf_gradient_step(pf_hierarchy* h, int level, const double* x_dev, const double* s_dev,
+                           double* g_dev);
 
 /* Hessian of the energy at x_lin_dev applied to v_dev, written to Hv_dev;
  * matrix-free (Sec. 4.2.1 Hessian; applied, not assembled).  All three

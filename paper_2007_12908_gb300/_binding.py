@@ -33,6 +33,7 @@ EXPORTS = [
     "pf_unet_set_params", "pf_unet_get_params", "pf_unet_get_grads", "pf_unet_forward",
     "pf_unet_backward", "pf_unet_mse", "pf_unet_adam", "pf_learned_features", "pf_learned_target",
     "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient", "pf_rmtr_load_step_batch",
+    "pf_energy_diff_mixed", "pf_gradient_step",
 ]
 
 
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_energy": (i, [vp, i, vp, i, C.POINTER(d)]),
         "pf_energy_diff": (i, [vp, i, vp, vp, i, vp]),
         "pf_gradient": (i, [vp, i, vp, vp, i]),
+        "pf_energy_diff_mixed": (i, [vp, i, vp, vp, vp, vp]),
+        "pf_gradient_step": (i, [vp, i, vp, vp, vp]),
         "pf_hessvec": (i, [vp, i, vp, vp, vp, i]),
         "pf_prolong": (i, [vp, i, vp, vp, i]),
         "pf_restrict": (i, [vp, i, vp, vp, i]),
@@ -262,6 +265,27 @@ def energy_diff(H: Hierarchy, level: int, x, s) -> np.ndarray:
     _check(lib().pf_energy_diff(H.handle, level, _dev(x, H.ndof(level)), _dev(s, H.ndof(level)),
                                 _prec(x), out.ctypes.data_as(C.c_void_p)))
     return out
+
+
+def energy_diff_mixed(H: Hierarchy, level: int, x, s, g) -> np.ndarray:
+    """(g.s, a2, a3, a4): FP64 dot product and the FP32 higher-order
+    coefficients of E(x + t s) - E(x); x, s, g FP64."""
+    import torch
+    n = H.ndof(level)
+    out = np.zeros(4)
+    _check(lib().pf_energy_diff_mixed(H.handle, level, _dev(x, n, torch.float64),
+                                      _dev(s, n, torch.float64), _dev(g, n, torch.float64),
+                                      out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def gradient_step(H: Hierarchy, level: int, x, s, g):
+    """g += grad E(x) - grad E(x - s) in place (FP64 vectors, FP32 difference)."""
+    import torch
+    n = H.ndof(level)
+    _check(lib().pf_gradient_step(H.handle, level, _dev(x, n, torch.float64),
+                                  _dev(s, n, torch.float64), _dev(g, n, torch.float64)))
+    return g
 
 
 def gradient(H: Hierarchy, level: int, x, out=None):

@@ -295,6 +295,19 @@ pf_status pf_energy_diff(pf_hierarchy* h, int level, const void* x, const void* 
   return PF_OK;
 }
 
+pf_status pf_energy_diff_mixed(pf_hierarchy* h, int level, const double* x, const double* s,
+                               const double* g, double* a_host) {
+  if (!valid_level(h, level) || !x || !s || !g || !a_host)
+    return bad("energy_diff_mixed: bad argument");
+  PF_TRY_CUDA(elem_energy_diff_hi(h->geo[level], h->mat[level], x, s, g, h->scratch, h->d_res, h->st),
+              "energy_diff_mixed");
+  PF_TRY_CUDA(cudaMemcpyAsync(h->h_res, h->d_res, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st),
+              "energy_diff_mixed");
+  PF_TRY_CUDA(cudaStreamSynchronize(h->st), "energy_diff_mixed");
+  for (int k = 0; k < 4; ++k) a_host[k] = h->h_res[k];
+  return PF_OK;
+}
+
 pf_status pf_gradient(pf_hierarchy* h, int level, const void* x, void* g, int prec) {
   if (!valid_level(h, level) || !x || !g) return bad("gradient: bad argument");
   if (check_prec(prec)) return PF_EINVAL;
@@ -304,6 +317,13 @@ pf_status pf_gradient(pf_hierarchy* h, int level, const void* x, void* g, int pr
                 "gradient");
   else
     PF_TRY_CUDA(elem_gradient(h->geo[level], h->mat[level], x, g, prec, h->st), "gradient");
+  return PF_OK;
+}
+
+pf_status pf_gradient_step(pf_hierarchy* h, int level, const double* x, const double* s,
+                           double* g) {
+  if (!valid_level(h, level) || !x || !s || !g) return bad("gradient_step: bad argument");
+  PF_TRY_CUDA(elem_gradient_step(h->geo[level], h->mat[level], x, s, g, h->st), "gradient_step");
   return PF_OK;
 }
 

@@ -414,6 +414,82 @@ __device__ __forceinline__ void elem_gradient(const T (*xe)[1 << D], const Mat<T
   test<D, T>(s0, sc, out[D]);
 }
 
+// Gradient difference grad E_e(x + s) - grad E_e(x), written so that every
+// term is of order one or higher in s (no difference of two gradients is
+// formed; for c' = c + s_c, u' = u + s_u):
+//   u-rows  int [g(c') sigma(s_u) + (g(c') - g(c)) (sigma(u) + p I)] : grad phi
+//   c-row   int [g'(c') (psi_1 + psi(s_u) + p tr s_u)
+//                + (g'(c') - g'(c)) (psi(u) + p tr u) + Gc s_c/ls] phi
+//               + Gc ls grad s_c . grad phi
+// with psi_1 = lam tr(u) tr(s_u) + 2 mu eps(u) : eps(s_u),
+// g(c') - g(c) = (1-k) s_c (s_c - 2 (1-c)) and g'(c') - g'(c) = 2 (1-k) s_c.
+template <int D, class T>
+__device__ __forceinline__ void elem_gradient_diff(const T (*xe)[1 << D], const T (*se)[1 << D],
+                                                   const Mat<T>& m, T (*out)[1 << D]) {
+  constexpr int NQ = 1 << D;
+  T su[D][D][NQ], s0[NQ], sc[D][NQ];
+  {
+    T gu[D][D][NQ], cv[NQ], gcx[D][NQ], dummy[NQ];
+    T gs[D][D][NQ], scv[NQ], gsc[D][NQ];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      interp<D, T>(xe[i], dummy, gu[i]);
+      interp<D, T>(se[i], dummy, gs[i]);
+    }
+    interp<D, T>(xe[D], cv, gcx);
+    interp<D, T>(se[D], scv, gsc);
+    const T omk = T(1) - m.k;
+    const T kc = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
+    const T gcl = m.Gc / m.ls;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T G[D][D], Gs[D][D];
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          G[i][k] = gu[i][k][q] * m.inv_h;
+          Gs[i][k] = gs[i][k][q] * m.inv_h;
+        }
+      StrainSym<D, T> e0, e1;
+      e0.set(G);
+      e1.set(Gs);
+      T e01 = T(0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) e01 += G[i][i] * Gs[i][i];
+#pragma unroll
+      for (int j = 0; j < (D == 3 ? 3 : 1); ++j) e01 += T(0.5) * e0.off[j] * e1.off[j];
+      const T psi0 = T(0.5) * m.lam * e0.tr * e0.tr + m.mu * e0.ee;
+      const T psi2 = T(0.5) * m.lam * e1.tr * e1.tr + m.mu * e1.ee;
+      const T psi1 = m.lam * e0.tr * e1.tr + T(2) * m.mu * e01;
+      const T omc = T(1) - cv[q], sq = scv[q], omc1 = omc - sq;
+      const T g1 = omk * omc1 * omc1 + m.k;         // g(c')
+      const T dg = omk * sq * (sq - T(2) * omc);      // g(c') - g(c)
+      const T dp1 = T(-2) * omk * omc1;               // g'(c')
+      const T wg1 = m.w * m.inv_h * g1, wdg = m.w * m.inv_h * dg;
+      const T d0 = m.lam * e0.tr + m.p, d1 = m.lam * e1.tr;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        su[i][i][q] = wg1 * (d1 + T(2) * m.mu * Gs[i][i]) + wdg * (d0 + T(2) * m.mu * G[i][i]);
+#pragma unroll
+        for (int k = i + 1; k < D; ++k) {
+          const int j = sym_index<D>(i, k) - D;
+          const T v = m.mu * (wg1 * e1.off[j] + wdg * e0.off[j]);
+          su[i][k][q] = v;
+          su[k][i][q] = v;
+        }
+      }
+      s0[q] = m.w * (dp1 * (psi1 + psi2 + m.p * e1.tr) + T(2) * omk * sq * (psi0 + m.p * e0.tr) +
+                     gcl * sq);
+#pragma unroll
+      for (int k = 0; k < D; ++k) sc[k][q] = kc * gsc[k][q];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) test<D, T>(nullptr, su[i], out[i]);
+  test<D, T>(s0, sc, out[D]);
+}
+
 // ---------------------------------------------------------------- Hessian
 // The Hessian at x applied to v,
 //   u-rows  int [g sigma(v_u) + g' v_c (sigma(u) + p I)] : grad phi

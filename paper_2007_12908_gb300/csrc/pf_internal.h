@@ -54,6 +54,11 @@ cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, vo
 // then each node sums its elements' in a fixed order.
 cudaError_t elem_gradient_fp64(const Geom& g, const Mat<double>& m, const double* x, double* y,
                                double* scratch, cudaStream_t st);
+// y += grad E(x) - grad E(x - s) with the difference in FP32 arithmetic from
+// FP64 x and s (every term of order one or higher in s): the gradient at x
+// from the one at x - s.
+cudaError_t elem_gradient_step(const Geom& g, const Mat<double>& m, const double* x,
+                               const double* s, double* y, cudaStream_t st);
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
                          void* y, int prec, cudaStream_t st, const int* skip = nullptr);
 // FP64 lagged Hessian: Gauss-point coefficients of x (coef holds

@@ -194,7 +194,9 @@ struct Tile<2> {
   static constexpr int X = 32, Y = 8, Z = 1, THREADS = 128;
 };
 
-enum { OP_GRAD = 0, OP_HESS = 1, OP_DIAG = 2 };
+// OP_GDIFF: y += grad E(x) - grad E(x - v), the gradient step from x - v to
+// x in the arithmetic of TC (elem_gradient_diff at x with step -v).
+enum { OP_GRAD = 0, OP_HESS = 1, OP_DIAG = 2, OP_GDIFF = 3 };
 
 // Lagged Gauss-point coefficients of the Hessian, one element per thread;
 // stored coef[(q * NCOEF + k) * NE + e] so that consecutive elements are
@@ -223,9 +225,10 @@ __global__ void __launch_bounds__(256) k_hess_coef(Geom g, Mat<T> m, const T* __
 // device-side CG stops this way without a host round trip).
 // FP32 instances are limited to 128 registers so that two CTAs (16 warps)
 // share an SM and hide the gather and barrier latency.
-template <int D, class TC, class TIO, int OP>
+// TM: precision of x in memory (converted to TC in registers).
+template <int D, class TC, class TIO, int OP, class TM = TC>
 __global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
-    k_elem_scatter(Geom g, Mat<TC> m, const TC* __restrict__ x, const TIO* __restrict__ v,
+    k_elem_scatter(Geom g, Mat<TC> m, const TM* __restrict__ x, const TIO* __restrict__ v,
                    TIO* __restrict__ y, const int* __restrict__ skip) {
   if (skip && *skip) return;
   constexpr int F = D + 1, NC = 1 << D;
@@ -245,8 +248,26 @@ __global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
     TC out[F][NC];
     if (valid) {
       TC xe[F][NC];
-      gather<D, TC>(g, x, gx, gy, gz, xe);
-      if constexpr (OP == OP_HESS) {
+      if constexpr (std::is_same<TM, TC>::value) {
+        gather<D, TC>(g, x, gx, gy, gz, xe);
+      } else {
+        TM xt[F][NC];
+        gather<D, TM>(g, x, gx, gy, gz, xt);
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+#pragma unroll
+          for (int a = 0; a < NC; ++a) xe[f][a] = TC(xt[f][a]);
+      }
+      if constexpr (OP == OP_GDIFF) {
+        TC se[F][NC];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          const long long idx = corner_node<D>(g, gx, gy, gz, a);
+#pragma unroll
+          for (int f = 0; f < F; ++f) se[f][a] = -TC(v[f * g.N + idx]);
+        }
+        elem_gradient_diff<D, TC>(xe, se, m, out);
+      } else if constexpr (OP == OP_HESS) {
         TC ve[F][NC];
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
@@ -283,7 +304,10 @@ __global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
     if (gx < g.n[0] && gy < g.n[1] && gz < g.n[2]) {
       const long long idx = gx + g.n[0] * (gy + (long long)g.n[1] * gz);
 #pragma unroll
-      for (int f = 0; f < F; ++f) y[f * g.N + idx] = TIO(acc[f][i]);
+      for (int f = 0; f < F; ++f) {
+        if constexpr (OP == OP_GDIFF) y[f * g.N + idx] -= TIO(acc[f][i]);
+        else y[f * g.N + idx] = TIO(acc[f][i]);
+      }
     }
   }
 }
@@ -294,13 +318,19 @@ static dim3 scatter_grid(const Geom& g) {
               D == 3 ? (g.n[2] + Tile<D>::Z - 1) / Tile<D>::Z : 1);
 }
 
-template <int D, class TC, class TIO, int OP>
+template <int D, class TC, class TIO, int OP, class TM = TC>
 static cudaError_t launch_scatter(const Geom& g, const Mat<double>& m, const void* x,
                                   const void* v, void* y, const int* skip, cudaStream_t st) {
-  k_elem_scatter<D, TC, TIO, OP><<<scatter_grid<D>(g), Tile<D>::THREADS, 0, st>>>(
-      g, cast_mat<TC>(m), static_cast<const TC*>(x), static_cast<const TIO*>(v),
+  k_elem_scatter<D, TC, TIO, OP, TM><<<scatter_grid<D>(g), Tile<D>::THREADS, 0, st>>>(
+      g, cast_mat<TC>(m), static_cast<const TM*>(x), static_cast<const TIO*>(v),
       static_cast<TIO*>(y), skip);
   return cudaGetLastError();
+}
+
+cudaError_t elem_gradient_step(const Geom& g, const Mat<double>& m, const double* x,
+                               const double* s, double* y, cudaStream_t st) {
+  if (g.dim == 3) return launch_scatter<3, float, double, OP_GDIFF, double>(g, m, x, s, y, nullptr, st);
+  return launch_scatter<2, float, double, OP_GDIFF, double>(g, m, x, s, y, nullptr, st);
 }
 
 cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, void* y, int prec,

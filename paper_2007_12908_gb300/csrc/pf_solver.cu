@@ -11,6 +11,7 @@
 #include <cmath>
 #include <string>
 #include <type_traits>
+#include <vector>
 
 #include "pf_hier.h"
 #include "pf_reduce.cuh"
@@ -122,12 +123,14 @@ struct Solver {
   cudaStream_t st;
   int L, F;
   bool mixed;
-  // the finest level's B.g holds grad f at its current B.x (set by pg_norm,
-  // cleared whenever that x or the gradient buffer changes)
-  bool fine_grad_valid = false;
+  // What each level's B.g holds: G_NONE, G_AT_X (grad h at B.x) or G_STEP
+  // (grad h at B.x - B.s: an accepted step not yet applied to the gradient)
+  enum { G_NONE = 0, G_AT_X = 1, G_STEP = 2 };
+  std::vector<int> gstate;
 
   Solver(pf_hierarchy* h, const pf_rmtr_params& p, pf_rmtr_stats& s)
-      : H(h), P(p), S(s), st(h->st), L(h->L), F(h->dim + 1), mixed(p.precision == PF_FP32) {}
+      : H(h), P(p), S(s), st(h->st), L(h->L), F(h->dim + 1), mixed(p.precision == PF_FP32),
+        gstate(h->L, G_NONE) {}
 
   // ---------------------------------------------------------------- helpers
   template <class Fn>
@@ -314,6 +317,26 @@ struct Solver {
     dH(l, d, B.gout == nullptr ? B.t2 : B.t2);
     const double* e = B.t2;
     map(B.n, [=] __device__(long long i) { out[i] += dg[i] + e[i]; });
+  }
+
+  // Levels whose gradient follows accepted steps by FP32 gradient steps
+  // (mixed mode, FP32-Hessian levels whose model gradient differs from that
+  // of f~ by a constant).  The exact FP64 gradient is still taken for every
+  // stopping test and at every new coarse start.
+  bool step_update(int l) const { return mixed32(l) && !galerkin(l); }
+
+  // B.g := grad h(B.x)
+  void grad_at(int l) {
+    LevelBuf& B = H->lv[l];
+    if (gstate[l] == G_STEP && step_update(l)) {
+      // grad h(x) = grad h(x - s) + [grad f~(x) - grad f~(x - s)]
+      ck(elem_gradient_step(H->geo[l], H->mat[l], B.x, B.s, B.g, st), "gradient_step");
+      S.launches += 1;
+      S.fe_gradient += frac(l);
+    } else if (gstate[l] != G_AT_X) {
+      grad_h(l, B.x, B.g);
+    }
+    gstate[l] = G_AT_X;
   }
 
   // h(x + s) - h(x) without subtracting totals; gx = grad h(x) (FP64).
@@ -636,6 +659,7 @@ struct Solver {
     if (rho > P.eta1) {
       const double *s = B.s, *lb = B.lb, *ub = B.ub;
       map(B.n, [=] __device__(long long i) { x[i] = fmin(fmax(x[i] + s[i], lb[i]), ub[i]); });
+      gstate[l] = gstate[l] == G_AT_X ? G_STEP : G_NONE;
     }
     if (rho < P.eta1) delta = P.gamma1 * delta;
     else if (rho > P.eta2) delta = std::min(P.gamma2 * delta, P.delta_max);
@@ -646,8 +670,7 @@ struct Solver {
     LevelBuf& B = H->lv[l];
     double chi0 = -1.0;
     for (int it = 0; it < iters; ++it) {
-      if (!(finest(l) && fine_grad_valid)) grad_h(l, B.x, B.g);
-      fine_grad_valid = false;
+      grad_at(l);
       if (P.level_rtol > 0.0 && !finest(l)) {
         // stop once the level's projected gradient fell by level_rtol
         const double chi = pg_norm_level(l);
@@ -701,7 +724,7 @@ struct Solver {
     }
     // dg = R grad h^l(x_mu1) - grad f~(x0); g0 = R grad h^l(x_mu1) is the
     // coarse model's gradient at x0 (first-order coherence)
-    grad_h(l, B.x, B.g);
+    grad_at(l);
     ck(xfer_restrict(gc, gf, F, B.g, C.g0, 0, false, st), "restrict");
     S.launches += 1;
     gradient(l - 1, C.x0, C.t1);
@@ -711,6 +734,9 @@ struct Solver {
       map(C.n, [=] __device__(long long i) { dg[i] = g0[i] - t[i]; });
     }
     set_lag(l - 1, C.x0);
+    // the coarse iterate starts at x0, where grad h^{l-1} = g0
+    copy(C.g, C.g0, C.n);
+    gstate[l - 1] = G_AT_X;
     double dc = delta;
     if (l - 1 == 0) nonlinear_solve(0, dc, P.coarse_its, P.cg_coarse);
     else vcycle(l - 1, dc);
@@ -750,7 +776,7 @@ struct Solver {
   double pg_norm(const double* x) {
     LevelBuf& B = H->lv[L - 1];
     gradient(L - 1, x, B.g);
-    fine_grad_valid = (x == B.x);
+    gstate[L - 1] = (x == B.x) ? G_AT_X : G_NONE;
     const double *g = B.g, *lb = B.lb, *ub = B.ub;
     double r;
     reduce<1, OpSum>(B.n, [=] __device__(long long i, double(&v)[1]) {

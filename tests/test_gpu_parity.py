@@ -73,6 +73,29 @@ def test_hessvec_fp32(pf, dim, nc, L, hc):
     assert relinf(host(gr), O.gradient(g, Ho.prm, x)) <= TOL32
 
 
+@pytest.mark.parametrize("dim,nc,L,hc", SMALL[:2])
+@pytest.mark.parametrize("k_res", [0.0, 0.01])
+@pytest.mark.parametrize("scale", [0.1, 1e-6])
+def test_mixed_difference_kernels(pf, dim, nc, L, hc, k_res, scale):
+    """FP32 higher-order energy-difference coefficients and the FP32 gradient
+    step: their error is relative to the size of the change along s, at any
+    step size (no difference of two large totals is formed)."""
+    H, Ho = pair(dim, nc, L, hc, E=1.3, nu=0.27, Gc=0.9, k_res=k_res, p=0.05)
+    level = L - 1
+    g = Ho.grids[level]
+    x = PI.random_state(300, dim, g.N, u_scale=0.05)
+    s = scale * PI.random_direction(301, x.size)
+    go = O.gradient(g, Ho.prm, x)
+    a = pf.energy_diff_mixed(H, level, dev(x), dev(s), dev(go))
+    ao = O.energy_diff_coeffs(g, Ho.prm, x, s)
+    assert abs(a[0] - ao[0]) <= 1e-9 * abs(ao[0])
+    assert np.max(np.abs(a[1:] - ao[1:])) <= TOL32 * np.max(np.abs(ao[1:]))
+    g_before = O.gradient(g, Ho.prm, x - s)
+    y = pf.gradient_step(H, level, dev(x), dev(s), dev(g_before))
+    change = go - g_before
+    assert np.max(np.abs(host(y) - go)) <= TOL32 * np.max(np.abs(change))
+
+
 def test_deterministic(pf):
     H, Ho = pair(3, (10, 7, 6), 2, 1 / 9, p=1e-3)
     g = Ho.grids[-1]
