@@ -26,22 +26,6 @@ struct LevelBuf {
   double* stencil = nullptr;  // assembled lagged FP64 Hessian (3^d block stencil)
 };
 
-// Device-resident control block of one projected CG run: the scalars each
-// iteration needs and the reason it stopped, updated by the last block of
-// each reduction so the host only polls it.
-struct CgCtrl {
-  double rr;      // r.r of the current residual
-  double rz;      // r.M^-1 r (preconditioned CG)
-  double tol;     // forcing tolerance on ||r||
-  double alpha;   // step of the current iteration
-  double beta;    // direction update of the current iteration
-  double kappa;   // p.Hp of the current iteration
-  int done;       // 1 once the run has stopped; later launches are no-ops
-  int state;      // why it stopped (CG_*)
-  int used;       // Hessian-vector products spent by the CG loop
-  int cg_max;     // budget
-};
-enum { CG_RUNNING = 0, CG_NEGCURV = 1, CG_LEAVE = 2, CG_CONV = 3, CG_BUDGET = 4 };
 
 void set_error(const std::string& msg);
 

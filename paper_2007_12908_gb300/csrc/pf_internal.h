@@ -26,6 +26,23 @@ struct Scratch {
   unsigned* counter;  // 1, zero between reductions
 };
 
+// Device-resident control block of one projected CG run: the scalars each
+// iteration needs and the reason it stopped, updated by the last block of
+// each reduction so the host only polls it.
+struct CgCtrl {
+  double rr;      // r.r of the current residual
+  double rz;      // r.M^-1 r (preconditioned CG)
+  double tol;     // forcing tolerance on ||r||
+  double alpha;   // step of the current iteration
+  double beta;    // direction update of the current iteration
+  double kappa;   // p.Hp of the current iteration
+  int done;       // 1 once the run has stopped; later launches are no-ops
+  int state;      // why it stopped (CG_*)
+  int used;       // Hessian-vector products spent by the CG loop
+  int cg_max;     // budget
+};
+enum { CG_RUNNING = 0, CG_NEGCURV = 1, CG_LEAVE = 2, CG_CONV = 3, CG_BUDGET = 4 };
+
 Geom make_geom(int dim, const int n[3], double h);
 Mat<double> make_mat(const Geom& g, double E, double nu, double Gc, double ls, double k,
                      double p);

@@ -456,81 +456,101 @@ __device__ __forceinline__ void shape_tables(int a, int q, double& na, double (&
   }
 }
 
+// One thread per (node i, stencil offset o): the 4x4 (3x3 in 2D) block of
+// the lagged Hessian coupling node i with node i + o, summed over the corner
+// pairs (a, b = a + o) of the elements that contain both and over their
+// Gauss points.  Every entry of S is written once (no atomics, no clearing);
+// per pair the Gauss-point sum is formed first, then added to the block.
 template <int D>
 __global__ void __launch_bounds__(128) k_assemble(Geom g, Mat<double> m,
                                                   const double* __restrict__ coef,
                                                   double* __restrict__ S) {
-  constexpr int F = D + 1, NC = 1 << D, NCF = NCoef<D>::value;
+  constexpr int F = D + 1, NC = 1 << D, NCF = NCoef<D>::value, NO = D == 3 ? 27 : 9;
   const double kc = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long total = NO * g.N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int o = int(t / g.N);
+    const long long i = t - (long long)o * g.N;
     const int ix = int(i % g.n[0]);
     const long long r = i / g.n[0];
     const int iy = int(r % g.n[1]);
     const int iz = int(r / g.n[1]);
     const int ic[3] = {ix, iy, iz};
+    int dof[3] = {0, 0, 0};  // o = sum_k (d_k + 1) 3^k
+    {
+      int oo = o;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        dof[k] = oo % 3 - 1;
+        oo /= 3;
+      }
+    }
+    double tot[F][F];
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int h = 0; h < F; ++h) tot[f][h] = 0.0;
     for (int a = 0; a < NC; ++a) {  // node i is corner a of element i - corner(a)
-      int ec[3] = {0, 0, 0};
+      int ec[3] = {0, 0, 0}, b = 0;
       bool ok = true;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        ec[k] = ic[k] - ((a >> k) & 1);
-        ok = ok && ec[k] >= 0 && ec[k] < g.ne[k];
+        const int ak = (a >> k) & 1, bk = ak + dof[k];
+        ec[k] = ic[k] - ak;
+        ok = ok && ec[k] >= 0 && ec[k] < g.ne[k] && bk >= 0 && bk <= 1;
+        b |= (bk & 1) << k;
       }
       if (!ok) continue;
       const long long e = ec[0] + (long long)g.ne[0] * (ec[1] + (long long)g.ne[1] * ec[2]);
-      for (int b = 0; b < NC; ++b) {
-        int o = 0, stride = 1;
+      double blk[F][F];
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          o += (((b >> k) & 1) - ((a >> k) & 1) + 1) * stride;
-          stride *= 3;
-        }
-        double blk[F][F];
+      for (int f = 0; f < F; ++f)
 #pragma unroll
-        for (int f = 0; f < F; ++f)
+        for (int h = 0; h < F; ++h) blk[f][h] = 0.0;
 #pragma unroll
-          for (int h = 0; h < F; ++h) blk[f][h] = 0.0;
+      for (int q = 0; q < NC; ++q) {
+        double na, nb, da[D], db[D];
+        shape_tables<D>(a, q, na, da);
+        shape_tables<D>(b, q, nb, db);
+        const double A = coef[(q * NCF + 0) * g.NE + e];
+        const double M = coef[(q * NCF + 1) * g.NE + e];
+        double B[D][D];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          double na, nb, da[D], db[D];
-          shape_tables<D>(a, q, na, da);
-          shape_tables<D>(b, q, nb, db);
-          const double A = coef[(q * NCF + 0) * g.NE + e];
-          const double M = coef[(q * NCF + 1) * g.NE + e];
-          double B[D][D];
+        for (int ii = 0; ii < D; ++ii)
 #pragma unroll
-          for (int ii = 0; ii < D; ++ii)
+          for (int kk = 0; kk < D; ++kk) B[ii][kk] = coef[(q * NCF + 2 + sym_index<D>(ii, kk)) * g.NE + e];
+        double dd = 0.0;
 #pragma unroll
-            for (int kk = 0; kk < D; ++kk) B[ii][kk] = coef[(q * NCF + 2 + sym_index<D>(ii, kk)) * g.NE + e];
-          double dd = 0.0;
+        for (int k = 0; k < D; ++k) dd += da[k] * db[k];
 #pragma unroll
-          for (int k = 0; k < D; ++k) dd += da[k] * db[k];
+        for (int ii = 0; ii < D; ++ii) {
 #pragma unroll
-          for (int ii = 0; ii < D; ++ii) {
-#pragma unroll
-            for (int jj = 0; jj < D; ++jj) {
-              double v = m.lam * da[ii] * db[jj] + m.mu * da[jj] * db[ii];
-              if (ii == jj) v += m.mu * dd;
-              blk[ii][jj] += A * v;
-            }
-            double bu = 0.0, bc = 0.0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-              bu += B[ii][k] * da[k];
-              bc += B[ii][k] * db[k];
-            }
-            blk[ii][D] += bu * nb;  // u_i(a) - c(b)
-            blk[D][ii] += na * bc;  // c(a) - u_i(b)
+          for (int jj = 0; jj < D; ++jj) {
+            double v = m.lam * da[ii] * db[jj] + m.mu * da[jj] * db[ii];
+            if (ii == jj) v += m.mu * dd;
+            blk[ii][jj] += A * v;
           }
-          blk[D][D] += M * na * nb + kc * dd;
+          double bu = 0.0, bc = 0.0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            bu += B[ii][k] * da[k];
+            bc += B[ii][k] * db[k];
+          }
+          blk[ii][D] += bu * nb;  // u_i(a) - c(b)
+          blk[D][ii] += na * bc;  // c(a) - u_i(b)
         }
-#pragma unroll
-        for (int f = 0; f < F; ++f)
-#pragma unroll
-          for (int h = 0; h < F; ++h) S[((long long)(o * F + f) * F + h) * g.N + i] += blk[f][h];
+        blk[D][D] += M * na * nb + kc * dd;
       }
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int h = 0; h < F; ++h) tot[f][h] += blk[f][h];
     }
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int h = 0; h < F; ++h) S[((long long)(o * F + f) * F + h) * g.N + i] = tot[f][h];
   }
 }
 
@@ -569,11 +589,42 @@ __global__ void __launch_bounds__(256) k_stencil_apply(Geom g, const double* __r
   }
 }
 
+// The product on grids too small to fill the SMs with one thread per node:
+// one thread per (node, output row), the same summation order per output.
+template <int D>
+__global__ void __launch_bounds__(128) k_stencil_apply_rows(Geom g, const double* __restrict__ S,
+                                                            const double* __restrict__ v,
+                                                            double* __restrict__ y,
+                                                            const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int F = D + 1, NO = D == 3 ? 27 : 9;
+  const long long total = F * g.N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int f = int(t / g.N);
+    const long long i = t - (long long)f * g.N;
+    const int ix = int(i % g.n[0]);
+    const long long r = i / g.n[0];
+    const int iy = int(r % g.n[1]);
+    const int iz = int(r / g.n[1]);
+    double acc = 0.0;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = D == 3 ? o / 9 - 1 : 0;
+      const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+      if (jx < 0 || jx >= g.n[0] || jy < 0 || jy >= g.n[1] || jz < 0 || jz >= g.n[2]) continue;
+      const long long j = jx + g.n[0] * (jy + (long long)g.n[1] * jz);
+#pragma unroll
+      for (int h = 0; h < F; ++h) acc += S[((long long)(o * F + f) * F + h) * g.N + i] * v[h * g.N + j];
+    }
+    y[f * g.N + i] = acc;
+  }
+}
+
 cudaError_t stencil_assemble(const Geom& g, const Mat<double>& m, const double* coef, double* S,
                              cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * stencil_count(g), st);
-  if (e != cudaSuccess) return e;
-  const int nb = int(std::min<long long>((g.N + 127) / 128, 16LL * 1216));
+  const long long total = (g.dim == 3 ? 27LL : 9LL) * g.N;
+  const int nb = int(std::min<long long>((total + 127) / 128, 16LL * 1216));
   if (g.dim == 3) k_assemble<3><<<nb, 128, 0, st>>>(g, m, coef, S);
   else k_assemble<2><<<nb, 128, 0, st>>>(g, m, coef, S);
   return cudaGetLastError();
@@ -581,6 +632,13 @@ cudaError_t stencil_assemble(const Geom& g, const Mat<double>& m, const double* 
 
 cudaError_t stencil_apply(const Geom& g, const double* S, const double* v, double* y,
                           cudaStream_t st, const int* skip) {
+  if (g.N < 152LL * 512) {  // fewer nodes than two 256-thread CTAs per SM
+    const long long total = (g.dim + 1) * g.N;
+    const int nb = int(std::min<long long>((total + 127) / 128, 16LL * 1216));
+    if (g.dim == 3) k_stencil_apply_rows<3><<<nb, 128, 0, st>>>(g, S, v, y, skip);
+    else k_stencil_apply_rows<2><<<nb, 128, 0, st>>>(g, S, v, y, skip);
+    return cudaGetLastError();
+  }
   const int nb = int(std::min<long long>((g.N + 255) / 256, 16LL * 1216));
   if (g.dim == 3) k_stencil_apply<3><<<nb, 256, 0, st>>>(g, S, v, y, skip);
   else k_stencil_apply<2><<<nb, 256, 0, st>>>(g, S, v, y, skip);

@@ -93,6 +93,187 @@ __global__ void __launch_bounds__(256) k_red(long long n, F f, double* partials,
   grid_finish<K, Op>(acc, partials, counter, out);
 }
 
+// ---------------------------------------------------------------- FP32 CG passes
+// The vector passes of one projected-CG iteration on FP32 vectors, on groups
+// of four dofs (n a multiple of 4, 16-byte aligned vectors; 16-byte loads
+// keep more bytes in flight per instruction).  ga/gb are the free gaps
+// (a < 0 < b on the free set, both 0 elsewhere); off the free set r, p and
+// w are 0 and stay 0, so a group whose four dofs are all outside reads only
+// its gaps.
+__device__ __forceinline__ float4 ld4(const float* v, long long j) {
+  return reinterpret_cast<const float4*>(v)[j];
+}
+__device__ __forceinline__ void st4(float* v, long long j, float4 x) {
+  reinterpret_cast<float4*>(v)[j] = x;
+}
+__device__ __forceinline__ bool any_free(float4 a) {
+  return (a.x < 0.f) | (a.y < 0.f) | (a.z < 0.f) | (a.w < 0.f);
+}
+
+// Restart of the CG loop at s: r = -(g + Hs) and p = M^-1 r on the free set
+// of s (0 elsewhere), w = 0, the gaps of s; (r.r, r.M^-1 r) to out.
+struct CgInitOp {
+  __device__ __forceinline__ static void lane(float lo, float hi, float s, float g, float hs,
+                                              float m, float& r, float& p, float& a, float& b,
+                                              float& rr, float& rz) {
+    const float ai = lo - s, bi = hi - s;
+    const bool fr = ai < 0.f && 0.f < bi;
+    const float ri = fr ? -(g + hs) : 0.f;
+    const float zi = m * ri;
+    r = ri;
+    p = zi;
+    a = fr ? ai : 0.f;
+    b = fr ? bi : 0.f;
+    rr += ri * ri;
+    rz += ri * zi;
+  }
+};
+
+__global__ void __launch_bounds__(256) k_cg_init4(long long n4, const float* __restrict__ lo,
+                                                  const float* __restrict__ hi,
+                                                  const float* __restrict__ s,
+                                                  const float* __restrict__ g,
+                                                  const float* __restrict__ Hs,
+                                                  const float* __restrict__ mi, bool pc,
+                                                  float* __restrict__ r, float* __restrict__ p,
+                                                  float* __restrict__ w, float* __restrict__ ga,
+                                                  float* __restrict__ gb, double* partials,
+                                                  unsigned* counter, double* out) {
+  float rr = 0.f, rz = 0.f;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4;
+       j += (long long)gridDim.x * blockDim.x) {
+    const float4 l4 = ld4(lo, j), h4 = ld4(hi, j), s4 = ld4(s, j);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 g4 = z4, hs4 = z4, m4 = make_float4(1.f, 1.f, 1.f, 1.f);
+    const float4 a4 = make_float4(l4.x - s4.x, l4.y - s4.y, l4.z - s4.z, l4.w - s4.w);
+    const float4 b4 = make_float4(h4.x - s4.x, h4.y - s4.y, h4.z - s4.z, h4.w - s4.w);
+    const bool any = ((a4.x < 0.f) & (b4.x > 0.f)) | ((a4.y < 0.f) & (b4.y > 0.f)) |
+                     ((a4.z < 0.f) & (b4.z > 0.f)) | ((a4.w < 0.f) & (b4.w > 0.f));
+    if (any) {
+      g4 = ld4(g, j);
+      hs4 = ld4(Hs, j);
+      if (pc) m4 = ld4(mi, j);
+    }
+    float4 r4, p4, ga4, gb4;
+    CgInitOp::lane(l4.x, h4.x, s4.x, g4.x, hs4.x, m4.x, r4.x, p4.x, ga4.x, gb4.x, rr, rz);
+    CgInitOp::lane(l4.y, h4.y, s4.y, g4.y, hs4.y, m4.y, r4.y, p4.y, ga4.y, gb4.y, rr, rz);
+    CgInitOp::lane(l4.z, h4.z, s4.z, g4.z, hs4.z, m4.z, r4.z, p4.z, ga4.z, gb4.z, rr, rz);
+    CgInitOp::lane(l4.w, h4.w, s4.w, g4.w, hs4.w, m4.w, r4.w, p4.w, ga4.w, gb4.w, rr, rz);
+    st4(r, j, r4);
+    st4(p, j, p4);
+    st4(w, j, z4);
+    st4(ga, j, ga4);
+    st4(gb, j, gb4);
+  }
+  double acc[2] = {double(rr), double(rz)};
+  grid_finish<2, OpSum>(acc, partials, counter, out);
+}
+
+// Update after the product q = H p: w += alpha p, r -= alpha q (free set);
+// the last block tests the box, the forcing term and the budget, and sets
+// beta (CG_* states of the control block).
+__device__ __forceinline__ void cg_update_lane(float al, float a, float b, float q, float p,
+                                               float& w, float& r, float m, float& rr, float& lv,
+                                               float& rz) {
+  const float qi = a < 0.f ? q : 0.f;
+  w = w + al * p;
+  r = r - al * qi;
+  rr += r * r;
+  lv += ((w < a) | (w > b)) ? 1.f : 0.f;
+  rz += r * (m * r);
+}
+
+__global__ void __launch_bounds__(256) k_cg_update4(long long n4, const float* __restrict__ ga,
+                                                    const float* __restrict__ gb,
+                                                    const float* __restrict__ q,
+                                                    const float* __restrict__ p,
+                                                    const float* __restrict__ mi, bool pc,
+                                                    float* __restrict__ w, float* __restrict__ r,
+                                                    CgCtrl* c, double* partials,
+                                                    unsigned* counter) {
+  if (c->done) return;
+  const float al = float(c->alpha);
+  float rr = 0.f, lv = 0.f, rz = 0.f;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4;
+       j += (long long)gridDim.x * blockDim.x) {
+    const float4 a4 = ld4(ga, j);
+    if (!any_free(a4)) continue;
+    const float4 b4 = ld4(gb, j), q4 = ld4(q, j), p4 = ld4(p, j);
+    float4 w4 = ld4(w, j), r4 = ld4(r, j);
+    const float4 m4 = pc ? ld4(mi, j) : make_float4(1.f, 1.f, 1.f, 1.f);
+    cg_update_lane(al, a4.x, b4.x, q4.x, p4.x, w4.x, r4.x, m4.x, rr, lv, rz);
+    cg_update_lane(al, a4.y, b4.y, q4.y, p4.y, w4.y, r4.y, m4.y, rr, lv, rz);
+    cg_update_lane(al, a4.z, b4.z, q4.z, p4.z, w4.z, r4.z, m4.z, rr, lv, rz);
+    cg_update_lane(al, a4.w, b4.w, q4.w, p4.w, w4.w, r4.w, m4.w, rr, lv, rz);
+    st4(w, j, w4);
+    st4(r, j, r4);
+  }
+  double acc[3] = {double(rr), double(lv), double(rz)};
+  auto fin = [c](double(&a)[3]) {
+    if (a[1] > 0.0) {
+      c->done = 1;
+      c->state = CG_LEAVE;
+    } else if (sqrt(a[0]) <= c->tol) {
+      c->done = 1;
+      c->state = CG_CONV;
+    } else if (c->used >= c->cg_max) {
+      c->done = 1;
+      c->state = CG_BUDGET;
+    } else {
+      c->beta = a[2] / c->rz;
+      c->rr = a[0];
+      c->rz = a[2];
+    }
+  };
+  grid_finish_fn<3, OpSum>(acc, partials, counter, fin);
+}
+
+// p . q for q = H p, and the step alpha = r.M^-1 r / p.q (or a stop on
+// non-positive curvature); a group with p = 0 (outside the free set) reads
+// only p.
+__global__ void __launch_bounds__(256) k_cg_dot4(long long n4, const float* __restrict__ p,
+                                                 const float* __restrict__ q, CgCtrl* c,
+                                                 double* partials, unsigned* counter) {
+  if (c->done) return;
+  float pq = 0.f;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4;
+       j += (long long)gridDim.x * blockDim.x) {
+    const float4 p4 = ld4(p, j);
+    if (p4.x == 0.f && p4.y == 0.f && p4.z == 0.f && p4.w == 0.f) continue;
+    const float4 q4 = ld4(q, j);
+    pq += p4.x * q4.x + p4.y * q4.y + p4.z * q4.z + p4.w * q4.w;
+  }
+  double acc[1] = {double(pq)};
+  auto fin = [c](double(&a)[1]) {
+    c->kappa = a[0];
+    c->used += 1;
+    if (a[0] <= 0.0) {
+      c->done = 1;
+      c->state = CG_NEGCURV;
+    } else {
+      c->alpha = c->rz / a[0];
+    }
+  };
+  grid_finish_fn<1, OpSum>(acc, partials, counter, fin);
+}
+
+// Direction update p = M^-1 r + beta p (free set; p stays 0 elsewhere).
+__global__ void __launch_bounds__(256) k_cg_dir4(long long n4, const float* __restrict__ ga,
+                                                 const float* __restrict__ r,
+                                                 const float* __restrict__ mi, bool pc,
+                                                 float* __restrict__ p, const CgCtrl* c) {
+  if (c->done) return;
+  const float be = float(c->beta);
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4;
+       j += (long long)gridDim.x * blockDim.x) {
+    if (!any_free(ld4(ga, j))) continue;
+    const float4 r4 = ld4(r, j), p4 = ld4(p, j);
+    const float4 m4 = pc ? ld4(mi, j) : make_float4(1.f, 1.f, 1.f, 1.f);
+    st4(p, j, make_float4(m4.x * r4.x + be * p4.x, m4.y * r4.y + be * p4.y,
+                          m4.z * r4.z + be * p4.z, m4.w * r4.w + be * p4.w));
+  }
+}
+
 static int map_grid(long long n) {
   long long b = (n + 255) / 256;
   return int(std::max(1LL, std::min(b, 4LL * 1216)));
@@ -499,19 +680,31 @@ struct Solver {
     while (used < cg_max) {
       double rr2[2];
       // residual of the model on the free set of s, its gaps, p = M^-1 r
-      reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
-        const V a = lo[i] - s[i], b = hi[i] - s[i];
-        const bool fr = a < Z && Z < b;
-        const V ri = fr ? -(g[i] + Hs[i]) : Z;
-        const V zi = pc ? mi[i] * ri : ri;
-        r[i] = ri;
-        p[i] = zi;
-        w[i] = Z;
-        ga[i] = fr ? a : Z;
-        gb[i] = fr ? b : Z;
-        o[0] = ri * ri;
-        o[1] = ri * zi;
-      }, rr2);
+      if constexpr (std::is_same<V, float>::value) {
+        if (n % 4 == 0) {
+          const long long n4 = n / 4;
+          k_cg_init4<<<reduce_grid(n4), 256, 0, st>>>(n4, lo, hi, s, g, Hs, mi, pc, r, p, w, ga, gb,
+                                                       H->scratch.partials, H->scratch.counter,
+                                                       H->d_res);
+          ck(cudaGetLastError(), "cg_init");
+          S.launches += 1;
+          fetch(2, rr2);
+        }
+      }
+      if (!(std::is_same<V, float>::value && n % 4 == 0))
+        reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
+          const V a = lo[i] - s[i], b = hi[i] - s[i];
+          const bool fr = a < Z && Z < b;
+          const V ri = fr ? -(g[i] + Hs[i]) : Z;
+          const V zi = pc ? mi[i] * ri : ri;
+          r[i] = ri;
+          p[i] = zi;
+          w[i] = Z;
+          ga[i] = fr ? a : Z;
+          gb[i] = fr ? b : Z;
+          o[0] = ri * ri;
+          o[1] = ri * zi;
+        }, rr2);
       const double rr = rr2[0];
       if (tol < 0.0) {
         const double r0 = std::sqrt(rr);
@@ -531,48 +724,74 @@ struct Solver {
       int chunk = 2;
       for (;;) {
         for (int k = 0; k < chunk; ++k) {
-          hv<V>(l, p, q, skip, false);
-          red_fin<1, OpSum, V>(n, [=] __device__(long long i, V(&o)[1]) { o[0] = p[i] * q[i]; },
-                               [=] __device__(double(&a)[1]) {
-            c->kappa = a[0];
-            c->used += 1;
-            if (a[0] <= 0.0) {
-              c->done = 1;
-              c->state = CG_NEGCURV;
-            } else {
-              c->alpha = c->rz / a[0];
-            }
-          }, skip);
-          red_fin<3, OpSum, V>(n, [=] __device__(long long i, V(&o)[3]) {
-            const V al = V(c->alpha);
-            const V a = ga[i];
-            const V qi = a < Z ? q[i] : Z;
-            const V wi = w[i] + al * p[i];
-            w[i] = wi;
-            const V ri = r[i] - al * qi;
-            r[i] = ri;
-            o[0] = ri * ri;
-            o[1] = (wi < a || wi > gb[i]) ? V(1) : Z;
-            o[2] = ri * (pc ? mi[i] * ri : ri);
-          }, [=] __device__(double(&a)[3]) {
-            if (a[1] > 0.0) {
-              c->done = 1;
-              c->state = CG_LEAVE;
-            } else if (sqrt(a[0]) <= c->tol) {
-              c->done = 1;
-              c->state = CG_CONV;
-            } else if (c->used >= c->cg_max) {
-              c->done = 1;
-              c->state = CG_BUDGET;
-            } else {
-              c->beta = a[2] / c->rz;
-              c->rr = a[0];
-              c->rz = a[2];
-            }
-          }, skip);
-          map_skip(n, [=] __device__(long long i) {
-            p[i] = (pc ? mi[i] * r[i] : r[i]) + V(c->beta) * p[i];
-          }, skip);
+          if (std::is_same<V, float>::value && n % 4 == 0) {
+            hv<V>(l, p, q, skip, false);
+            const long long n4 = n / 4;
+            k_cg_dot4<<<reduce_grid(n4), 256, 0, st>>>(n4, reinterpret_cast<const float*>(p),
+                                                      reinterpret_cast<const float*>(q), c,
+                                                      H->scratch.partials, H->scratch.counter);
+            ck(cudaGetLastError(), "cg_dot");
+            S.launches += 1;
+          } else {
+            hv<V>(l, p, q, skip, false);
+            red_fin<1, OpSum, V>(n, [=] __device__(long long i, V(&o)[1]) { o[0] = p[i] * q[i]; },
+                                 [=] __device__(double(&a)[1]) {
+              c->kappa = a[0];
+              c->used += 1;
+              if (a[0] <= 0.0) {
+                c->done = 1;
+                c->state = CG_NEGCURV;
+              } else {
+                c->alpha = c->rz / a[0];
+              }
+            }, skip);
+          }
+          if (std::is_same<V, float>::value && n % 4 == 0) {
+            const long long n4 = n / 4;
+            const float *fa = reinterpret_cast<const float*>(ga),
+                        *fb = reinterpret_cast<const float*>(gb),
+                        *fq = reinterpret_cast<const float*>(q),
+                        *fm = reinterpret_cast<const float*>(mi);
+            float *fw = reinterpret_cast<float*>(w), *fr = reinterpret_cast<float*>(r),
+                  *fp = reinterpret_cast<float*>(p);
+            k_cg_update4<<<reduce_grid(n4), 256, 0, st>>>(n4, fa, fb, fq, fp, fm, pc, fw, fr, c,
+                                                         H->scratch.partials, H->scratch.counter);
+            ck(cudaGetLastError(), "cg_update");
+            k_cg_dir4<<<reduce_grid(n4), 256, 0, st>>>(n4, fa, fr, fm, pc, fp, c);
+            ck(cudaGetLastError(), "cg_dir");
+            S.launches += 2;
+          } else {
+            red_fin<3, OpSum, V>(n, [=] __device__(long long i, V(&o)[3]) {
+              const V al = V(c->alpha);
+              const V a = ga[i];
+              const V qi = a < Z ? q[i] : Z;
+              const V wi = w[i] + al * p[i];
+              w[i] = wi;
+              const V ri = r[i] - al * qi;
+              r[i] = ri;
+              o[0] = ri * ri;
+              o[1] = (wi < a || wi > gb[i]) ? V(1) : Z;
+              o[2] = ri * (pc ? mi[i] * ri : ri);
+            }, [=] __device__(double(&a)[3]) {
+              if (a[1] > 0.0) {
+                c->done = 1;
+                c->state = CG_LEAVE;
+              } else if (sqrt(a[0]) <= c->tol) {
+                c->done = 1;
+                c->state = CG_CONV;
+              } else if (c->used >= c->cg_max) {
+                c->done = 1;
+                c->state = CG_BUDGET;
+              } else {
+                c->beta = a[2] / c->rz;
+                c->rr = a[0];
+                c->rz = a[2];
+              }
+            }, skip);
+            map_skip(n, [=] __device__(long long i) {
+              p[i] = (pc ? mi[i] * r[i] : r[i]) + V(c->beta) * p[i];
+            }, skip);
+          }
         }
         ck(cudaMemcpyAsync(H->h_ctrl, c, sizeof(CgCtrl), cudaMemcpyDeviceToHost, st), "ctrl");
         ck(cudaStreamSynchronize(st), "sync");
