@@ -312,6 +312,87 @@ __global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
   }
 }
 
+// 3D FP32 Hessian product with the tile's inputs staged in shared memory.
+// A CTA owns 8^3 nodes and evaluates the 9^3 elements touching them; their
+// corners span the 10^3 nodes [o-1, o+8] per axis.  Those nodes' x_lag and v
+// are loaded once per tile (coalesced along x, converted from TV) and kept
+// as one float4 per node, so an element reads its 8 corners of each vector
+// with 8 16-byte shared loads at fixed offsets, and the colour-phase sums
+// add one float4 per node.  Same element algebra and the same fixed
+// summation order as k_elem_scatter<3, float, ..., OP_HESS>.
+template <class TV>
+__global__ void __launch_bounds__(256, 2)
+    k_hess_tile3(Geom g, Mat<float> m, const float* __restrict__ x, const TV* __restrict__ v,
+                 TV* __restrict__ y, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int T = 8, E = T + 1, NN = T + 2, NH = NN * NN * NN, NT = 256;
+  __shared__ float4 xs[NH], vs[NH];
+  __shared__ float4 acc[T * T * T];
+  const int ox = blockIdx.x * T, oy = blockIdx.y * T, oz = blockIdx.z * T;
+  const int nx0 = g.n[0], ny0 = g.n[1], nz0 = g.n[2];
+  const long long N = g.N;
+  for (int j = threadIdx.x; j < NH; j += NT) {
+    const int i = j % NN, jj = (j / NN) % NN, k = j / (NN * NN);
+    const int gx = ox - 1 + i, gy = oy - 1 + jj, gz = oz - 1 + k;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (gx >= 0 && gx < nx0 && gy >= 0 && gy < ny0 && gz >= 0 && gz < nz0) {
+      const long long idx = gx + (long long)nx0 * (gy + (long long)ny0 * gz);
+      a = make_float4(x[idx], x[N + idx], x[2 * N + idx], x[3 * N + idx]);
+      b = make_float4(float(v[idx]), float(v[N + idx]), float(v[2 * N + idx]), float(v[3 * N + idx]));
+    }
+    xs[j] = a;
+    vs[j] = b;
+  }
+  for (int i = threadIdx.x; i < T * T * T; i += NT) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  constexpr int NEL = E * E * E;
+  for (int base = 0; base < NEL; base += NT) {
+    const int e = base + threadIdx.x;
+    const int lx = e % E - 1, ly = (e / E) % E - 1, lz = e / (E * E) - 1;
+    const bool valid = e < NEL && ox + lx >= 0 && ox + lx < g.ne[0] && oy + ly >= 0 &&
+                       oy + ly < g.ne[1] && oz + lz >= 0 && oz + lz < g.ne[2];
+    float out[4][8];
+    if (valid) {
+      const int c0 = (lx + 1) + NN * ((ly + 1) + NN * (lz + 1));
+      float xe[4][8], ve[4][8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int c = c0 + (a & 1) + NN * ((a >> 1) & 1) + NN * NN * ((a >> 2) & 1);
+        const float4 xa = xs[c], va = vs[c];
+        xe[0][a] = xa.x; xe[1][a] = xa.y; xe[2][a] = xa.z; xe[3][a] = xa.w;
+        ve[0][a] = va.x; ve[1][a] = va.y; ve[2][a] = va.z; ve[3][a] = va.w;
+      }
+      p2::elem_hessvec(xe, ve, m, out);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int nx = lx + (a & 1), ny = ly + ((a >> 1) & 1), nz = lz + ((a >> 2) & 1);
+      if (valid && nx >= 0 && nx < T && ny >= 0 && ny < T && nz >= 0 && nz < T) {
+        const int li = nx + T * (ny + T * nz);
+        float4 t = acc[li];
+        t.x += out[0][a];
+        t.y += out[1][a];
+        t.z += out[2][a];
+        t.w += out[3][a];
+        acc[li] = t;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < T * T * T; i += NT) {
+    const int nx = i % T, ny = (i / T) % T, nz = i / (T * T);
+    const int gx = ox + nx, gy = oy + ny, gz = oz + nz;
+    if (gx < nx0 && gy < ny0 && gz < nz0) {
+      const long long idx = gx + (long long)nx0 * (gy + (long long)ny0 * gz);
+      const float4 t = acc[i];
+      y[idx] = TV(t.x);
+      y[N + idx] = TV(t.y);
+      y[2 * N + idx] = TV(t.z);
+      y[3 * N + idx] = TV(t.w);
+    }
+  }
+}
+
 template <int D>
 static dim3 scatter_grid(const Geom& g) {
   return dim3((g.n[0] + Tile<D>::X - 1) / Tile<D>::X, (g.n[1] + Tile<D>::Y - 1) / Tile<D>::Y,
@@ -342,10 +423,19 @@ cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, vo
               : launch_scatter<2, double, double, OP_GRAD>(g, m, x, nullptr, y, nullptr, st);
 }
 
+template <class TV>
+static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const float* x,
+                                     const TV* v, TV* y, const int* skip, cudaStream_t st) {
+  k_hess_tile3<TV><<<scatter_grid<3>(g), 256, 0, st>>>(g, cast_mat<float>(m), x, v, y, skip);
+  return cudaGetLastError();
+}
+
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
                          void* y, int prec, cudaStream_t st, const int* skip) {
   if (g.dim == 3)
-    return prec ? launch_scatter<3, float, float, OP_HESS>(g, m, x, v, y, skip, st)
+    return prec ? launch_hess_tile3<float>(g, m, static_cast<const float*>(x),
+                                           static_cast<const float*>(v), static_cast<float*>(y),
+                                           skip, st)
                 : launch_scatter<3, double, double, OP_HESS>(g, m, x, v, y, skip, st);
   return prec ? launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st)
               : launch_scatter<2, double, double, OP_HESS>(g, m, x, v, y, skip, st);
@@ -656,7 +746,7 @@ cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, in
 
 cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float* x32,
                                const double* v, double* y, cudaStream_t st, const int* skip) {
-  if (g.dim == 3) return launch_scatter<3, float, double, OP_HESS>(g, m, x32, v, y, skip, st);
+  if (g.dim == 3) return launch_hess_tile3<double>(g, m, x32, v, y, skip, st);
   return launch_scatter<2, float, double, OP_HESS>(g, m, x32, v, y, skip, st);
 }
 
