@@ -82,8 +82,12 @@ typedef struct {
   double rtol;           /* stop when ||x - P(x - grad f)|| <= rtol * start  */
   double atol;           /* ... or <= atol                                   */
   int coarse_model;      /* PF_GALERKIN or PF_FIRST_ORDER                    */
-  int precision;         /* PF_FP64, or PF_FP32 = mixed: FP32 hessvec and CG,
-                            FP64 energy, gradient, rho, radius, norms        */
+  int precision;         /* PF_FP64, or PF_FP32 = mixed: on every level but
+                            the coarsest an FP32 Hessian and FP32 subproblem,
+                            FP32 gradient steps after accepted steps and FP32
+                            higher-order terms of rho's energy difference;
+                            FP64 stopping-test gradients, energy, first-order
+                            term of rho, radius, norms and coarsest level   */
   int precondition;      /* 1: Jacobi (Hessian-diagonal) preconditioned CG (1) */
   double level_rtol;     /* a non-finest level stops its TR steps once its
                             projected gradient fell by this factor (1e-3;
@@ -112,7 +116,10 @@ typedef struct {
   int cycles;            /* V-cycles taken                                   */
   int converged;         /* 1 if the stopping test passed                    */
   double energy;         /* E(x) at return (FP64)                            */
-  double pg0, pg;        /* projected-gradient norm at start / at return     */
+  double pg0, pg;        /* projected-gradient norm at start / at return;
+                            pg0 of an extrapolated mixed-precision start uses
+                            the FP32 gradient step from x_{t-1} (its error is
+                            relative to the change of the gradient)         */
   long long hessvecs;    /* Hessian-vector products on any level             */
   long long cg;          /* CG iterations                                    */
   long long tr_its;      /* TR iterations on all levels                      */

@@ -194,19 +194,40 @@ __global__ void __launch_bounds__(256) k_cg_update4(long long n4, const float* _
   if (c->done) return;
   const float al = float(c->alpha);
   float rr = 0.f, lv = 0.f, rz = 0.f;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4;
-       j += (long long)gridDim.x * blockDim.x) {
-    const float4 a4 = ld4(ga, j);
-    if (!any_free(a4)) continue;
-    const float4 b4 = ld4(gb, j), q4 = ld4(q, j), p4 = ld4(p, j);
-    float4 w4 = ld4(w, j), r4 = ld4(r, j);
-    const float4 m4 = pc ? ld4(mi, j) : make_float4(1.f, 1.f, 1.f, 1.f);
-    cg_update_lane(al, a4.x, b4.x, q4.x, p4.x, w4.x, r4.x, m4.x, rr, lv, rz);
-    cg_update_lane(al, a4.y, b4.y, q4.y, p4.y, w4.y, r4.y, m4.y, rr, lv, rz);
-    cg_update_lane(al, a4.z, b4.z, q4.z, p4.z, w4.z, r4.z, m4.z, rr, lv, rz);
-    cg_update_lane(al, a4.w, b4.w, q4.w, p4.w, w4.w, r4.w, m4.w, rr, lv, rz);
-    st4(w, j, w4);
-    st4(r, j, r4);
+  // two groups per iteration, every load of both issued before any store
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; j0 < n4; j0 += 2 * stride) {
+    const long long j1 = j0 + stride;
+    const bool h1 = j1 < n4;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), one4 = make_float4(1.f, 1.f, 1.f, 1.f);
+    const float4 a0 = ld4(ga, j0), a1 = h1 ? ld4(ga, j1) : z4;
+    const bool f0 = any_free(a0), f1 = any_free(a1);
+    float4 b[2] = {z4, z4}, qq[2] = {z4, z4}, pp[2] = {z4, z4}, ww[2] = {z4, z4}, rv[2] = {z4, z4};
+    float4 mm[2] = {one4, one4};
+    if (f0) {
+      b[0] = ld4(gb, j0); qq[0] = ld4(q, j0); pp[0] = ld4(p, j0); ww[0] = ld4(w, j0); rv[0] = ld4(r, j0);
+      if (pc) mm[0] = ld4(mi, j0);
+    }
+    if (f1) {
+      b[1] = ld4(gb, j1); qq[1] = ld4(q, j1); pp[1] = ld4(p, j1); ww[1] = ld4(w, j1); rv[1] = ld4(r, j1);
+      if (pc) mm[1] = ld4(mi, j1);
+    }
+    const float4 aa[2] = {a0, a1};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      cg_update_lane(al, aa[k].x, b[k].x, qq[k].x, pp[k].x, ww[k].x, rv[k].x, mm[k].x, rr, lv, rz);
+      cg_update_lane(al, aa[k].y, b[k].y, qq[k].y, pp[k].y, ww[k].y, rv[k].y, mm[k].y, rr, lv, rz);
+      cg_update_lane(al, aa[k].z, b[k].z, qq[k].z, pp[k].z, ww[k].z, rv[k].z, mm[k].z, rr, lv, rz);
+      cg_update_lane(al, aa[k].w, b[k].w, qq[k].w, pp[k].w, ww[k].w, rv[k].w, mm[k].w, rr, lv, rz);
+    }
+    if (f0) {
+      st4(w, j0, ww[0]);
+      st4(r, j0, rv[0]);
+    }
+    if (f1) {
+      st4(w, j1, ww[1]);
+      st4(r, j1, rv[1]);
+    }
   }
   double acc[3] = {double(rr), double(lv), double(rz)};
   auto fin = [c](double(&a)[3]) {
@@ -236,12 +257,16 @@ __global__ void __launch_bounds__(256) k_cg_dot4(long long n4, const float* __re
                                                  double* partials, unsigned* counter) {
   if (c->done) return;
   float pq = 0.f;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4;
-       j += (long long)gridDim.x * blockDim.x) {
-    const float4 p4 = ld4(p, j);
-    if (p4.x == 0.f && p4.y == 0.f && p4.z == 0.f && p4.w == 0.f) continue;
-    const float4 q4 = ld4(q, j);
-    pq += p4.x * q4.x + p4.y * q4.y + p4.z * q4.z + p4.w * q4.w;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; j0 < n4; j0 += 2 * stride) {
+    const long long j1 = j0 + stride;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 p0 = ld4(p, j0), p1 = j1 < n4 ? ld4(p, j1) : z4;
+    const bool n0 = p0.x != 0.f || p0.y != 0.f || p0.z != 0.f || p0.w != 0.f;
+    const bool n1 = p1.x != 0.f || p1.y != 0.f || p1.z != 0.f || p1.w != 0.f;
+    const float4 q0 = n0 ? ld4(q, j0) : z4, q1 = n1 ? ld4(q, j1) : z4;
+    pq += p0.x * q0.x + p0.y * q0.y + p0.z * q0.z + p0.w * q0.w;
+    pq += p1.x * q1.x + p1.y * q1.y + p1.z * q1.z + p1.w * q1.w;
   }
   double acc[1] = {double(pq)};
   auto fin = [c](double(&a)[1]) {
@@ -264,13 +289,29 @@ __global__ void __launch_bounds__(256) k_cg_dir4(long long n4, const float* __re
                                                  float* __restrict__ p, const CgCtrl* c) {
   if (c->done) return;
   const float be = float(c->beta);
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4;
-       j += (long long)gridDim.x * blockDim.x) {
-    if (!any_free(ld4(ga, j))) continue;
-    const float4 r4 = ld4(r, j), p4 = ld4(p, j);
-    const float4 m4 = pc ? ld4(mi, j) : make_float4(1.f, 1.f, 1.f, 1.f);
-    st4(p, j, make_float4(m4.x * r4.x + be * p4.x, m4.y * r4.y + be * p4.y,
-                          m4.z * r4.z + be * p4.z, m4.w * r4.w + be * p4.w));
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; j0 < n4; j0 += 2 * stride) {
+    const long long j1 = j0 + stride;
+    const bool h1 = j1 < n4;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f), one4 = make_float4(1.f, 1.f, 1.f, 1.f);
+    const bool f0 = any_free(ld4(ga, j0)), f1 = h1 && any_free(ld4(ga, j1));
+    float4 rv[2] = {z4, z4}, pp[2] = {z4, z4}, mm[2] = {one4, one4};
+    if (f0) {
+      rv[0] = ld4(r, j0); pp[0] = ld4(p, j0);
+      if (pc) mm[0] = ld4(mi, j0);
+    }
+    if (f1) {
+      rv[1] = ld4(r, j1); pp[1] = ld4(p, j1);
+      if (pc) mm[1] = ld4(mi, j1);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float4 m4 = mm[k], r4 = rv[k], p4 = pp[k];
+      pp[k] = make_float4(m4.x * r4.x + be * p4.x, m4.y * r4.y + be * p4.y,
+                          m4.z * r4.z + be * p4.z, m4.w * r4.w + be * p4.w);
+    }
+    if (f0) st4(p, j0, pp[0]);
+    if (f1) st4(p, j1, pp[1]);
   }
 }
 
@@ -1042,11 +1083,15 @@ struct Solver {
     const long long N = g.N;
     const int dim = H->dim;
     double pg_ref = P.pg_ref;
+    bool g_at_t3 = false;  // B.g holds the FP64 gradient at B.t3 = the plain start
     const double p_before = P.p_prev > 0.0 ? P.p_prev : H->p_last;
     if (P.start == PF_START_EXTRAPOLATE && p_before > 0.0 && H->p != p_before) {
       // the displacement is nearly linear in p: start from u p / p_last, c
       // unchanged, and stop at the accuracy of the plain start
-      if (!(pg_ref > 0.0)) pg_ref = pg_at(x_user);
+      if (!(pg_ref > 0.0)) {
+        pg_ref = pg_at(x_user);  // B.g = grad f(x_{t-1}), B.t3 = x_{t-1}
+        g_at_t3 = true;
+      }
       const double r = H->p / p_before;
       double* xu = x_user;
       map((long long)dim * N, [=] __device__(long long i) { xu[i] *= r; });
@@ -1077,7 +1122,23 @@ struct Solver {
         x[i] = fmin(fmax(x[i], l), u);
       });
     }
-    const double pg0 = pg_norm(B.x);
+    double pg0;
+    if (g_at_t3 && step_update(L - 1)) {
+      // the gradient at the extrapolated start by an FP32 gradient step from
+      // the FP64 one at x_{t-1} (only u moved); the stopping tests of the
+      // cycles evaluate the FP64 gradient again
+      const double* x0 = B.t3;
+      const double* x = B.x;
+      double* sv = B.s;
+      map(B.n, [=] __device__(long long i) { sv[i] = x[i] - x0[i]; });
+      ck(elem_gradient_step(H->geo[L - 1], H->mat[L - 1], B.x, B.s, B.g, st), "gradient_step");
+      S.launches += 1;
+      S.fe_gradient += 1.0;
+      gstate[L - 1] = G_AT_X;
+      pg0 = pg_norm_level(L - 1);
+    } else {
+      pg0 = pg_norm(B.x);
+    }
     if (!std::isfinite(pg0)) {
       copy(x_user, B.x, B.n);
       ck(cudaStreamSynchronize(st), "sync");
