@@ -218,11 +218,14 @@ def kernels_only(pf, B, H, x, W):
     pf.hessvec_lagged(H, level, v, out)
     pf.hessvec(H, level, x32, v32, o32)
     pf.gradient(H, level, x, out)
+    pf.gradient_df(H, level, x, out)
     torch.cuda.synchronize()
     res = {}
     for name, fn in (("hessvec_fp64", lambda: pf.hessvec_lagged(H, level, v, out)),
                      ("hessvec_fp32", lambda: pf.hessvec(H, level, x32, v32, o32)),
                      ("gradient_fp64", lambda: pf.gradient(H, level, x, out)),
+                     ("gradient_df", lambda: pf.gradient_df(H, level, x, out)),
+                     ("energy_df", lambda: pf.energy_df(H, level, x)),
                      ("energy_diff_fp64", lambda: pf.energy_diff(H, level, x, v)),
                      ("energy_fp64", lambda: pf.energy(H, level, x))):
         a = torch.cuda.Event(enable_timing=True)

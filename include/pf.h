@@ -86,8 +86,9 @@ typedef struct {
                             the coarsest an FP32 Hessian and FP32 subproblem,
                             FP32 gradient steps after accepted steps and FP32
                             higher-order terms of rho's energy difference;
-                            FP64 stopping-test gradients, energy, first-order
-                            term of rho, radius, norms and coarsest level   */
+                            double-float (pf_gradient_df) stopping-test
+                            gradients and energy; FP64 first-order term of
+                            rho, radius, norms and coarsest-level Hessian  */
   int precondition;      /* 1: Jacobi (Hessian-diagonal) preconditioned CG (1) */
   double level_rtol;     /* a non-finest level stops its TR steps once its
                             projected gradient fell by this factor (1e-3;
@@ -115,7 +116,7 @@ typedef struct {
 typedef struct {
   int cycles;            /* V-cycles taken                                   */
   int converged;         /* 1 if the stopping test passed                    */
-  double energy;         /* E(x) at return (FP64)                            */
+  double energy;         /* E(x) at return (FP64; double-float in mixed mode) */
   double pg0, pg;        /* projected-gradient norm at start / at return;
                             pg0 of an extrapolated mixed-precision start uses
                             the FP32 gradient step from x_{t-1} (its error is
@@ -192,6 +193,18 @@ pf_status pf_energy_diff_mixed(pf_hierarchy* h, int level, const double* x_dev,
 /* Gradient of the energy at x_dev written to g_dev (same precision, same
  * layout), all dofs, no boundary masking. */
 pf_status pf_gradient(pf_hierarchy* h, int level, const void* x_dev, void* g_dev, int prec);
+
+/* Gradient (to g_dev) and energy (to *E_host, stream synchronised) of the
+ * FP64 state x_dev in double-float arithmetic: every value an unevaluated
+ * sum of two FP32 numbers (about 48 significant bits, FP32's exponent
+ * range), run on the FP32 pipes, which GB300 issues at 64x its FP64 rate.
+ * The mixed-precision solver takes its stopping-test gradients and the
+ * returned energy this way (Sec. 2 energy and its gradient).  FP64 device
+ * vectors of (dim+1)*N values.  PF_EINVAL on grids whose coefficient
+ * buffer cannot hold the double-float scratch (only grids with very few
+ * elements per axis). */
+pf_status pf_gradient_df(pf_hierarchy* h, int level, const double* x_dev, double* g_dev);
+pf_status pf_energy_df(pf_hierarchy* h, int level, const double* x_dev, double* E_host);
 
 /* Gradient step: g_dev += grad E(x_dev) - grad E(x_dev - s_dev), so that
  * g_dev = grad E(x - s) on entry leaves grad E(x).  FP64 vectors; the

@@ -33,7 +33,7 @@ EXPORTS = [
     "pf_unet_set_params", "pf_unet_get_params", "pf_unet_get_grads", "pf_unet_forward",
     "pf_unet_backward", "pf_unet_mse", "pf_unet_adam", "pf_learned_features", "pf_learned_target",
     "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient", "pf_rmtr_load_step_batch",
-    "pf_energy_diff_mixed", "pf_gradient_step",
+    "pf_energy_diff_mixed", "pf_gradient_step", "pf_gradient_df", "pf_energy_df",
 ]
 
 
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_gradient": (i, [vp, i, vp, vp, i]),
         "pf_energy_diff_mixed": (i, [vp, i, vp, vp, vp, vp]),
         "pf_gradient_step": (i, [vp, i, vp, vp, vp]),
+        "pf_gradient_df": (i, [vp, i, vp, vp]),
+        "pf_energy_df": (i, [vp, i, vp, C.POINTER(d)]),
         "pf_hessvec": (i, [vp, i, vp, vp, vp, i]),
         "pf_prolong": (i, [vp, i, vp, vp, i]),
         "pf_restrict": (i, [vp, i, vp, vp, i]),
@@ -277,6 +279,25 @@ def energy_diff_mixed(H: Hierarchy, level: int, x, s, g) -> np.ndarray:
                                       _dev(s, n, torch.float64), _dev(g, n, torch.float64),
                                       out.ctypes.data_as(C.c_void_p)))
     return out
+
+
+def gradient_df(H: Hierarchy, level: int, x, out=None):
+    """Gradient of FP64 x in double-float arithmetic (FP64 result)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(x)
+    n = H.ndof(level)
+    _check(lib().pf_gradient_df(H.handle, level, _dev(x, n, torch.float64),
+                                _dev(out, n, torch.float64)))
+    return out
+
+
+def energy_df(H: Hierarchy, level: int, x) -> float:
+    """Energy of FP64 x in double-float arithmetic."""
+    import torch
+    out = C.c_double()
+    _check(lib().pf_energy_df(H.handle, level, _dev(x, H.ndof(level), torch.float64), C.byref(out)))
+    return out.value
 
 
 def gradient_step(H: Hierarchy, level: int, x, s, g):

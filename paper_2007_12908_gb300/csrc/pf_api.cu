@@ -320,6 +320,27 @@ pf_status pf_gradient(pf_hierarchy* h, int level, const void* x, void* g, int pr
   return PF_OK;
 }
 
+pf_status pf_gradient_df(pf_hierarchy* h, int level, const double* x, double* g) {
+  if (!valid_level(h, level) || !x || !g) return bad("gradient_df: bad argument");
+  if (!df_scratch_fits(h->geo[level])) return bad("gradient_df: grid too small for the scratch");
+  PF_TRY_CUDA(elem_gradient_df(h->geo[level], h->mat[level], x, g, h->lv[level].coef, h->st),
+              "gradient_df");
+  return PF_OK;
+}
+
+pf_status pf_energy_df(pf_hierarchy* h, int level, const double* x, double* E_host) {
+  if (!valid_level(h, level) || !x || !E_host) return bad("energy_df: bad argument");
+  if (!df_scratch_fits(h->geo[level])) return bad("energy_df: grid too small for the scratch");
+  PF_TRY_CUDA(elem_energy_df(h->geo[level], h->mat[level], x, h->lv[level].coef, h->scratch,
+                             h->d_res, h->st),
+              "energy_df");
+  PF_TRY_CUDA(cudaMemcpyAsync(h->h_res, h->d_res, sizeof(double), cudaMemcpyDeviceToHost, h->st),
+              "energy_df");
+  PF_TRY_CUDA(cudaStreamSynchronize(h->st), "energy_df");
+  *E_host = h->h_res[0];
+  return PF_OK;
+}
+
 pf_status pf_gradient_step(pf_hierarchy* h, int level, const double* x, const double* s,
                            double* g) {
   if (!valid_level(h, level) || !x || !s || !g) return bad("gradient_step: bad argument");

@@ -76,6 +76,17 @@ cudaError_t elem_gradient_fp64(const Geom& g, const Mat<double>& m, const double
 // from the one at x - s.
 cudaError_t elem_gradient_step(const Geom& g, const Mat<double>& m, const double* x,
                                const double* s, double* y, cudaStream_t st);
+// The gradient (to y, FP64) and the energy (to out_dev[0]) of FP64 x in
+// double-float arithmetic on the FP32 pipes (about 48 significant bits).
+// scratch: a level's coefficient buffer (coef_count(g) doubles), which
+// holds x in double-float and the gradient's corner contributions;
+// cudaErrorInvalidValue where it is too small (df_scratch_fits false: only
+// grids with very few elements per axis).
+bool df_scratch_fits(const Geom& g);
+cudaError_t elem_gradient_df(const Geom& g, const Mat<double>& m, const double* x, double* y,
+                             double* scratch, cudaStream_t st);
+cudaError_t elem_energy_df(const Geom& g, const Mat<double>& m, const double* x, double* scratch,
+                           const Scratch& s, double* out_dev, cudaStream_t st);
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
                          void* y, int prec, cudaStream_t st, const int* skip = nullptr);
 // FP64 lagged Hessian: Gauss-point coefficients of x (coef holds

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "pf_df.cuh"
 #include "pf_element_f2.cuh"
 #include "pf_internal.h"
 #include "pf_reduce.cuh"
@@ -518,6 +519,156 @@ cudaError_t elem_gradient_fp64(const Geom& g, const Mat<double>& m, const double
     k_grad_elem<2><<<nb, 128, 0, st>>>(g, m, x, scratch);
     k_grad_gather<2><<<nn, 256, 0, st>>>(g, scratch, y);
   }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ double-float passes
+// The gradient and the energy in double-float arithmetic (pf_df.cuh) on the
+// FP32 pipes: x is split once per call into (hi, lo) planes, the element
+// algebra is the FP64 code instantiated with df, and nodal sums and totals
+// are formed in df (gradient) or FP64 (energy totals across threads).
+__global__ void k_to_df(long long n, const double* __restrict__ x, float2* __restrict__ xd) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const df v = df_from(x[i]);
+    xd[i] = make_float2(v.hi, v.lo);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void gather_df(const Geom& g, const float2* __restrict__ xd, int ex,
+                                          int ey, int ez, df (*xe)[1 << D]) {
+#pragma unroll
+  for (int a = 0; a < (1 << D); ++a) {
+    const long long idx = corner_node<D>(g, ex, ey, ez, a);
+#pragma unroll
+    for (int f = 0; f <= D; ++f) {
+      const float2 v = xd[f * g.N + idx];
+      xe[f][a] = df(v.x, v.y);
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_grad_elem_df(Geom g, Mat<df> m,
+                                                      const float2* __restrict__ xd,
+                                                      float2* __restrict__ scratch) {
+  constexpr int F = D + 1, NC = 1 << D;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.NE;
+       e += (long long)gridDim.x * blockDim.x) {
+    int ex, ey, ez;
+    elem_coords<D>(g, e, ex, ey, ez);
+    df xe[F][NC], out[F][NC];
+    gather_df<D>(g, xd, ex, ey, ez, xe);
+    elem_gradient<D, df>(xe, m, out);
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+        scratch[(f * NC + a) * g.NE + e] = make_float2(out[f][a].hi, out[f][a].lo);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_grad_gather_df(Geom g, const float2* __restrict__ scratch,
+                                                        double* __restrict__ y) {
+  constexpr int F = D + 1, NC = 1 << D;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = int(i % g.n[0]);
+    const long long r = i / g.n[0];
+    const int iy = int(r % g.n[1]);
+    const int iz = int(r / g.n[1]);
+    const int ic[3] = {ix, iy, iz};
+    df acc[F];
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+      int ec[3] = {0, 0, 0};
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        ec[k] = ic[k] - ((a >> k) & 1);
+        ok = ok && ec[k] >= 0 && ec[k] < g.ne[k];
+      }
+      if (!ok) continue;
+      const long long e = ec[0] + (long long)g.ne[0] * (ec[1] + (long long)g.ne[1] * ec[2]);
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        const float2 v = scratch[(f * NC + a) * g.NE + e];
+        acc[f] += df(v.x, v.y);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) y[f * g.N + i] = df_to_double(acc[f]);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_energy_df(Geom g, Mat<df> m, const float2* __restrict__ xd,
+                                                   double* partials, unsigned* counter,
+                                                   double* out) {
+  df part;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.NE;
+       e += (long long)gridDim.x * blockDim.x) {
+    int ex, ey, ez;
+    elem_coords<D>(g, e, ex, ey, ez);
+    df xe[D + 1][1 << D];
+    gather_df<D>(g, xd, ex, ey, ez, xe);
+    part += elem_energy<D, df>(xe, m);
+  }
+  double acc[1] = {df_to_double(part)};
+  grid_finish<1, OpSum>(acc, partials, counter, out);
+}
+
+// Scratch of the double-float passes inside a buffer of `cap` doubles
+// (a level's coefficient buffer): x in df, then the gradient's corner
+// contributions.  False when the buffer is too small.
+static bool df_layout(const Geom& g, long long cap, long long& off_contrib) {
+  const long long n = (long long)(g.dim + 1) * g.N;
+  const long long contrib = (long long)(g.dim + 1) * (1LL << g.dim) * g.NE;
+  off_contrib = n;
+  return n + contrib <= cap;
+}
+
+bool df_scratch_fits(const Geom& g) {
+  long long off;
+  return df_layout(g, coef_count(g), off);
+}
+
+cudaError_t elem_gradient_df(const Geom& g, const Mat<double>& m, const double* x, double* y,
+                             double* scratch, cudaStream_t st) {
+  long long off;
+  if (!df_layout(g, coef_count(g), off)) return cudaErrorInvalidValue;
+  float2* xd = reinterpret_cast<float2*>(scratch);
+  float2* contrib = reinterpret_cast<float2*>(scratch) + off;
+  const long long n = (long long)(g.dim + 1) * g.N;
+  const int nv = int(std::min<long long>((n + 255) / 256, 16LL * 1216));
+  const int nb = int(std::min<long long>((g.NE + 127) / 128, 32LL * 1216));
+  const int nn = int(std::min<long long>((g.N + 255) / 256, 16LL * 1216));
+  k_to_df<<<nv, 256, 0, st>>>(n, x, xd);
+  if (g.dim == 3) {
+    k_grad_elem_df<3><<<nb, 128, 0, st>>>(g, cast_mat<df>(m), xd, contrib);
+    k_grad_gather_df<3><<<nn, 256, 0, st>>>(g, contrib, y);
+  } else {
+    k_grad_elem_df<2><<<nb, 128, 0, st>>>(g, cast_mat<df>(m), xd, contrib);
+    k_grad_gather_df<2><<<nn, 256, 0, st>>>(g, contrib, y);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t elem_energy_df(const Geom& g, const Mat<double>& m, const double* x, double* scratch,
+                           const Scratch& s, double* out, cudaStream_t st) {
+  long long off;
+  if (!df_layout(g, coef_count(g), off)) return cudaErrorInvalidValue;
+  float2* xd = reinterpret_cast<float2*>(scratch);
+  const long long n = (long long)(g.dim + 1) * g.N;
+  const int nv = int(std::min<long long>((n + 255) / 256, 16LL * 1216));
+  const int nb = reduce_grid(g.NE, 256);
+  k_to_df<<<nv, 256, 0, st>>>(n, x, xd);
+  if (g.dim == 3)
+    k_energy_df<3><<<nb, 256, 0, st>>>(g, cast_mat<df>(m), xd, s.partials, s.counter, out);
+  else
+    k_energy_df<2><<<nb, 256, 0, st>>>(g, cast_mat<df>(m), xd, s.partials, s.counter, out);
   return cudaGetLastError();
 }
 

@@ -409,12 +409,19 @@ struct Solver {
   }
 
   // ---------------------------------------------------------------- element ops
+  // Gradient and energy of f~ on level l: FP64, or double-float on the FP32
+  // pipes in the mixed mode; elements evaluated once; the level's
+  // coefficient buffer is free scratch outside the assembly in set_lag.
+  bool use_df(int l) const { return mixed && df_scratch_fits(H->geo[l]); }
   void gradient(int l, const double* x, double* out) {
-    // FP64, elements evaluated once; the level's coefficient buffer is free
-    // scratch outside the assembly in set_lag
-    ck(elem_gradient_fp64(H->geo[l], H->mat[l], x, out, H->lv[l].coef, st), "gradient");
+    if (use_df(l)) {
+      ck(elem_gradient_df(H->geo[l], H->mat[l], x, out, H->lv[l].coef, st), "gradient_df");
+      S.launches += 3;
+    } else {
+      ck(elem_gradient_fp64(H->geo[l], H->mat[l], x, out, H->lv[l].coef, st), "gradient");
+      S.launches += 2;
+    }
     S.fe_gradient += frac(l);
-    S.launches += 2;
   }
   double ediff(int l, const double* x, const double* s) {
     ck(elem_energy_diff(H->geo[l], H->mat[l], x, s, 0, H->scratch, H->d_res, st), "ediff");
@@ -425,9 +432,15 @@ struct Solver {
     return a[0] + a[1] + a[2] + a[3];
   }
   double energy(int l, const double* x) {
-    ck(elem_energy(H->geo[l], H->mat[l], x, 0, H->scratch, H->d_res, st), "energy");
+    if (use_df(l)) {
+      ck(elem_energy_df(H->geo[l], H->mat[l], x, H->lv[l].coef, H->scratch, H->d_res, st),
+         "energy_df");
+      S.launches += 2;
+    } else {
+      ck(elem_energy(H->geo[l], H->mat[l], x, 0, H->scratch, H->d_res, st), "energy");
+      S.launches += 1;
+    }
     S.fe_energy += frac(l);
-    S.launches += 1;
     double e;
     fetch(1, &e);
     return e;

@@ -96,6 +96,25 @@ def test_mixed_difference_kernels(pf, dim, nc, L, hc, k_res, scale):
     assert np.max(np.abs(host(y) - go)) <= TOL32 * np.max(np.abs(change))
 
 
+@pytest.mark.parametrize("dim,nc,L,hc", SMALL)
+@pytest.mark.parametrize("k_res", [0.0, 0.01])
+def test_double_float_gradient_energy(pf, dim, nc, L, hc, k_res):
+    """Gradient and energy in double-float arithmetic (two FP32 words,
+    about 48 significant bits) against the FP64 oracle."""
+    H, Ho = pair(dim, nc, L, hc, E=1.3, nu=0.27, Gc=0.9, k_res=k_res, p=0.05)
+    for level in range(L):
+        g = Ho.grids[level]
+        x = PI.random_state(400 + level, dim, g.N, u_scale=0.05)
+        xd = dev(x)
+        if g.NE == 1 and dim == 2:  # too few elements for the scratch layout
+            with pytest.raises(pf.PfError):
+                pf.gradient_df(H, level, xd)
+            continue
+        assert relinf(host(pf.gradient_df(H, level, xd)), O.gradient(g, Ho.prm, x)) <= 1e-11
+        eo = O.energy(g, Ho.prm, x)
+        assert abs(pf.energy_df(H, level, xd) - eo) <= 1e-12 * abs(eo)
+
+
 def test_deterministic(pf):
     H, Ho = pair(3, (10, 7, 6), 2, 1 / 9, p=1e-3)
     g = Ho.grids[-1]
