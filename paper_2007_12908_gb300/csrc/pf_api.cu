@@ -98,6 +98,10 @@ pf_status pf_mesh_hierarchy_destroy(pf_hierarchy* h) {
   if (!h) return PF_OK;
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
+  for (auto& G : h->cg_graphs) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+  }
   for (void* p : h->allocations) cudaFree(p);
   if (h->h_res) cudaFreeHost(h->h_res);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);

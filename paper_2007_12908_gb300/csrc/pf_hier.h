@@ -44,6 +44,21 @@ struct pf_hierarchy {
   double* c_prev = nullptr; // finest N values
   pf::CgCtrl* ctrl = nullptr;    // device CG control block
   pf::CgCtrl* h_ctrl = nullptr;  // pinned host mirror
+  // executable graphs of the FP32 CG loop per level (built by the solver)
+  struct CgGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // what the captured launches depend on besides the level's fixed buffers
+    double p = 0.0;               // pressure (argument of the FP32 Hessian)
+    int pc = -1;                  // preconditioning flag
+    int vsize = 0;                // 4: FP32 vectors, 8: FP64 vectors
+    int precision = -1;           // PF_FP64 / PF_FP32 (selects the Hessian kernel)
+    int coarse_model = -1;        // selects the level's model Hessian
+    const void* vp = nullptr;     // direction vector
+    int nodes = 0;                // kernel launches per iteration of the body
+  };
+  std::vector<CgGraph> cg_graphs;
+  bool cg_graph_ok = true;  // false once the driver refused to build one
   bool have_fractures = false;
   std::vector<pf::LevelBuf> lv;
   std::vector<void*> allocations;

@@ -315,6 +315,17 @@ __global__ void __launch_bounds__(256) k_cg_dir4(long long n4, const float* __re
   }
 }
 
+// Condition of the CG loop's while node: repeat while the run is not done.
+// The update pass stops the run at the budget; the cap here only guards
+// against a control block that stopped counting.
+__global__ void k_cg_cond(CgCtrl* c, cudaGraphConditionalHandle h) {
+  if (!c->done && c->used > c->cg_max) {
+    c->done = 1;
+    c->state = CG_BUDGET;
+  }
+  cudaGraphSetConditional(h, c->done ? 0u : 1u);
+}
+
 static int map_grid(long long n) {
   long long b = (n + 255) / 256;
   return int(std::max(1LL, std::min(b, 4LL * 1216)));
@@ -640,6 +651,160 @@ struct Solver {
     V *s, *Hs, *r, *p, *q, *w, *a, *b, *t1, *t2;
   };
 
+  // One projected-CG iteration on FP32 vectors with float4 passes (n a
+  // multiple of 4) on stream s: q = H p, p.q and alpha, the update with its
+  // tests and beta, the direction.  No-ops once the control block is done.
+  void cg_iter4(int l, const float* p, float* q, const float* ga, const float* gb,
+                const float* mi, float* w, float* r, bool pc, cudaStream_t s) {
+    LevelBuf& B = H->lv[l];
+    CgCtrl* c = H->ctrl;
+    const long long n4 = B.n / 4;
+    ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done), "hessvec32");
+    k_cg_dot4<<<reduce_grid(n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials, H->scratch.counter);
+    ck(cudaGetLastError(), "cg_dot");
+    k_cg_update4<<<reduce_grid(n4), 256, 0, s>>>(n4, ga, gb, q, p, mi, pc, w, r, c,
+                                                 H->scratch.partials, H->scratch.counter);
+    ck(cudaGetLastError(), "cg_update");
+    k_cg_dir4<<<reduce_grid(n4), 256, 0, s>>>(n4, ga, r, mi, pc, const_cast<float*>(p), c);
+    ck(cudaGetLastError(), "cg_dir");
+  }
+
+  // One projected-CG iteration on level l on the solver's stream: q = H p,
+  // p.q and alpha, the update with its tests and beta, the direction.
+  // Launches after the control block is done are no-ops.
+  template <class V>
+  void cg_iter(int l, V* p, V* q, const V* ga, const V* gb, const V* mi, V* w, V* r, bool pc) {
+    const long long n = H->lv[l].n;
+    CgCtrl* c = H->ctrl;
+    const int* skip = &H->ctrl->done;
+    const V Z = V(0);
+    if constexpr (std::is_same<V, float>::value) {
+      if (n % 4 == 0) {
+        cg_iter4(l, p, q, ga, gb, mi, w, r, pc, st);
+        S.launches += 4;
+        return;
+      }
+    }
+    hv<V>(l, p, q, skip, false);
+    red_fin<1, OpSum, V>(n, [=] __device__(long long i, V(&o)[1]) { o[0] = p[i] * q[i]; },
+                         [=] __device__(double(&a)[1]) {
+      c->kappa = a[0];
+      c->used += 1;
+      if (a[0] <= 0.0) {
+        c->done = 1;
+        c->state = CG_NEGCURV;
+      } else {
+        c->alpha = c->rz / a[0];
+      }
+    }, skip);
+    red_fin<3, OpSum, V>(n, [=] __device__(long long i, V(&o)[3]) {
+      const V al = V(c->alpha);
+      const V a = ga[i];
+      const V qi = a < Z ? q[i] : Z;
+      const V wi = w[i] + al * p[i];
+      w[i] = wi;
+      const V ri = r[i] - al * qi;
+      r[i] = ri;
+      o[0] = ri * ri;
+      o[1] = (wi < a || wi > gb[i]) ? V(1) : Z;
+      o[2] = ri * (pc ? mi[i] * ri : ri);
+    }, [=] __device__(double(&a)[3]) {
+      if (a[1] > 0.0) {
+        c->done = 1;
+        c->state = CG_LEAVE;
+      } else if (sqrt(a[0]) <= c->tol) {
+        c->done = 1;
+        c->state = CG_CONV;
+      } else if (c->used >= c->cg_max) {
+        c->done = 1;
+        c->state = CG_BUDGET;
+      } else {
+        c->beta = a[2] / c->rz;
+        c->rr = a[0];
+        c->rz = a[2];
+      }
+    }, skip);
+    map_skip(n, [=] __device__(long long i) {
+      p[i] = (pc ? mi[i] * r[i] : r[i]) + V(c->beta) * p[i];
+    }, skip);
+  }
+
+  // The CG loop of level l as an executable graph: a while node whose body
+  // is cg_iter and k_cg_cond.  Built on first use and rebuilt when the
+  // pressure (a kernel argument of the FP32 Hessian) or the preconditioning
+  // flag changes; a level's subproblem vectors sit at fixed addresses.  Null where the driver cannot build it (the caller then
+  // drives the loop from the host).
+  template <class V>
+  cudaGraphExec_t cg_graph(int l, V* p, V* q, const V* ga, const V* gb, const V* mi, V* w, V* r,
+                           bool pc) {
+    if (!H->cg_graph_ok) return nullptr;
+    if ((int)H->cg_graphs.size() < L) H->cg_graphs.resize(L);
+    pf_hierarchy::CgGraph& G = H->cg_graphs[l];
+    if (G.exec && G.p == H->p && G.pc == (pc ? 1 : 0) && G.vsize == int(sizeof(V)) &&
+        G.precision == P.precision && G.coarse_model == P.coarse_model && G.vp == p)
+      return G.exec;
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = pf_hierarchy::CgGraph{};
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    cudaGraph_t body = nullptr;
+    if (ok) ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+      if (ok) body = cp.conditional.phGraph_out[0];
+    }
+    if (ok) ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      bool launched = true;
+      const cudaStream_t saved = st;
+      const long long saved_launches = S.launches;
+      st = cs;  // cg_iter launches on st
+      try {
+        cg_iter<V>(l, p, q, ga, gb, mi, w, r, pc);
+        k_cg_cond<<<1, 1, 0, cs>>>(H->ctrl, h);
+        launched = cudaGetLastError() == cudaSuccess;
+      } catch (const CudaFail&) {
+        launched = false;
+      }
+      st = saved;
+      G.nodes = int(S.launches - saved_launches) + 1;  // + the condition kernel
+      S.launches = saved_launches;
+      cudaGraph_t out = nullptr;
+      ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && launched;
+    }
+    if (cs) cudaStreamDestroy(cs);
+    cudaGraphExec_t ex = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();  // clear a non-sticky error of the failed build
+      if (g) cudaGraphDestroy(g);
+      H->cg_graph_ok = false;
+      return nullptr;
+    }
+    const int nodes = G.nodes;
+    G.graph = g;
+    G.exec = ex;
+    G.nodes = nodes;
+    G.p = H->p;
+    G.pc = pc ? 1 : 0;
+    G.vsize = int(sizeof(V));
+    G.precision = P.precision;
+    G.coarse_model = P.coarse_model;
+    G.vp = p;
+    return ex;
+  }
+
   // Projected-search truncated CG for min g.s + 1/2 s.Hs over lo <= s <= hi
   // (eq. model_qp); the step is left in B.s (FP64).  On sub32 levels the
   // solve runs on FP32 copies of g and of the box, rounded towards zero so
@@ -775,78 +940,21 @@ struct Solver {
       k_ctrl_start<<<1, 1, 0, st>>>(c, rr, rr2[1], tol, used, cg_max);
       ck(cudaGetLastError(), "ctrl");
       S.launches += 1;
+      bool ran = false;
+      // the whole loop as one CUDA graph: a while node around one
+      // iteration, repeated on the device until the control block stops the
+      // run (no host polls); the host-polled loop below where no graph can
+      // be built
+      if (cudaGraphExec_t ex = cg_graph<V>(l, p, q, ga, gb, mi, w, r, pc)) {
+        ck(cudaGraphLaunch(ex, st), "cg_graph");
+        ck(cudaMemcpyAsync(H->h_ctrl, c, sizeof(CgCtrl), cudaMemcpyDeviceToHost, st), "ctrl");
+        ck(cudaStreamSynchronize(st), "sync");
+        S.launches += (long long)H->cg_graphs[l].nodes * (H->h_ctrl->used - used);
+        ran = true;
+      }
       int chunk = 2;
-      for (;;) {
-        for (int k = 0; k < chunk; ++k) {
-          if (std::is_same<V, float>::value && n % 4 == 0) {
-            hv<V>(l, p, q, skip, false);
-            const long long n4 = n / 4;
-            k_cg_dot4<<<reduce_grid(n4), 256, 0, st>>>(n4, reinterpret_cast<const float*>(p),
-                                                      reinterpret_cast<const float*>(q), c,
-                                                      H->scratch.partials, H->scratch.counter);
-            ck(cudaGetLastError(), "cg_dot");
-            S.launches += 1;
-          } else {
-            hv<V>(l, p, q, skip, false);
-            red_fin<1, OpSum, V>(n, [=] __device__(long long i, V(&o)[1]) { o[0] = p[i] * q[i]; },
-                                 [=] __device__(double(&a)[1]) {
-              c->kappa = a[0];
-              c->used += 1;
-              if (a[0] <= 0.0) {
-                c->done = 1;
-                c->state = CG_NEGCURV;
-              } else {
-                c->alpha = c->rz / a[0];
-              }
-            }, skip);
-          }
-          if (std::is_same<V, float>::value && n % 4 == 0) {
-            const long long n4 = n / 4;
-            const float *fa = reinterpret_cast<const float*>(ga),
-                        *fb = reinterpret_cast<const float*>(gb),
-                        *fq = reinterpret_cast<const float*>(q),
-                        *fm = reinterpret_cast<const float*>(mi);
-            float *fw = reinterpret_cast<float*>(w), *fr = reinterpret_cast<float*>(r),
-                  *fp = reinterpret_cast<float*>(p);
-            k_cg_update4<<<reduce_grid(n4), 256, 0, st>>>(n4, fa, fb, fq, fp, fm, pc, fw, fr, c,
-                                                         H->scratch.partials, H->scratch.counter);
-            ck(cudaGetLastError(), "cg_update");
-            k_cg_dir4<<<reduce_grid(n4), 256, 0, st>>>(n4, fa, fr, fm, pc, fp, c);
-            ck(cudaGetLastError(), "cg_dir");
-            S.launches += 2;
-          } else {
-            red_fin<3, OpSum, V>(n, [=] __device__(long long i, V(&o)[3]) {
-              const V al = V(c->alpha);
-              const V a = ga[i];
-              const V qi = a < Z ? q[i] : Z;
-              const V wi = w[i] + al * p[i];
-              w[i] = wi;
-              const V ri = r[i] - al * qi;
-              r[i] = ri;
-              o[0] = ri * ri;
-              o[1] = (wi < a || wi > gb[i]) ? V(1) : Z;
-              o[2] = ri * (pc ? mi[i] * ri : ri);
-            }, [=] __device__(double(&a)[3]) {
-              if (a[1] > 0.0) {
-                c->done = 1;
-                c->state = CG_LEAVE;
-              } else if (sqrt(a[0]) <= c->tol) {
-                c->done = 1;
-                c->state = CG_CONV;
-              } else if (c->used >= c->cg_max) {
-                c->done = 1;
-                c->state = CG_BUDGET;
-              } else {
-                c->beta = a[2] / c->rz;
-                c->rr = a[0];
-                c->rz = a[2];
-              }
-            }, skip);
-            map_skip(n, [=] __device__(long long i) {
-              p[i] = (pc ? mi[i] * r[i] : r[i]) + V(c->beta) * p[i];
-            }, skip);
-          }
-        }
+      while (!ran) {
+        for (int k = 0; k < chunk; ++k) cg_iter<V>(l, p, q, ga, gb, mi, w, r, pc);
         ck(cudaMemcpyAsync(H->h_ctrl, c, sizeof(CgCtrl), cudaMemcpyDeviceToHost, st), "ctrl");
         ck(cudaStreamSynchronize(st), "sync");
         if (H->h_ctrl->done) break;
