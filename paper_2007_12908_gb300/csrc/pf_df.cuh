@@ -6,11 +6,11 @@
 //
 // Built on error-free transformations: TwoSum (Knuth, TAOCP vol. 2,
 // Sec. 4.2.2) and FastTwoSum (Dekker 1971) give s + e = a + b exactly;
-// TwoProduct with a fused multiply-add gives p + e = a * b exactly.  The sum
-// is the accurate double-length addition (both parts added separately,
-// renormalised twice), the product Dekker's double-length multiplication
-// with its cross terms folded in by FMA, the quotient long division with
-// two correction steps.  Relative error of each operation about 2^-47.
+// TwoProduct with a fused multiply-add gives p + e = a * b exactly.  The
+// product is Dekker's double-length multiplication with its cross terms
+// folded in by FMA, the quotient long division with two correction steps;
+// sums come in Dekker's form (operator+) and an accurate form (both parts
+// added separately, renormalised twice) for cancelling totals.
 // Requires IEEE FP32 without flush-to-zero and without reassociation (the
 // library is built without fast-math).
 #pragma once
@@ -47,13 +47,27 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
   e = b - (s - a);
 }
 
-__device__ __forceinline__ df operator+(df x, df y) {
+// Accurate double-length sum: error about 2^-47 |x + y| even under
+// cancellation.  Used where sums of many elements cancel (nodal sums of
+// element contributions, energy totals).
+__device__ __forceinline__ df add_accurate(df x, df y) {
   float s, e, t, f;
   two_sum(x.hi, y.hi, s, e);
   two_sum(x.lo, y.lo, t, f);
   e += t;
   fast_two_sum(s, e, s, e);
   e += f;
+  fast_two_sum(s, e, s, e);
+  return df(s, e);
+}
+
+// Dekker's double-length sum: error about 2^-46 (|x| + |y|), half the
+// instructions of add_accurate.  The operator form, used inside the element
+// algebra, whose intermediate sums do not cancel to far below their terms.
+__device__ __forceinline__ df operator+(df x, df y) {
+  float s, e;
+  two_sum(x.hi, y.hi, s, e);
+  e += x.lo + y.lo;
   fast_two_sum(s, e, s, e);
   return df(s, e);
 }

@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(256) k_grad_gather_df(Geom g, const float2* __
 #pragma unroll
       for (int f = 0; f < F; ++f) {
         const float2 v = scratch[(f * NC + a) * g.NE + e];
-        acc[f] += df(v.x, v.y);
+        acc[f] = add_accurate(acc[f], df(v.x, v.y));
       }
     }
 #pragma unroll
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(256) k_energy_df(Geom g, Mat<df> m, const floa
     elem_coords<D>(g, e, ex, ey, ez);
     df xe[D + 1][1 << D];
     gather_df<D>(g, xd, ex, ey, ez, xe);
-    part += elem_energy<D, df>(xe, m);
+    part = add_accurate(part, elem_energy<D, df>(xe, m));
   }
   double acc[1] = {df_to_double(part)};
   grid_finish<1, OpSum>(acc, partials, counter, out);
