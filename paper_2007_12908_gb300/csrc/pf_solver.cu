@@ -326,6 +326,24 @@ __global__ void k_cg_cond(CgCtrl* c, cudaGraphConditionalHandle h) {
   cudaGraphSetConditional(h, c->done ? 0u : 1u);
 }
 
+// Grid for a grid-stride kernel of 256-thread blocks over `items` work
+// items: every block resident at once (occupancy x SMs, computed once per
+// kernel), no more than the items need and no more than the reduction
+// scratch holds.  A second, partial wave of blocks would leave SMs idle.
+template <class K>
+static int resident_grid(K kernel, long long items) {
+  static const int cap = [kernel] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+    const int r = per_sm * sms;
+    return r > 0 ? std::min(r, kMaxBlocks) : kMaxBlocks;
+  }();
+  const long long want = (items + 255) / 256;
+  return int(std::max(1LL, std::min<long long>(want, cap)));
+}
+
 static int map_grid(long long n) {
   long long b = (n + 255) / 256;
   return int(std::max(1LL, std::min(b, 4LL * 1216)));
@@ -660,12 +678,14 @@ struct Solver {
     CgCtrl* c = H->ctrl;
     const long long n4 = B.n / 4;
     ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done), "hessvec32");
-    k_cg_dot4<<<reduce_grid(n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials, H->scratch.counter);
+    k_cg_dot4<<<resident_grid(k_cg_dot4, n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials,
+                                                            H->scratch.counter);
     ck(cudaGetLastError(), "cg_dot");
-    k_cg_update4<<<reduce_grid(n4), 256, 0, s>>>(n4, ga, gb, q, p, mi, pc, w, r, c,
-                                                 H->scratch.partials, H->scratch.counter);
+    k_cg_update4<<<resident_grid(k_cg_update4, n4), 256, 0, s>>>(
+        n4, ga, gb, q, p, mi, pc, w, r, c, H->scratch.partials, H->scratch.counter);
     ck(cudaGetLastError(), "cg_update");
-    k_cg_dir4<<<reduce_grid(n4), 256, 0, s>>>(n4, ga, r, mi, pc, const_cast<float*>(p), c);
+    k_cg_dir4<<<resident_grid(k_cg_dir4, n4), 256, 0, s>>>(n4, ga, r, mi, pc, const_cast<float*>(p),
+                                                            c);
     ck(cudaGetLastError(), "cg_dir");
   }
 
@@ -762,6 +782,10 @@ struct Solver {
       ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
       if (ok) body = cp.conditional.phGraph_out[0];
     }
+    // occupancy queries of the captured launches happen before the capture
+    resident_grid(k_cg_dot4, 1);
+    resident_grid(k_cg_update4, 1);
+    resident_grid(k_cg_dir4, 1);
     if (ok) ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
     if (ok) ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -902,7 +926,7 @@ struct Solver {
       if constexpr (std::is_same<V, float>::value) {
         if (n % 4 == 0) {
           const long long n4 = n / 4;
-          k_cg_init4<<<reduce_grid(n4), 256, 0, st>>>(n4, lo, hi, s, g, Hs, mi, pc, r, p, w, ga, gb,
+          k_cg_init4<<<resident_grid(k_cg_init4, n4), 256, 0, st>>>(n4, lo, hi, s, g, Hs, mi, pc, r, p, w, ga, gb,
                                                        H->scratch.partials, H->scratch.counter,
                                                        H->d_res);
           ck(cudaGetLastError(), "cg_init");
