@@ -386,7 +386,7 @@ struct Solver {
   // ---------------------------------------------------------------- helpers
   template <class Fn>
   void map(long long n, Fn f) {
-    k_map<<<map_grid(n), 256, 0, st>>>(n, f);
+    k_map<<<resident_grid(k_map<Fn>, n), 256, 0, st>>>(n, f);
     ck(cudaGetLastError(), "map");
     S.launches += 1;
   }
@@ -408,8 +408,8 @@ struct Solver {
 
   template <int K, class Op, class A = double, class Fn>
   void reduce(long long n, Fn f, double* out) {
-    k_red<K, Op, A><<<reduce_grid(n), 256, 0, st>>>(n, f, H->scratch.partials, H->scratch.counter,
-                                                     H->d_res);
+    k_red<K, Op, A><<<resident_grid(k_red<K, Op, A, Fn>, n), 256, 0, st>>>(
+        n, f, H->scratch.partials, H->scratch.counter, H->d_res);
     ck(cudaGetLastError(), "reduce");
     S.launches += 1;
     fetch(K, out);
