@@ -164,7 +164,9 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
   for (int l = 0; l < h->L; ++l) {
     LevelBuf& B = h->lv[l];
     B.n = F * h->geo[l].N;
-    const size_t bytes = sizeof(double) * B.n;
+    // 4 spare values: the FP32 subproblem keeps two 16-byte-aligned FP32
+    // vectors of padded length in one buffer
+    const size_t bytes = sizeof(double) * (B.n + 4);
     double** vecs[] = {&B.x, &B.lb, &B.ub, &B.x0, &B.xlag, &B.dg, &B.g, &B.s, &B.lo, &B.hi,
                        &B.Hs, &B.r, &B.p, &B.q, &B.w, &B.Hw, &B.t1, &B.t2, &B.t3, &B.gin,
                        &B.gout, &B.dh, &B.minv, &B.g0};

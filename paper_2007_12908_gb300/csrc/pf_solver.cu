@@ -344,6 +344,19 @@ static int resident_grid(K kernel, long long items) {
   return int(std::max(1LL, std::min<long long>(want, cap)));
 }
 
+static inline long long pad4(long long n) { return (n + 3) & ~3LL; }
+
+// Zero lanes [n, np) of up to 16 FP32 vectors.
+struct PadLanes {
+  float* v[16];
+  int count;
+  long long n, np;
+};
+__global__ void k_zero_pad(PadLanes z) {
+  const long long pad = z.np - z.n;
+  for (int t = threadIdx.x; t < z.count * pad; t += blockDim.x) z.v[t / pad][z.n + t % pad] = 0.f;
+}
+
 static int map_grid(long long n) {
   long long b = (n + 255) / 256;
   return int(std::max(1LL, std::min(b, 4LL * 1216)));
@@ -676,7 +689,7 @@ struct Solver {
                 const float* mi, float* w, float* r, bool pc, cudaStream_t s) {
     LevelBuf& B = H->lv[l];
     CgCtrl* c = H->ctrl;
-    const long long n4 = B.n / 4;
+    const long long n4 = pad4(B.n) / 4;
     ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done), "hessvec32");
     k_cg_dot4<<<resident_grid(k_cg_dot4, n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials,
                                                             H->scratch.counter);
@@ -699,11 +712,9 @@ struct Solver {
     const int* skip = &H->ctrl->done;
     const V Z = V(0);
     if constexpr (std::is_same<V, float>::value) {
-      if (n % 4 == 0) {
-        cg_iter4(l, p, q, ga, gb, mi, w, r, pc, st);
-        S.launches += 4;
-        return;
-      }
+      cg_iter4(l, p, q, ga, gb, mi, w, r, pc, st);
+      S.launches += 4;
+      return;
     }
     hv<V>(l, p, q, skip, false);
     red_fin<1, OpSum, V>(n, [=] __device__(long long i, V(&o)[1]) { o[0] = p[i] * q[i]; },
@@ -843,7 +854,10 @@ struct Solver {
                             B.t1, B.t2});
       return;
     }
-    auto half = [n](double* d, int k) { return reinterpret_cast<float*>(d) + k * n; };
+    // two FP32 vectors per FP64 buffer, each on a 16-byte boundary (stride
+    // pad4(n); the buffers carry 4 spare doubles for it)
+    const long long np = pad4(n);
+    auto half = [np](double* d, int k) { return reinterpret_cast<float*>(d) + k * np; };
     float *g32 = half(B.t3, 0), *lo32 = half(B.t3, 1), *hi32 = half(B.Hw, 0);
     {
       const double *g = B.g, *lo = B.lo, *hi = B.hi;
@@ -857,6 +871,16 @@ struct Solver {
                            half(B.Hw, 1), half(B.Hs, 0), half(B.Hs, 1), half(B.p, 0),
                            half(B.p, 1), half(B.w, 0), half(B.w, 1), half(B.r, 0),
                            half(B.r, 1), half(B.q, 0)};
+    if (np != n) {
+      // lanes n .. np-1 of every view: 0, so that they act as fixed dofs
+      // (zero gaps) in the float4 passes and no stale value meets a 0
+      PadLanes z{{g32, lo32, hi32, reinterpret_cast<float*>(B.minv), v.s, v.Hs, v.r, v.p, v.q, v.w,
+                  v.a, v.b, v.t1, v.t2},
+                 14, n, np};
+      k_zero_pad<<<1, 64, 0, st>>>(z);
+      ck(cudaGetLastError(), "zero_pad");
+      S.launches += 1;
+    }
     subproblem_t<float>(l, delta, cg_max, v);
     const float* s32 = v.s;
     double* s = B.s;
@@ -924,17 +948,14 @@ struct Solver {
       double rr2[2];
       // residual of the model on the free set of s, its gaps, p = M^-1 r
       if constexpr (std::is_same<V, float>::value) {
-        if (n % 4 == 0) {
-          const long long n4 = n / 4;
-          k_cg_init4<<<resident_grid(k_cg_init4, n4), 256, 0, st>>>(n4, lo, hi, s, g, Hs, mi, pc, r, p, w, ga, gb,
-                                                       H->scratch.partials, H->scratch.counter,
-                                                       H->d_res);
-          ck(cudaGetLastError(), "cg_init");
-          S.launches += 1;
-          fetch(2, rr2);
-        }
-      }
-      if (!(std::is_same<V, float>::value && n % 4 == 0))
+        const long long n4 = pad4(n) / 4;
+        k_cg_init4<<<resident_grid(k_cg_init4, n4), 256, 0, st>>>(
+            n4, lo, hi, s, g, Hs, mi, pc, r, p, w, ga, gb, H->scratch.partials, H->scratch.counter,
+            H->d_res);
+        ck(cudaGetLastError(), "cg_init");
+        S.launches += 1;
+        fetch(2, rr2);
+      } else {
         reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
           const V a = lo[i] - s[i], b = hi[i] - s[i];
           const bool fr = a < Z && Z < b;
@@ -948,6 +969,7 @@ struct Solver {
           o[0] = ri * ri;
           o[1] = ri * zi;
         }, rr2);
+      }
       const double rr = rr2[0];
       if (tol < 0.0) {
         const double r0 = std::sqrt(rr);
