@@ -46,6 +46,14 @@ METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same G
 TRAFFIC_HESSVEC_FP32 = 68.723e6 + 10.559e6
 TRAFFIC_HESSVEC_FP64 = 7595.291e6 + 86.475e6
 UNIT = "s/load-step"
+# FP32 flops of one element of the 3D FP32 Hessian product (the paired-FMA
+# element algebra and its corner sums), from the FP32 instruction counts of
+# one ncu capture (FFMA2 x4, FFMA x2, FADD2/FMUL2 x2, FADD/FMUL x1) divided by
+# the element evaluations of the launch (profiles/elem_kernels_3d_129cubed_ncu.md).
+FLOP32_PER_ELEMENT = 2055
+# FP32 peak of one GB300 from its unit counts and clock: 152 SMs x 128 FP32
+# lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # Finest-level-equivalent element passes per load step of the CUDA path on
 # this workload (default configuration: mixed precision, extrapolated
@@ -338,6 +346,7 @@ def run_ours(args):
     t32 = time_kernel(lambda: pf.hessvec(H, level, x32, v32, o32))
     t_grad = time_kernel(lambda: pf.gradient(H, level, x, out))
     fma64 = B.probe_fma(pf.PF_FP64)
+    fma32 = B.probe_fma(pf.PF_FP32)
     hbm = None
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -355,12 +364,20 @@ def run_ours(args):
               "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
               "flop_per_node": 864, "fp64_fma_peak_tflops": fma64 / 1e12,
               "gdofs": ndof / t64 / 1e9, "us_per_launch": t64 * 1e6}
-    roof32 = {"kernel": "hessvec_fp32", "bound": "hbm", "achieved": bytes32 / t32 / 1e9,
-              "peak": hbm, "unit": "GB/s", "frac": bytes32 / t32 / 1e9 / hbm,
+    # The FP32 product is bound by FP32 issue (FMA pipe ~60 % busy, DRAM ~5 %):
+    # ALU roofline, algorithmic flops = FLOP32_PER_ELEMENT x elements
+    ne = (g_n[0] - 1) * (g_n[1] - 1) * (g_n[2] - 1)
+    flops32 = FLOP32_PER_ELEMENT * ne
+    roof32 = {"kernel": "hessvec_fp32", "bound": "alu", "achieved": flops32 / t32 / 1e12,
+              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+              "frac": flops32 / t32 / 1e12 / FP32_PEAK_TFLOPS,
               # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
               # this kernel (profiles/elem_kernels_3d_129cubed_ncu.md), per launch
               "traffic": TRAFFIC_HESSVEC_FP32,
-              "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+              "fp32_fma_probe_tflops": fma32 / 1e12,
+              "flop_per_element": FLOP32_PER_ELEMENT,
+              "hbm_achieved_gbs": bytes32 / t32 / 1e9, "hbm_peak_gbs": hbm,
               "gdofs": ndof / t32 / 1e9, "us_per_launch": t32 * 1e6}
     roofline = roof64 if args.precision == "fp64" else roof32
 
