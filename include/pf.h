@@ -82,13 +82,13 @@ typedef struct {
   double rtol;           /* stop when ||x - P(x - grad f)|| <= rtol * start  */
   double atol;           /* ... or <= atol                                   */
   int coarse_model;      /* PF_GALERKIN or PF_FIRST_ORDER                    */
-  int precision;         /* PF_FP64, or PF_FP32 = mixed: on every level but
-                            the coarsest an FP32 Hessian and FP32 subproblem,
-                            FP32 gradient steps after accepted steps and FP32
-                            higher-order terms of rho's energy difference;
-                            double-float (pf_gradient_df) stopping-test
-                            gradients and energy; FP64 first-order term of
-                            rho, radius, norms and coarsest-level Hessian  */
+  int precision;         /* PF_FP64, or PF_FP32 = mixed: on every level an
+                            FP32 Hessian and FP32 subproblem, FP32 gradient
+                            steps after accepted steps and FP32 higher-order
+                            terms of rho's energy difference; double-float
+                            (pf_gradient_df) stopping-test gradients and
+                            energy; FP64 first-order term of rho, radius and
+                            norms                                            */
   int precondition;      /* 1: Jacobi (Hessian-diagonal) preconditioned CG (1) */
   double level_rtol;     /* a non-finest level stops its TR steps once its
                             projected gradient fell by this factor (1e-3;

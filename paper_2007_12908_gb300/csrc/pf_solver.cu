@@ -533,9 +533,8 @@ struct Solver {
   // ---------------------------------------------------------------- level model h^l
   bool finest(int l) const { return l == L - 1; }
   bool galerkin(int l) const { return !finest(l) && P.coarse_model == PF_GALERKIN; }
-  // mixed precision: FP32 Hessian on every level but the coarsest (which,
-  // like energy, rho and the radius, stays FP64)
-  bool mixed32(int l) const { return mixed && (l > 0 || L == 1); }
+  // mixed precision: FP32 Hessian (and FP32 subproblem) on every level
+  bool mixed32(int l) const { return mixed; }
 
   // finest-level units of one application of the lagged model Hessian
   double hlag_units(int l) const { return galerkin(l) ? hlag_units(l + 1) : frac(l); }
