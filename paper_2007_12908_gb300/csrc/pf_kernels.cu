@@ -321,12 +321,19 @@ __global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
 // with 8 16-byte shared loads at fixed offsets, and the colour-phase sums
 // add one float4 per node.  Same element algebra and the same fixed
 // summation order as k_elem_scatter<3, float, ..., OP_HESS>.
-template <class TV>
-__global__ void __launch_bounds__(256, 2)
+// T: tile edge in nodes, 8 (256 threads, three element rounds) or 4 (128
+// threads, one round) for grids too small to give every SM two 8^3 tiles.
+template <int T>
+struct HessTile {
+  static constexpr int THREADS = T == 8 ? 256 : 128;
+};
+
+template <class TV, int T = 8>
+__global__ void __launch_bounds__(HessTile<T>::THREADS, T == 8 ? 2 : 4)
     k_hess_tile3(Geom g, Mat<float> m, const float* __restrict__ x, const TV* __restrict__ v,
                  TV* __restrict__ y, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  constexpr int T = 8, E = T + 1, NN = T + 2, NH = NN * NN * NN, NT = 256;
+  constexpr int E = T + 1, NN = T + 2, NH = NN * NN * NN, NT = HessTile<T>::THREADS;
   __shared__ float4 xs[NH], vs[NH];
   __shared__ float4 acc[T * T * T];
   const int ox = blockIdx.x * T, oy = blockIdx.y * T, oz = blockIdx.z * T;
@@ -427,7 +434,15 @@ cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, vo
 template <class TV>
 static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const float* x,
                                      const TV* v, TV* y, const int* skip, cudaStream_t st) {
-  k_hess_tile3<TV><<<scatter_grid<3>(g), 256, 0, st>>>(g, cast_mat<float>(m), x, v, y, skip);
+  auto tiles = [&g](int t) {
+    return dim3((g.n[0] + t - 1) / t, (g.n[1] + t - 1) / t, (g.n[2] + t - 1) / t);
+  };
+  const dim3 b8 = tiles(8);
+  if ((long long)b8.x * b8.y * b8.z >= 2 * 152)
+    k_hess_tile3<TV, 8><<<b8, HessTile<8>::THREADS, 0, st>>>(g, cast_mat<float>(m), x, v, y, skip);
+  else
+    k_hess_tile3<TV, 4><<<tiles(4), HessTile<4>::THREADS, 0, st>>>(g, cast_mat<float>(m), x, v, y,
+                                                                  skip);
   return cudaGetLastError();
 }
 
