@@ -919,14 +919,30 @@ struct Solver {
     bool ok = false;
     for (int bt = 0; bt <= P.cauchy_backtracks; ++bt) {
       const V tt = V(t);
-      map(n, [=] __device__(long long i) { s[i] = clampv(-tt * g[i], lo[i], hi[i]); });
-      hv<V>(l, s, Hs);
-      S.hv_cauchy += 1;
+      // s = P(-t g).  Where no movable dof is cut by its bound, s = -t t1
+      // exactly, so Hs = -t H t1, g.s = -t t1.t1 and s.Hs = t^2 t1.Ht1 come
+      // from the products above; the pass counts the cut dofs.
+      double cut;
+      reduce<1, OpSum, V>(n, [=] __device__(long long i, V(&o)[1]) {
+        const V gi = g[i], di = -tt * gi;
+        const V si = clampv(di, lo[i], hi[i]);
+        s[i] = si;
+        Hs[i] = -tt * t2[i];
+        const bool mv = (gi < Z && hi[i] > Z) || (gi > Z && lo[i] < Z);
+        o[0] = (mv && si != di) ? V(1) : Z;
+      }, &cut);
       double a[2];
-      reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
-        o[0] = g[i] * s[i];
-        o[1] = s[i] * Hs[i];
-      }, a);
+      if (cut == 0.0) {
+        a[0] = -double(tt) * cg2[1];
+        a[1] = double(tt) * double(tt) * cg2[0];
+      } else {
+        hv<V>(l, s, Hs);
+        S.hv_cauchy += 1;
+        reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
+          o[0] = g[i] * s[i];
+          o[1] = s[i] * Hs[i];
+        }, a);
+      }
       if (a[0] + 0.5 * a[1] <= P.cauchy_c * a[0]) {
         ok = true;
         break;
