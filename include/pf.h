@@ -138,6 +138,9 @@ typedef struct {
   long long hv_cauchy;   /* Hessian applications in Cauchy-point searches    */
   long long hv_search;   /* Hessian applications in projected searches       */
   long long cg_restarts; /* CG runs restarted after a projected search       */
+  double pg_ref;         /* the stopping test's reference: params.pg_ref if
+                            given, else the projected gradient at the plain
+                            start (extrapolated start), else pg0           */
 } pf_rmtr_stats;
 
 /* Fills p with the defaults listed beside each field above. */

@@ -66,7 +66,8 @@ class RmtrStats(C.Structure):
                 ("fe_gradient", C.c_double), ("fe_energy", C.c_double),
                 ("cg_level", C.c_longlong * 8), ("tr_level", C.c_longlong * 8),
                 ("rej_level", C.c_longlong * 8), ("hv_cauchy", C.c_longlong),
-                ("hv_search", C.c_longlong), ("cg_restarts", C.c_longlong)]
+                ("hv_search", C.c_longlong), ("cg_restarts", C.c_longlong),
+                ("pg_ref", C.c_double)]
 
     def as_dict(self):
         out = {}

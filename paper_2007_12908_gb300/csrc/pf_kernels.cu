@@ -328,9 +328,11 @@ struct HessTile {
   static constexpr int THREADS = T == 8 ? 256 : 128;
 };
 
-template <class TV, int T = 8>
+// OP: OP_HESS (y = H(x) v, paired FP32 algebra) or OP_GDIFF (y += grad E(x)
+// - grad E(x - v), scalar FP32 algebra); TX: type of x in memory.
+template <class TV, int T = 8, int OP = OP_HESS, class TX = float>
 __global__ void __launch_bounds__(HessTile<T>::THREADS, T == 8 ? 2 : 4)
-    k_hess_tile3(Geom g, Mat<float> m, const float* __restrict__ x, const TV* __restrict__ v,
+    k_hess_tile3(Geom g, Mat<float> m, const TX* __restrict__ x, const TV* __restrict__ v,
                  TV* __restrict__ y, const int* __restrict__ skip) {
   if (skip && *skip) return;
   constexpr int E = T + 1, NN = T + 2, NH = NN * NN * NN, NT = HessTile<T>::THREADS;
@@ -345,8 +347,9 @@ __global__ void __launch_bounds__(HessTile<T>::THREADS, T == 8 ? 2 : 4)
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
     if (gx >= 0 && gx < nx0 && gy >= 0 && gy < ny0 && gz >= 0 && gz < nz0) {
       const long long idx = gx + (long long)nx0 * (gy + (long long)ny0 * gz);
-      a = make_float4(x[idx], x[N + idx], x[2 * N + idx], x[3 * N + idx]);
+      a = make_float4(float(x[idx]), float(x[N + idx]), float(x[2 * N + idx]), float(x[3 * N + idx]));
       b = make_float4(float(v[idx]), float(v[N + idx]), float(v[2 * N + idx]), float(v[3 * N + idx]));
+      if constexpr (OP == OP_GDIFF) b = make_float4(-b.x, -b.y, -b.z, -b.w);
     }
     xs[j] = a;
     vs[j] = b;
@@ -370,7 +373,8 @@ __global__ void __launch_bounds__(HessTile<T>::THREADS, T == 8 ? 2 : 4)
         xe[0][a] = xa.x; xe[1][a] = xa.y; xe[2][a] = xa.z; xe[3][a] = xa.w;
         ve[0][a] = va.x; ve[1][a] = va.y; ve[2][a] = va.z; ve[3][a] = va.w;
       }
-      p2::elem_hessvec(xe, ve, m, out);
+      if constexpr (OP == OP_GDIFF) elem_gradient_diff<3, float>(xe, ve, m, out);
+      else p2::elem_hessvec(xe, ve, m, out);
     }
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -393,10 +397,17 @@ __global__ void __launch_bounds__(HessTile<T>::THREADS, T == 8 ? 2 : 4)
     if (gx < nx0 && gy < ny0 && gz < nz0) {
       const long long idx = gx + (long long)nx0 * (gy + (long long)ny0 * gz);
       const float4 t = acc[i];
-      y[idx] = TV(t.x);
-      y[N + idx] = TV(t.y);
-      y[2 * N + idx] = TV(t.z);
-      y[3 * N + idx] = TV(t.w);
+      if constexpr (OP == OP_GDIFF) {
+        y[idx] -= TV(t.x);
+        y[N + idx] -= TV(t.y);
+        y[2 * N + idx] -= TV(t.z);
+        y[3 * N + idx] -= TV(t.w);
+      } else {
+        y[idx] = TV(t.x);
+        y[N + idx] = TV(t.y);
+        y[2 * N + idx] = TV(t.z);
+        y[3 * N + idx] = TV(t.w);
+      }
     }
   }
 }
@@ -418,7 +429,12 @@ static cudaError_t launch_scatter(const Geom& g, const Mat<double>& m, const voi
 
 cudaError_t elem_gradient_step(const Geom& g, const Mat<double>& m, const double* x,
                                const double* s, double* y, cudaStream_t st) {
-  if (g.dim == 3) return launch_scatter<3, float, double, OP_GDIFF, double>(g, m, x, s, y, nullptr, st);
+  if (g.dim == 3) {
+    const dim3 b8((g.n[0] + 7) / 8, (g.n[1] + 7) / 8, (g.n[2] + 7) / 8);
+    k_hess_tile3<double, 8, OP_GDIFF, double><<<b8, HessTile<8>::THREADS, 0, st>>>(
+        g, cast_mat<float>(m), x, s, y, nullptr);
+    return cudaGetLastError();
+  }
   return launch_scatter<2, float, double, OP_GDIFF, double>(g, m, x, s, y, nullptr, st);
 }
 
@@ -972,15 +988,79 @@ cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x,
               : launch_energy_diff<2, double>(g, m, x, sv, s, out, st);
 }
 
+// 3D form of k_energy_diff_hi on element tiles: a block takes 8^3-element
+// tiles in turn (each element once), stages the tile's 9^3 corner nodes of x
+// and s in shared memory as float4, and adds the FP64 g . s of the nodes the
+// tile owns ([o, o+8) per axis, the last tile of an axis also its end node).
+// out = (gx . s, a2, a3, a4), deterministic (fixed tile order per block).
+__global__ void __launch_bounds__(256) k_energy_diff_hi_tile3(Geom g, Mat<float> m,
+                                                              const double* __restrict__ x,
+                                                              const double* __restrict__ s,
+                                                              const double* __restrict__ gx,
+                                                              double* partials, unsigned* counter,
+                                                              double* out) {
+  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN, NT = 256;
+  __shared__ float4 xs[NH], ss[NH];
+  const int tx = (g.ne[0] + T - 1) / T, ty = (g.ne[1] + T - 1) / T, tz = (g.ne[2] + T - 1) / T;
+  const long long ntiles = (long long)tx * ty * tz;
+  const long long N = g.N;
+  float acc[3] = {0.f, 0.f, 0.f};
+  double dot = 0.0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int bx = int(t % tx), by = int((t / tx) % ty), bz = int(t / ((long long)tx * ty));
+    const int ox = bx * T, oy = by * T, oz = bz * T;
+    __syncthreads();  // the previous tile's reads are done
+    for (int j = threadIdx.x; j < NH; j += NT) {
+      const int i = j % NN, jj = (j / NN) % NN, k = j / (NN * NN);
+      const int nx = ox + i, ny = oy + jj, nz = oz + k;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (nx < g.n[0] && ny < g.n[1] && nz < g.n[2]) {
+        const long long idx = nx + (long long)g.n[0] * (ny + (long long)g.n[1] * nz);
+        a = make_float4(float(x[idx]), float(x[N + idx]), float(x[2 * N + idx]), float(x[3 * N + idx]));
+        b = make_float4(float(s[idx]), float(s[N + idx]), float(s[2 * N + idx]), float(s[3 * N + idx]));
+        // g . s over the nodes this tile owns
+        const bool own = (i < T || bx == tx - 1) && (jj < T || by == ty - 1) && (k < T || bz == tz - 1);
+        if (gx && own)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) dot += gx[f * N + idx] * s[f * N + idx];
+      }
+      xs[j] = a;
+      ss[j] = b;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < T * T * T; e += NT) {
+      const int lx = e % T, ly = (e / T) % T, lz = e / (T * T);
+      if (ox + lx >= g.ne[0] || oy + ly >= g.ne[1] || oz + lz >= g.ne[2]) continue;
+      const int c0 = lx + NN * (ly + NN * lz);
+      float xe[4][8], se[4][8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int c = c0 + (a & 1) + NN * ((a >> 1) & 1) + NN * NN * ((a >> 2) & 1);
+        const float4 xa = xs[c], sa = ss[c];
+        xe[0][a] = xa.x; xe[1][a] = xa.y; xe[2][a] = xa.z; xe[3][a] = xa.w;
+        se[0][a] = sa.x; se[1][a] = sa.y; se[2][a] = sa.z; se[3][a] = sa.w;
+      }
+      float a4[4];
+      elem_energy_diff<3, float>(xe, se, m, a4);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[k] += a4[k + 1];
+    }
+  }
+  double d[4] = {dot, double(acc[0]), double(acc[1]), double(acc[2])};
+  grid_finish<4, OpSum>(d, partials, counter, out);
+}
+
 cudaError_t elem_energy_diff_hi(const Geom& g, const Mat<double>& m, const double* x,
                                 const double* sv, const double* gx, const Scratch& s,
                                 double* out, cudaStream_t st) {
   const int nb = reduce_grid(g.NE, 256);
   const long long n = (long long)(g.dim + 1) * g.N;
-  if (g.dim == 3)
-    k_energy_diff_hi<3><<<nb, 256, 0, st>>>(g, cast_mat<float>(m), x, sv, gx, n, s.partials,
-                                            s.counter, out);
-  else
+  if (g.dim == 3) {
+    const long long tiles = (long long)((g.ne[0] + 7) / 8) * ((g.ne[1] + 7) / 8) * ((g.ne[2] + 7) / 8);
+    const int nt = int(std::min<long long>(tiles, kMaxBlocks));
+    k_energy_diff_hi_tile3<<<nt, 256, 0, st>>>(g, cast_mat<float>(m), x, sv, gx, s.partials,
+                                                s.counter, out);
+  } else
     k_energy_diff_hi<2><<<nb, 256, 0, st>>>(g, cast_mat<float>(m), x, sv, gx, n, s.partials,
                                             s.counter, out);
   return cudaGetLastError();

@@ -1344,6 +1344,7 @@ struct Solver {
     S.converged = conv ? 1 : 0;
     S.pg0 = pg0;
     S.pg = pg;
+    S.pg_ref = ref;
     S.energy = energy(L - 1, B.x);
     copy(x_user, B.x, B.n);
     ck(cudaStreamSynchronize(st), "sync");

@@ -200,3 +200,24 @@ def test_mixed_precision_reaches_fp64_energy(pf):
     s32 = pf.rmtr_load_step(H, x2, pf.default_params(rtol=1e-12, precision=pf.PF_FP32))
     assert s32["converged"]
     assert abs(s32["energy"] - s64["energy"]) <= 1e-8 * abs(s64["energy"])
+
+
+def test_stopping_reference(pf):
+    """An extrapolated load step stops relative to the projected gradient at
+    the plain start under the new pressure (the state as given), which the
+    stats report: equal to pf_projected_gradient at that state."""
+    import torch
+    H, Ho = pair(3, (5, 5, 5), 3, 0.25, nu=0.25, p=0.0)
+    g = Ho.fine
+    rows = np.array([[0.5, 0.45, 0.52, 0.0, 0.6, 0.8, 0.3], [0.3, 0.6, 0.4, 1.0, 0.0, 0.0, 0.2]])
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    pf.fractures_set(H, pf.PF_DISC3D, rows, g.h, x)
+    for prec in (pf.PF_FP32, pf.PF_FP64):
+        prm = pf.default_params(precision=prec, start=pf.PF_START_EXTRAPOLATE)
+        for p in (1e-3, 1.5e-3, 2e-3):
+            pf.pressure_set(H, p)
+            direct = pf.projected_gradient(H, x)
+            st = pf.rmtr_load_step(H, x, prm)
+            assert st["converged"]
+            if st["pg_ref"] != st["pg0"]:  # extrapolated steps
+                assert abs(st["pg_ref"] - direct) <= 1e-10 * direct
