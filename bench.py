@@ -234,6 +234,8 @@ def kernels_only(pf, B, H, x, W):
                      ("gradient_fp64", lambda: pf.gradient(H, level, x, out)),
                      ("gradient_df", lambda: pf.gradient_df(H, level, x, out)),
                      ("energy_df", lambda: pf.energy_df(H, level, x)),
+                     ("gradient_step_fp32", lambda: pf.gradient_step(H, level, x, v, out)),
+                     ("energy_diff_mixed", lambda: pf.energy_diff_mixed(H, level, x, v, out)),
                      ("energy_diff_fp64", lambda: pf.energy_diff(H, level, x, v)),
                      ("energy_fp64", lambda: pf.energy(H, level, x))):
         a = torch.cuda.Event(enable_timing=True)
