@@ -253,6 +253,11 @@ pf_status pf_coarse_bounds(pf_hierarchy* h, int coarse, const double* lo_f_dev,
  * V-cycles (Algorithm 1, mu1 = mu2 = 1, Hessian lagging of Sec. 4.2.1) until
  * the projected gradient meets rtol/atol or max_cycles.  x_dev: finest FP64
  * state, updated in place.  params NULL = defaults.  stats may be NULL.
+ * Each level's CG loop runs as one CUDA graph (a conditional while node
+ * around one CG iteration), built on first use, rebuilt when the pressure,
+ * precision or coarse model change, and held by the hierarchy until
+ * pf_mesh_hierarchy_destroy.  The call synchronises the hierarchy's stream
+ * (it reads scalars back) and cannot itself be captured into a graph.
  * Errors: PF_ENOTCONV (x still updated), PF_ENONFINITE, PF_ECUDA. */
 pf_status pf_rmtr_load_step(pf_hierarchy* h, void* x_dev, const pf_rmtr_params* params,
                             pf_rmtr_stats* stats);
