@@ -85,6 +85,28 @@ __global__ void k_ctrl_start(CgCtrl* c, double rr, double rz, double tol, int us
   c->cg_max = cg_max;
 }
 
+// Start of a CG run from the restart reduction's (r.r, r.M^-1 r) on the
+// device: the forcing tolerance min(0.1, sqrt||r0||) ||r0|| on the first run
+// of a subproblem, and a run that starts already converged is stopped before
+// its first iteration (CG_CONV), so the host needs no read-back before it.
+__global__ void k_ctrl_start_dev(CgCtrl* c, const double* rrz, int first, int used, int cg_max) {
+  const double rr = rrz[0];
+  if (first) {
+    const double r0 = sqrt(rr);
+    c->tol = fmin(0.1, sqrt(r0)) * r0;
+  }
+  c->rr = rr;
+  c->rz = rrz[1];
+  c->alpha = 0.0;
+  c->beta = 0.0;
+  c->kappa = 0.0;
+  c->used = used;
+  c->cg_max = cg_max;
+  const bool stop = sqrt(rr) <= c->tol || rr == 0.0;
+  c->done = stop ? 1 : 0;
+  c->state = stop ? CG_CONV : CG_RUNNING;
+}
+
 template <int K, class Op, class A, class F>
 __global__ void __launch_bounds__(256) k_red(long long n, F f, double* partials, unsigned* counter,
                                              double* out) {
@@ -426,6 +448,15 @@ struct Solver {
     ck(cudaGetLastError(), "reduce");
     S.launches += 1;
     fetch(K, out);
+  }
+
+  // reduce() without the read-back: results stay at out_dev
+  template <int K, class Op, class A = double, class Fn>
+  void reduce_dev(long long n, Fn f, double* out_dev) {
+    k_red<K, Op, A><<<resident_grid(k_red<K, Op, A, Fn>, n), 256, 0, st>>>(
+        n, f, H->scratch.partials, H->scratch.counter, out_dev);
+    ck(cudaGetLastError(), "reduce");
+    S.launches += 1;
   }
 
   void fetch(int K, double* out) {
@@ -962,6 +993,8 @@ struct Solver {
     while (used < cg_max) {
       double rr2[2];
       // residual of the model on the free set of s, its gaps, p = M^-1 r
+      cudaGraphExec_t graph = cg_graph<V>(l, p, q, ga, gb, mi, w, r, pc);
+      bool ran = false;
       if constexpr (std::is_same<V, float>::value) {
         const long long n4 = pad4(n) / 4;
         k_cg_init4<<<resident_grid(k_cg_init4, n4), 256, 0, st>>>(
@@ -969,7 +1002,19 @@ struct Solver {
             H->d_res);
         ck(cudaGetLastError(), "cg_init");
         S.launches += 1;
-        fetch(2, rr2);
+        if (graph) {
+          // start, run and stop on the device: one read-back per CG run
+          k_ctrl_start_dev<<<1, 1, 0, st>>>(c, H->d_res, tol < 0.0 ? 1 : 0, used, cg_max);
+          ck(cudaGetLastError(), "ctrl");
+          ck(cudaGraphLaunch(graph, st), "cg_graph");
+          ck(cudaMemcpyAsync(H->h_ctrl, c, sizeof(CgCtrl), cudaMemcpyDeviceToHost, st), "ctrl");
+          ck(cudaStreamSynchronize(st), "sync");
+          S.launches += 1 + (long long)H->cg_graphs[l].nodes * (H->h_ctrl->used - used);
+          tol = H->h_ctrl->tol;
+          ran = true;
+        } else {
+          fetch(2, rr2);
+        }
       } else {
         reduce<2, OpSum, V>(n, [=] __device__(long long i, V(&o)[2]) {
           const V a = lo[i] - s[i], b = hi[i] - s[i];
@@ -985,12 +1030,14 @@ struct Solver {
           o[1] = ri * zi;
         }, rr2);
       }
-      const double rr = rr2[0];
-      if (tol < 0.0) {
-        const double r0 = std::sqrt(rr);
-        tol = std::min(0.1, std::sqrt(r0)) * r0;
+      if (!ran) {
+        const double rr = rr2[0];
+        if (tol < 0.0) {
+          const double r0 = std::sqrt(rr);
+          tol = std::min(0.1, std::sqrt(r0)) * r0;
+        }
+        if (std::sqrt(rr) <= tol || rr == 0.0) break;
       }
-      if (std::sqrt(rr) <= tol || rr == 0.0) break;
       // CG on the free set, driven on the device: each iteration is the
       // model Hessian, a reduction for p.Hp (its last block sets alpha or
       // flags non-positive curvature; p vanishes off the free set, so the
@@ -998,20 +1045,21 @@ struct Solver {
       // block tests the box, the forcing term and the budget and sets beta)
       // and the direction update.  The host polls the control block between
       // chunks of iterations; launches after a stop are no-ops.
-      k_ctrl_start<<<1, 1, 0, st>>>(c, rr, rr2[1], tol, used, cg_max);
-      ck(cudaGetLastError(), "ctrl");
-      S.launches += 1;
-      bool ran = false;
       // the whole loop as one CUDA graph: a while node around one
       // iteration, repeated on the device until the control block stops the
       // run (no host polls); the host-polled loop below where no graph can
       // be built
-      if (cudaGraphExec_t ex = cg_graph<V>(l, p, q, ga, gb, mi, w, r, pc)) {
-        ck(cudaGraphLaunch(ex, st), "cg_graph");
-        ck(cudaMemcpyAsync(H->h_ctrl, c, sizeof(CgCtrl), cudaMemcpyDeviceToHost, st), "ctrl");
-        ck(cudaStreamSynchronize(st), "sync");
-        S.launches += (long long)H->cg_graphs[l].nodes * (H->h_ctrl->used - used);
-        ran = true;
+      if (!ran) {
+        k_ctrl_start<<<1, 1, 0, st>>>(c, rr2[0], rr2[1], tol, used, cg_max);
+        ck(cudaGetLastError(), "ctrl");
+        S.launches += 1;
+        if (graph) {
+          ck(cudaGraphLaunch(graph, st), "cg_graph");
+          ck(cudaMemcpyAsync(H->h_ctrl, c, sizeof(CgCtrl), cudaMemcpyDeviceToHost, st), "ctrl");
+          ck(cudaStreamSynchronize(st), "sync");
+          S.launches += (long long)H->cg_graphs[l].nodes * (H->h_ctrl->used - used);
+          ran = true;
+        }
       }
       int chunk = 2;
       while (!ran) {
@@ -1122,17 +1170,33 @@ struct Solver {
       tr_box(l, B.x, delta);
       subproblem(l, delta, cg_max);
       Hlag(l, B.s, B.t2);
-      double a[2];
       const double *g = B.g, *s = B.s, *hs = B.t2;
-      reduce<2, OpSum>(B.n, [=] __device__(long long i, double(&v)[2]) {
+      auto pred_terms = [=] __device__(long long i, double(&v)[2]) {
         v[0] = g[i] * s[i];
         v[1] = s[i] * hs[i];
-      }, a);
-      const double pred = -(a[0] + 0.5 * a[1]);
+      };
+      double pred, dh = 0.0;
+      const bool merged = mixed32(l) && !galerkin(l);
+      if (merged) {
+        // the prediction's terms and the energy difference in one read-back
+        reduce_dev<2, OpSum>(B.n, pred_terms, H->d_res + 4);
+        ck(elem_energy_diff_hi(H->geo[l], H->mat[l], B.x, B.s, B.g, H->scratch, H->d_res, st),
+           "ediff_hi");
+        S.fe_energy += frac(l);
+        S.launches += 1;
+        double r6[6];
+        fetch(6, r6);
+        pred = -(r6[4] + 0.5 * r6[5]);
+        dh = r6[0] + r6[1] + r6[2] + r6[3];
+      } else {
+        double a[2];
+        reduce<2, OpSum>(B.n, pred_terms, a);
+        pred = -(a[0] + 0.5 * a[1]);
+      }
       S.tr_its += 1;
       S.tr_level[std::min(l, 7)] += 1;
       if (!(pred > 0.0)) break;
-      const double rho = -diff_h(l, B.x, B.s, B.g) / pred;
+      const double rho = -(merged ? dh : diff_h(l, B.x, B.s, B.g)) / pred;
       if (rho <= P.eta1) {
         S.tr_rejected += 1;
         S.rej_level[std::min(l, 7)] += 1;
