@@ -221,12 +221,12 @@ __global__ void __launch_bounds__(256) k_hess_coef(Geom g, Mat<T> m, const T* __
   }
 }
 
-// TC: compute precision (and that of x); TIO: precision of v and y.
+// TC: compute precision; TIO: precision of v and y; TM: precision of x in
+// memory (converted to TC in registers).
 // skip: when non-null and *skip != 0 the launch does nothing (the solver's
 // device-side CG stops this way without a host round trip).
 // FP32 instances are limited to 128 registers so that two CTAs (16 warps)
 // share an SM and hide the gather and barrier latency.
-// TM: precision of x in memory (converted to TC in registers).
 template <int D, class TC, class TIO, int OP, class TM = TC>
 __global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
     k_elem_scatter(Geom g, Mat<TC> m, const TM* __restrict__ x, const TIO* __restrict__ v,
@@ -276,10 +276,7 @@ __global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
 #pragma unroll
           for (int f = 0; f < F; ++f) ve[f][a] = TC(v[f * g.N + idx]);
         }
-        if constexpr (D == 3 && std::is_same<TC, float>::value)
-          p2::elem_hessvec(xe, ve, m, out);  // paired FP32 (FFMA2) arithmetic
-        else
-          elem_hessvec<D, TC>(xe, ve, m, out);
+        elem_hessvec<D, TC>(xe, ve, m, out);  // 3D FP32 products use k_hess_tile3
       } else if constexpr (OP == OP_DIAG) {
         elem_hessdiag<D, TC>(xe, m, out);
       } else {
