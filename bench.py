@@ -43,7 +43,7 @@ METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same G
 # DRAM bytes (read + write) per launch of the roofline kernels on this
 # workload from one ncu capture (profiles/elem_kernels_3d_129cubed_ncu.md);
 # to be re-captured whenever those kernels change.
-TRAFFIC_HESSVEC_FP32 = 68.723e6 + 10.559e6
+TRAFFIC_HESSVEC_FP32 = None  # re-captured below for the element-owned kernels
 TRAFFIC_HESSVEC_FP64 = 7595.291e6 + 86.475e6
 UNIT = "s/load-step"
 # FP32 flops of one element of the 3D FP32 Hessian product (the paired-FMA

@@ -152,6 +152,12 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
     pf_mesh_hierarchy_destroy(h);
     return rc;
   }
+  long long part = 0;
+  for (const Geom& g : h->geo) part = std::max(part, etile_part_count(g));
+  if (part > 0 && (rc = alloc(h, &h->etile_part, sizeof(float4) * part))) {
+    pf_mesh_hierarchy_destroy(h);
+    return rc;
+  }
   if (cudaMallocHost((void**)&h->h_res, sizeof(double) * kMaxSlots) != cudaSuccess ||
       cudaMallocHost((void**)&h->h_ctrl, sizeof(CgCtrl)) != cudaSuccess) {
     pf_mesh_hierarchy_destroy(h);
@@ -357,7 +363,9 @@ pf_status pf_gradient_step(pf_hierarchy* h, int level, const double* x, const do
 pf_status pf_hessvec(pf_hierarchy* h, int level, const void* x, const void* v, void* Hv, int prec) {
   if (!valid_level(h, level) || !x || !v || !Hv) return bad("hessvec: bad argument");
   if (check_prec(prec)) return PF_EINVAL;
-  PF_TRY_CUDA(elem_hessvec(h->geo[level], h->mat[level], x, v, Hv, prec, h->st), "hessvec");
+  PF_TRY_CUDA(elem_hessvec(h->geo[level], h->mat[level], x, v, Hv, prec, h->st, nullptr,
+                           h->etile_part),
+              "hessvec");
   return PF_OK;
 }
 
@@ -387,7 +395,9 @@ pf_status pf_hessvec_lagged(pf_hierarchy* h, int level, const void* v, void* Hv,
                               static_cast<double*>(Hv), h->st),
                 "hessvec_lagged");
   else
-    PF_TRY_CUDA(elem_hessvec(h->geo[level], h->mat[level], B.xlag32, v, Hv, 1, h->st), "hessvec_lagged");
+    PF_TRY_CUDA(elem_hessvec(h->geo[level], h->mat[level], B.xlag32, v, Hv, 1, h->st, nullptr,
+                             h->etile_part),
+                "hessvec_lagged");
   return PF_OK;
 }
 

@@ -44,6 +44,7 @@ struct pf_hierarchy {
   double* c_prev = nullptr; // finest N values
   pf::CgCtrl* ctrl = nullptr;    // device CG control block
   pf::CgCtrl* h_ctrl = nullptr;  // pinned host mirror
+  void* etile_part = nullptr;  // node sums of the element-owned FP32 Hessian tiles (3D)
   // executable graphs of the FP32 CG loop per level (built by the solver)
   struct CgGraph {
     cudaGraph_t graph = nullptr;

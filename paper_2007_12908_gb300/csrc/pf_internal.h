@@ -87,8 +87,15 @@ cudaError_t elem_gradient_df(const Geom& g, const Mat<double>& m, const double* 
                              double* scratch, cudaStream_t st);
 cudaError_t elem_energy_df(const Geom& g, const Mat<double>& m, const double* x, double* scratch,
                            const Scratch& s, double* out_dev, cudaStream_t st);
+// part: optional scratch of etile_part_count(g) float4; with it, 3D FP32
+// products on grids of at least two 8^3 tiles per SM evaluate every element
+// once (element-owned tiles, then a gather of the tiles' node sums).
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
-                         void* y, int prec, cudaStream_t st, const int* skip = nullptr);
+                         void* y, int prec, cudaStream_t st, const int* skip = nullptr,
+                         void* part = nullptr);
+long long etile_part_count(const Geom& g);
+// kernel launches of one 3D FP32 product (1, or 2 on the element-owned path)
+int hessvec32_launches(const Geom& g, const void* part);
 // FP64 lagged Hessian: Gauss-point coefficients of x (coef holds
 // NE * 2^d * (2 + d(d+1)/2) doubles), the input of the stencil assembly.
 cudaError_t elem_hess_coef(const Geom& g, const Mat<double>& m, const double* x, double* coef,
@@ -114,7 +121,7 @@ cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, in
 // (the mixed-precision solver's operator; conversions happen in registers).
 cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float* x32,
                                const double* v, double* y, cudaStream_t st,
-                               const int* skip = nullptr);
+                               const int* skip = nullptr, void* part = nullptr);
 
 // Fracture band rasterisation into the c plane (FP64) of x and c_prev.
 // rows: device array of precomputed shape rows (see pf_kernels.cu).

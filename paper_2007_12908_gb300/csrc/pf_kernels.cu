@@ -444,12 +444,139 @@ cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, vo
               : launch_scatter<2, double, double, OP_GRAD>(g, m, x, nullptr, y, nullptr, st);
 }
 
+// Element-owned 3D FP32 Hessian product, pass 1: a CTA owns 8^3 elements
+// and evaluates each once (no halo re-evaluation).  It stages their 9^3
+// corner nodes of x_lag and v, sums the corner contributions into those
+// nodes in the colour phases of k_hess_tile3, and writes the 9^3 node sums
+// to part (one block of 729 float4 per tile).
+template <class TV>
+__global__ void __launch_bounds__(256, 2)
+    k_hess_etile3(Geom g, Mat<float> m, const float* __restrict__ x, const TV* __restrict__ v,
+                  float4* __restrict__ part, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN, NT = 256;
+  __shared__ float4 xs[NH], vs[NH], acc[NH];
+  const int ox = blockIdx.x * T, oy = blockIdx.y * T, oz = blockIdx.z * T;
+  const int nx0 = g.n[0], ny0 = g.n[1], nz0 = g.n[2];
+  const long long N = g.N;
+  for (int j = threadIdx.x; j < NH; j += NT) {
+    const int i = j % NN, jj = (j / NN) % NN, k = j / (NN * NN);
+    const int gx = ox + i, gy = oy + jj, gz = oz + k;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    if (gx < nx0 && gy < ny0 && gz < nz0) {
+      const long long idx = gx + (long long)nx0 * (gy + (long long)ny0 * gz);
+      a = make_float4(x[idx], x[N + idx], x[2 * N + idx], x[3 * N + idx]);
+      b = make_float4(float(v[idx]), float(v[N + idx]), float(v[2 * N + idx]), float(v[3 * N + idx]));
+    }
+    xs[j] = a;
+    vs[j] = b;
+    acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int base = 0; base < T * T * T; base += NT) {
+    const int e = base + threadIdx.x;
+    const int lx = e % T, ly = (e / T) % T, lz = e / (T * T);
+    const bool valid = ox + lx < g.ne[0] && oy + ly < g.ne[1] && oz + lz < g.ne[2];
+    const int c0 = lx + NN * (ly + NN * lz);
+    float out[4][8];
+    if (valid) {
+      float xe[4][8], ve[4][8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int c = c0 + (a & 1) + NN * ((a >> 1) & 1) + NN * NN * ((a >> 2) & 1);
+        const float4 xa = xs[c], va = vs[c];
+        xe[0][a] = xa.x; xe[1][a] = xa.y; xe[2][a] = xa.z; xe[3][a] = xa.w;
+        ve[0][a] = va.x; ve[1][a] = va.y; ve[2][a] = va.z; ve[3][a] = va.w;
+      }
+      p2::elem_hessvec(xe, ve, m, out);
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      if (valid) {
+        const int c = c0 + (a & 1) + NN * ((a >> 1) & 1) + NN * NN * ((a >> 2) & 1);
+        float4 t = acc[c];
+        t.x += out[0][a];
+        t.y += out[1][a];
+        t.z += out[2][a];
+        t.w += out[3][a];
+        acc[c] = t;
+      }
+      __syncthreads();
+    }
+  }
+  const long long tile = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+  float4* o = part + tile * NH;
+  for (int j = threadIdx.x; j < NH; j += NT) o[j] = acc[j];
+}
+
+// Pass 2: each node sums the blocks of the up to 8 tiles that contain it,
+// in ascending tile order (z, y, x), and writes y.
+template <class TV>
+__global__ void __launch_bounds__(256) k_etile_gather3(Geom g, const float4* __restrict__ part,
+                                                       TV* __restrict__ y,
+                                                       const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN;
+  const int tx = (g.ne[0] + T - 1) / T, ty = (g.ne[1] + T - 1) / T, tz = (g.ne[2] + T - 1) / T;
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int i = int(n % g.n[0]);
+    const long long r = n / g.n[0];
+    const int j = int(r % g.n[1]), k = int(r / g.n[1]);
+    // tiles t with 8t <= coordinate <= 8t + 8
+    const int x0 = i >= T ? (i - 1) / T : 0, x1 = min(i / T, tx - 1);
+    const int y0 = j >= T ? (j - 1) / T : 0, y1 = min(j / T, ty - 1);
+    const int z0 = k >= T ? (k - 1) / T : 0, z1 = min(k / T, tz - 1);
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int bz = z0; bz <= z1; ++bz)
+      for (int by = y0; by <= y1; ++by)
+        for (int bx = x0; bx <= x1; ++bx) {
+          const long long tile = bx + (long long)tx * (by + (long long)ty * bz);
+          const int loc = (i - T * bx) + NN * ((j - T * by) + NN * (k - T * bz));
+          const float4 c = part[tile * NH + loc];
+          sum.x += c.x;
+          sum.y += c.y;
+          sum.z += c.z;
+          sum.w += c.w;
+        }
+    y[n] = TV(sum.x);
+    y[N + n] = TV(sum.y);
+    y[2 * N + n] = TV(sum.z);
+    y[3 * N + n] = TV(sum.w);
+  }
+}
+
+long long etile_part_count(const Geom& g) {
+  if (g.dim != 3) return 0;
+  const long long t = (long long)((g.ne[0] + 7) / 8) * ((g.ne[1] + 7) / 8) * ((g.ne[2] + 7) / 8);
+  return t * 729;
+}
+
+static bool etile_eligible(const Geom& g) {
+  const long long b8 = (long long)((g.n[0] + 7) / 8) * ((g.n[1] + 7) / 8) * ((g.n[2] + 7) / 8);
+  return g.dim == 3 && b8 >= 2 * 152;
+}
+
+int hessvec32_launches(const Geom& g, const void* part) {
+  return part && etile_eligible(g) ? 2 : 1;
+}
+
 template <class TV>
 static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const float* x,
-                                     const TV* v, TV* y, const int* skip, cudaStream_t st) {
+                                     const TV* v, TV* y, const int* skip, cudaStream_t st,
+                                     void* part = nullptr) {
   auto tiles = [&g](int t) {
     return dim3((g.n[0] + t - 1) / t, (g.n[1] + t - 1) / t, (g.n[2] + t - 1) / t);
   };
+  if (part && etile_eligible(g)) {
+    const dim3 be((g.ne[0] + 7) / 8, (g.ne[1] + 7) / 8, (g.ne[2] + 7) / 8);
+    float4* pp = static_cast<float4*>(part);
+    k_hess_etile3<TV><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, v, pp, skip);
+    const int nb = int(std::min<long long>((g.N + 255) / 256, 8LL * 1216));
+    k_etile_gather3<TV><<<nb, 256, 0, st>>>(g, pp, y, skip);
+    return cudaGetLastError();
+  }
   const dim3 b8 = tiles(8);
   if ((long long)b8.x * b8.y * b8.z >= 2 * 152)
     k_hess_tile3<TV, 8><<<b8, HessTile<8>::THREADS, 0, st>>>(g, cast_mat<float>(m), x, v, y, skip);
@@ -460,11 +587,11 @@ static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const 
 }
 
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
-                         void* y, int prec, cudaStream_t st, const int* skip) {
+                         void* y, int prec, cudaStream_t st, const int* skip, void* part) {
   if (g.dim == 3)
     return prec ? launch_hess_tile3<float>(g, m, static_cast<const float*>(x),
                                            static_cast<const float*>(v), static_cast<float*>(y),
-                                           skip, st)
+                                           skip, st, part)
                 : launch_scatter<3, double, double, OP_HESS>(g, m, x, v, y, skip, st);
   return prec ? launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st)
               : launch_scatter<2, double, double, OP_HESS>(g, m, x, v, y, skip, st);
@@ -924,8 +1051,9 @@ cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, in
 }
 
 cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float* x32,
-                               const double* v, double* y, cudaStream_t st, const int* skip) {
-  if (g.dim == 3) return launch_hess_tile3<double>(g, m, x32, v, y, skip, st);
+                               const double* v, double* y, cudaStream_t st, const int* skip,
+                               void* part) {
+  if (g.dim == 3) return launch_hess_tile3<double>(g, m, x32, v, y, skip, st, part);
   return launch_scatter<2, float, double, OP_HESS>(g, m, x32, v, y, skip, st);
 }
 

@@ -577,10 +577,11 @@ struct Solver {
     if (!galerkin(l)) {
       LevelBuf& B = H->lv[l];
       if (mixed32(l))
-        ck(elem_hessvec_mixed(H->geo[l], H->mat[l], B.xlag32, v, out, st, skip), "hessvec32");
+        ck(elem_hessvec_mixed(H->geo[l], H->mat[l], B.xlag32, v, out, st, skip, H->etile_part),
+           "hessvec32");
       else
         ck(stencil_apply(H->geo[l], B.stencil, v, out, st, skip), "hessvec");
-      S.launches += 1;
+      S.launches += mixed32(l) ? hessvec32_launches(H->geo[l], H->etile_part) : 1;
       if (count) {
         S.hessvecs += 1;
         S.fe_hessvec += frac(l);
@@ -694,8 +695,9 @@ struct Solver {
     if constexpr (std::is_same<V, double>::value) {
       Hlag(l, v, out, skip, count);
     } else {
-      ck(elem_hessvec(H->geo[l], H->mat[l], H->lv[l].xlag32, v, out, 1, st, skip), "hessvec32");
-      S.launches += 1;
+      ck(elem_hessvec(H->geo[l], H->mat[l], H->lv[l].xlag32, v, out, 1, st, skip, H->etile_part),
+         "hessvec32");
+      S.launches += hessvec32_launches(H->geo[l], H->etile_part);
       if (count) {
         S.hessvecs += 1;
         S.fe_hessvec += frac(l);
@@ -720,7 +722,8 @@ struct Solver {
     LevelBuf& B = H->lv[l];
     CgCtrl* c = H->ctrl;
     const long long n4 = pad4(B.n) / 4;
-    ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done), "hessvec32");
+    ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done, H->etile_part),
+       "hessvec32");
     k_cg_dot4<<<resident_grid(k_cg_dot4, n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials,
                                                             H->scratch.counter);
     ck(cudaGetLastError(), "cg_dot");
@@ -743,7 +746,7 @@ struct Solver {
     const V Z = V(0);
     if constexpr (std::is_same<V, float>::value) {
       cg_iter4(l, p, q, ga, gb, mi, w, r, pc, st);
-      S.launches += 4;
+      S.launches += 3 + hessvec32_launches(H->geo[l], H->etile_part);
       return;
     }
     hv<V>(l, p, q, skip, false);
