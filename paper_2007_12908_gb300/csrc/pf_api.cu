@@ -154,7 +154,8 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
   }
   long long part = 0;
   for (const Geom& g : h->geo) part = std::max(part, etile_part_count(g));
-  if (part > 0 && (rc = alloc(h, &h->etile_part, sizeof(float4) * part))) {
+  if ((part > 0 && (rc = alloc(h, &h->etile_part, sizeof(float4) * part))) ||
+      (rc = alloc(h, (void**)&h->p_dev, sizeof(float)))) {
     pf_mesh_hierarchy_destroy(h);
     return rc;
   }
@@ -165,6 +166,7 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
     return PF_ENOMEM;
   }
   cudaMemsetAsync(h->scratch.counter, 0, sizeof(unsigned), h->st);
+  cudaMemsetAsync(h->p_dev, 0, sizeof(float), h->st);  // the material starts at p = 0
   cudaMemsetAsync(h->c_prev, 0, sizeof(double) * h->geo.back().N, h->st);
   h->lv.resize(h->L);
   for (int l = 0; l < h->L; ++l) {
@@ -273,6 +275,10 @@ pf_status pf_pressure_set(pf_hierarchy* h, double p) {
   }
   h->p = p;
   for (auto& m : h->mat) m.p = p;
+  const float pf = float(p);
+  PF_TRY_CUDA(cudaMemcpyAsync(h->p_dev, &pf, sizeof(float), cudaMemcpyHostToDevice, h->st),
+              "pressure_set");
+  PF_TRY_CUDA(cudaStreamSynchronize(h->st), "pressure_set");
   return PF_OK;
 }
 
@@ -364,7 +370,7 @@ pf_status pf_hessvec(pf_hierarchy* h, int level, const void* x, const void* v, v
   if (!valid_level(h, level) || !x || !v || !Hv) return bad("hessvec: bad argument");
   if (check_prec(prec)) return PF_EINVAL;
   PF_TRY_CUDA(elem_hessvec(h->geo[level], h->mat[level], x, v, Hv, prec, h->st, nullptr,
-                           h->etile_part),
+                           h->etile_part, h->p_dev),
               "hessvec");
   return PF_OK;
 }
@@ -396,7 +402,7 @@ pf_status pf_hessvec_lagged(pf_hierarchy* h, int level, const void* v, void* Hv,
                 "hessvec_lagged");
   else
     PF_TRY_CUDA(elem_hessvec(h->geo[level], h->mat[level], B.xlag32, v, Hv, 1, h->st, nullptr,
-                             h->etile_part),
+                             h->etile_part, h->p_dev),
                 "hessvec_lagged");
   return PF_OK;
 }

@@ -45,6 +45,7 @@ struct pf_hierarchy {
   pf::CgCtrl* ctrl = nullptr;    // device CG control block
   pf::CgCtrl* h_ctrl = nullptr;  // pinned host mirror
   void* etile_part = nullptr;  // node sums of the element-owned FP32 Hessian tiles (3D)
+  float* p_dev = nullptr;      // the pressure in FP32 on the device (kept by pf_pressure_set)
   // executable graphs of the FP32 CG loop per level (built by the solver)
   struct CgGraph {
     cudaGraph_t graph = nullptr;

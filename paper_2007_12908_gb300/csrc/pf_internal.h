@@ -90,9 +90,12 @@ cudaError_t elem_energy_df(const Geom& g, const Mat<double>& m, const double* x,
 // part: optional scratch of etile_part_count(g) float4; with it, 3D FP32
 // products on grids of at least two 8^3 tiles per SM evaluate every element
 // once (element-owned tiles, then a gather of the tiles' node sums).
+// p_dev: optional device copy of the pressure (FP32), read by the 3D FP32
+// products instead of m.p, so that CUDA graphs capturing them stay valid
+// across pressure changes.
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
                          void* y, int prec, cudaStream_t st, const int* skip = nullptr,
-                         void* part = nullptr);
+                         void* part = nullptr, const float* p_dev = nullptr);
 long long etile_part_count(const Geom& g);
 // kernel launches of one 3D FP32 product (1, or 2 on the element-owned path)
 int hessvec32_launches(const Geom& g, const void* part);
@@ -121,7 +124,8 @@ cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, in
 // (the mixed-precision solver's operator; conversions happen in registers).
 cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float* x32,
                                const double* v, double* y, cudaStream_t st,
-                               const int* skip = nullptr, void* part = nullptr);
+                               const int* skip = nullptr, void* part = nullptr,
+                               const float* p_dev = nullptr);
 
 // Fracture band rasterisation into the c plane (FP64) of x and c_prev.
 // rows: device array of precomputed shape rows (see pf_kernels.cu).

@@ -327,11 +327,15 @@ struct HessTile {
 
 // OP: OP_HESS (y = H(x) v, paired FP32 algebra) or OP_GDIFF (y += grad E(x)
 // - grad E(x - v), scalar FP32 algebra); TX: type of x in memory.
+// p_dev: when non-null, the pressure is read from it (a CUDA graph that
+// captured the launch then follows pf_pressure_set).
 template <class TV, int T = 8, int OP = OP_HESS, class TX = float>
 __global__ void __launch_bounds__(HessTile<T>::THREADS, T == 8 ? 2 : 4)
     k_hess_tile3(Geom g, Mat<float> m, const TX* __restrict__ x, const TV* __restrict__ v,
-                 TV* __restrict__ y, const int* __restrict__ skip) {
+                 TV* __restrict__ y, const int* __restrict__ skip,
+                 const float* __restrict__ p_dev = nullptr) {
   if (skip && *skip) return;
+  if (p_dev) m.p = *p_dev;
   constexpr int E = T + 1, NN = T + 2, NH = NN * NN * NN, NT = HessTile<T>::THREADS;
   __shared__ float4 xs[NH], vs[NH];
   __shared__ float4 acc[T * T * T];
@@ -452,8 +456,10 @@ cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, vo
 template <class TV>
 __global__ void __launch_bounds__(256, 2)
     k_hess_etile3(Geom g, Mat<float> m, const float* __restrict__ x, const TV* __restrict__ v,
-                  float4* __restrict__ part, const int* __restrict__ skip) {
+                  float4* __restrict__ part, const int* __restrict__ skip,
+                  const float* __restrict__ p_dev) {
   if (skip && *skip) return;
+  if (p_dev) m.p = *p_dev;
   constexpr int T = 8, NN = T + 1, NH = NN * NN * NN, NT = 256;
   __shared__ float4 xs[NH], vs[NH], acc[NH];
   const int ox = blockIdx.x * T, oy = blockIdx.y * T, oz = blockIdx.z * T;
@@ -565,33 +571,35 @@ int hessvec32_launches(const Geom& g, const void* part) {
 template <class TV>
 static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const float* x,
                                      const TV* v, TV* y, const int* skip, cudaStream_t st,
-                                     void* part = nullptr) {
+                                     void* part = nullptr, const float* p_dev = nullptr) {
   auto tiles = [&g](int t) {
     return dim3((g.n[0] + t - 1) / t, (g.n[1] + t - 1) / t, (g.n[2] + t - 1) / t);
   };
   if (part && etile_eligible(g)) {
     const dim3 be((g.ne[0] + 7) / 8, (g.ne[1] + 7) / 8, (g.ne[2] + 7) / 8);
     float4* pp = static_cast<float4*>(part);
-    k_hess_etile3<TV><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, v, pp, skip);
+    k_hess_etile3<TV><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, v, pp, skip, p_dev);
     const int nb = int(std::min<long long>((g.N + 255) / 256, 8LL * 1216));
     k_etile_gather3<TV><<<nb, 256, 0, st>>>(g, pp, y, skip);
     return cudaGetLastError();
   }
   const dim3 b8 = tiles(8);
   if ((long long)b8.x * b8.y * b8.z >= 2 * 152)
-    k_hess_tile3<TV, 8><<<b8, HessTile<8>::THREADS, 0, st>>>(g, cast_mat<float>(m), x, v, y, skip);
+    k_hess_tile3<TV, 8><<<b8, HessTile<8>::THREADS, 0, st>>>(g, cast_mat<float>(m), x, v, y, skip,
+                                                              p_dev);
   else
     k_hess_tile3<TV, 4><<<tiles(4), HessTile<4>::THREADS, 0, st>>>(g, cast_mat<float>(m), x, v, y,
-                                                                  skip);
+                                                                  skip, p_dev);
   return cudaGetLastError();
 }
 
 cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, const void* v,
-                         void* y, int prec, cudaStream_t st, const int* skip, void* part) {
+                         void* y, int prec, cudaStream_t st, const int* skip, void* part,
+                         const float* p_dev) {
   if (g.dim == 3)
     return prec ? launch_hess_tile3<float>(g, m, static_cast<const float*>(x),
                                            static_cast<const float*>(v), static_cast<float*>(y),
-                                           skip, st, part)
+                                           skip, st, part, p_dev)
                 : launch_scatter<3, double, double, OP_HESS>(g, m, x, v, y, skip, st);
   return prec ? launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st)
               : launch_scatter<2, double, double, OP_HESS>(g, m, x, v, y, skip, st);
@@ -1052,8 +1060,8 @@ cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, in
 
 cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float* x32,
                                const double* v, double* y, cudaStream_t st, const int* skip,
-                               void* part) {
-  if (g.dim == 3) return launch_hess_tile3<double>(g, m, x32, v, y, skip, st, part);
+                               void* part, const float* p_dev) {
+  if (g.dim == 3) return launch_hess_tile3<double>(g, m, x32, v, y, skip, st, part, p_dev);
   return launch_scatter<2, float, double, OP_HESS>(g, m, x32, v, y, skip, st);
 }
 

@@ -577,7 +577,8 @@ struct Solver {
     if (!galerkin(l)) {
       LevelBuf& B = H->lv[l];
       if (mixed32(l))
-        ck(elem_hessvec_mixed(H->geo[l], H->mat[l], B.xlag32, v, out, st, skip, H->etile_part),
+        ck(elem_hessvec_mixed(H->geo[l], H->mat[l], B.xlag32, v, out, st, skip, H->etile_part,
+                              H->p_dev),
            "hessvec32");
       else
         ck(stencil_apply(H->geo[l], B.stencil, v, out, st, skip), "hessvec");
@@ -695,7 +696,8 @@ struct Solver {
     if constexpr (std::is_same<V, double>::value) {
       Hlag(l, v, out, skip, count);
     } else {
-      ck(elem_hessvec(H->geo[l], H->mat[l], H->lv[l].xlag32, v, out, 1, st, skip, H->etile_part),
+      ck(elem_hessvec(H->geo[l], H->mat[l], H->lv[l].xlag32, v, out, 1, st, skip, H->etile_part,
+                      H->p_dev),
          "hessvec32");
       S.launches += hessvec32_launches(H->geo[l], H->etile_part);
       if (count) {
@@ -722,7 +724,8 @@ struct Solver {
     LevelBuf& B = H->lv[l];
     CgCtrl* c = H->ctrl;
     const long long n4 = pad4(B.n) / 4;
-    ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done, H->etile_part),
+    ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done, H->etile_part,
+                    H->p_dev),
        "hessvec32");
     k_cg_dot4<<<resident_grid(k_cg_dot4, n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials,
                                                             H->scratch.counter);
@@ -804,7 +807,10 @@ struct Solver {
     if (!H->cg_graph_ok) return nullptr;
     if ((int)H->cg_graphs.size() < L) H->cg_graphs.resize(L);
     pf_hierarchy::CgGraph& G = H->cg_graphs[l];
-    if (G.exec && G.p == H->p && G.pc == (pc ? 1 : 0) && G.vsize == int(sizeof(V)) &&
+    // 3D products read the pressure from the device; 2D ones take it as an
+    // argument, so a 2D graph is rebuilt when it changes
+    const bool p_ok = H->dim == 3 || G.p == H->p;
+    if (G.exec && p_ok && G.pc == (pc ? 1 : 0) && G.vsize == int(sizeof(V)) &&
         G.precision == P.precision && G.coarse_model == P.coarse_model && G.vp == p)
       return G.exec;
     if (G.exec) cudaGraphExecDestroy(G.exec);
