@@ -43,7 +43,7 @@ METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same G
 # DRAM bytes (read + write) per launch of the roofline kernels on this
 # workload from one ncu capture (profiles/elem_kernels_3d_129cubed_ncu.md);
 # to be re-captured whenever those kernels change.
-TRAFFIC_HESSVEC_FP32 = None  # re-captured below for the element-owned kernels
+TRAFFIC_HESSVEC_FP32 = (69.041e6 + 18.728e6) + (47.788e6 + 1.013e6)  # element pass + gather
 TRAFFIC_HESSVEC_FP64 = 7595.291e6 + 86.475e6
 UNIT = "s/load-step"
 # FP32 flops of one element of the 3D FP32 Hessian product (the paired-FMA
@@ -366,7 +366,7 @@ def run_ours(args):
               "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
               "flop_per_node": 864, "fp64_fma_peak_tflops": fma64 / 1e12,
               "gdofs": ndof / t64 / 1e9, "us_per_launch": t64 * 1e6}
-    # The FP32 product is bound by FP32 issue (FMA pipe ~60 % busy, DRAM ~5 %):
+    # The FP32 product is bound by FP32 issue (FMA pipe ~67 % busy, DRAM ~10 %):
     # ALU roofline, algorithmic flops = FLOP32_PER_ELEMENT x elements
     ne = (g_n[0] - 1) * (g_n[1] - 1) * (g_n[2] - 1)
     flops32 = FLOP32_PER_ELEMENT * ne
@@ -374,7 +374,7 @@ def run_ours(args):
               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
               "frac": flops32 / t32 / 1e12 / FP32_PEAK_TFLOPS,
               # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
-              # this kernel (profiles/elem_kernels_3d_129cubed_ncu.md), per launch
+              # the product's two kernels (profiles/elem_kernels_3d_129cubed_ncu.md)
               "traffic": TRAFFIC_HESSVEC_FP32,
               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
               "fp32_fma_probe_tflops": fma32 / 1e12,
