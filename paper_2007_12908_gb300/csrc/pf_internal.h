@@ -43,6 +43,20 @@ struct CgCtrl {
 };
 enum { CG_RUNNING = 0, CG_NEGCURV = 1, CG_LEAVE = 2, CG_CONV = 3, CG_BUDGET = 4 };
 
+// The curvature step of a CG iteration from kappa = p.Hp: counts the
+// product, then alpha = r.M^-1 r / kappa, or a stop on non-positive
+// curvature.  Run by the last block of the p.Hp reduction.
+__device__ __forceinline__ void cg_take_curvature(CgCtrl* c, double kappa) {
+  c->kappa = kappa;
+  c->used += 1;
+  if (kappa <= 0.0) {
+    c->done = 1;
+    c->state = CG_NEGCURV;
+  } else {
+    c->alpha = c->rz / kappa;
+  }
+}
+
 Geom make_geom(int dim, const int n[3], double h);
 Mat<double> make_mat(const Geom& g, double E, double nu, double Gc, double ls, double k,
                      double p);
@@ -99,6 +113,16 @@ cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, con
 long long etile_part_count(const Geom& g);
 // kernel launches of one 3D FP32 product (1, or 2 on the element-owned path)
 int hessvec32_launches(const Geom& g, const void* part);
+// The FP32 CG product q = H p with p.q taken in the same launches: on the
+// element-owned path the gather pass reduces p.q and its last block runs
+// cg_take_curvature on c.  Returns cudaErrorNotSupported, launching
+// nothing, where that path does not apply (the caller then takes p.q in a
+// pass of its own).  partials needs kMaxBlocks doubles.
+cudaError_t elem_hessvec32_dot(const Geom& g, const Mat<double>& m, const float* x,
+                               const float* p, float* q, CgCtrl* c, double* partials,
+                               unsigned* counter, void* part, const float* p_dev,
+                               cudaStream_t st);
+bool hessvec32_dot_fused(const Geom& g, const void* part);
 // FP64 lagged Hessian: Gauss-point coefficients of x (coef holds
 // NE * 2^d * (2 + d(d+1)/2) doubles), the input of the stencil assembly.
 cudaError_t elem_hess_coef(const Geom& g, const Mat<double>& m, const double* x, double* coef,

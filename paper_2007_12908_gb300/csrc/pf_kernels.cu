@@ -515,42 +515,101 @@ __global__ void __launch_bounds__(256, 2)
   for (int j = threadIdx.x; j < NH; j += NT) o[j] = acc[j];
 }
 
-// Pass 2: each node sums the blocks of the up to 8 tiles that contain it,
-// in ascending tile order (z, y, x), and writes y.
+// Sum at node n of the blocks of the up to 8 element tiles that contain
+// it, in ascending tile order (z, y, x).  Along each axis a node lies in
+// one tile, or in two where it sits on a tile boundary; all candidate loads
+// are issued before the first add (absent tiles add an exact zero), so a
+// node costs one memory latency, not one per tile.
+__device__ __forceinline__ float4 etile_node_sum(const Geom& g, const float4* __restrict__ part,
+                                                 long long n, int tx, int ty, int tz) {
+  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN;
+  int i, j, k;
+  if (g.N <= 0xffffffffLL) {  // 32-bit index arithmetic where it suffices
+    unsigned u = unsigned(n);
+    i = int(u % unsigned(g.n[0]));
+    u /= unsigned(g.n[0]);
+    j = int(u % unsigned(g.n[1]));
+    k = int(u / unsigned(g.n[1]));
+  } else {
+    i = int(n % g.n[0]);
+    const long long r = n / g.n[0];
+    j = int(r % g.n[1]);
+    k = int(r / g.n[1]);
+  }
+  // tiles t with 8t <= coordinate <= 8t + 8: t0, and t0 + 1 if present
+  const int x0 = i >= T ? (i - 1) / T : 0, y0 = j >= T ? (j - 1) / T : 0;
+  const int z0 = k >= T ? (k - 1) / T : 0;
+  const bool hx = min(i / T, tx - 1) > x0, hy = min(j / T, ty - 1) > y0;
+  const bool hz = min(k / T, tz - 1) > z0;
+  float4 c[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
+    const bool ok = (!dx || hx) && (!dy || hy) && (!dz || hz);
+    const int bx = x0 + dx, by = y0 + dy, bz = z0 + dz;
+    const long long tile = bx + (long long)tx * (by + (long long)ty * bz);
+    const int loc = (i - T * bx) + NN * ((j - T * by) + NN * (k - T * bz));
+    c[q] = ok ? part[tile * NH + loc] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float4 sum = c[0];
+#pragma unroll
+  for (int q = 1; q < 8; ++q) {
+    sum.x += c[q].x;
+    sum.y += c[q].y;
+    sum.z += c[q].z;
+    sum.w += c[q].w;
+  }
+  return sum;
+}
+
+// Pass 2: each node sums the blocks of the tiles that contain it and
+// writes y.
 template <class TV>
 __global__ void __launch_bounds__(256) k_etile_gather3(Geom g, const float4* __restrict__ part,
                                                        TV* __restrict__ y,
                                                        const int* __restrict__ skip) {
   if (skip && *skip) return;
-  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN;
+  constexpr int T = 8;
   const int tx = (g.ne[0] + T - 1) / T, ty = (g.ne[1] + T - 1) / T, tz = (g.ne[2] + T - 1) / T;
   const long long N = g.N;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const int i = int(n % g.n[0]);
-    const long long r = n / g.n[0];
-    const int j = int(r % g.n[1]), k = int(r / g.n[1]);
-    // tiles t with 8t <= coordinate <= 8t + 8
-    const int x0 = i >= T ? (i - 1) / T : 0, x1 = min(i / T, tx - 1);
-    const int y0 = j >= T ? (j - 1) / T : 0, y1 = min(j / T, ty - 1);
-    const int z0 = k >= T ? (k - 1) / T : 0, z1 = min(k / T, tz - 1);
-    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int bz = z0; bz <= z1; ++bz)
-      for (int by = y0; by <= y1; ++by)
-        for (int bx = x0; bx <= x1; ++bx) {
-          const long long tile = bx + (long long)tx * (by + (long long)ty * bz);
-          const int loc = (i - T * bx) + NN * ((j - T * by) + NN * (k - T * bz));
-          const float4 c = part[tile * NH + loc];
-          sum.x += c.x;
-          sum.y += c.y;
-          sum.z += c.z;
-          sum.w += c.w;
-        }
+    const float4 sum = etile_node_sum(g, part, n, tx, ty, tz);
     y[n] = TV(sum.x);
     y[N + n] = TV(sum.y);
     y[2 * N + n] = TV(sum.z);
     y[3 * N + n] = TV(sum.w);
   }
+}
+
+// Pass 2 with p.q: as k_etile_gather3 for FP32 y = q, and each thread adds
+// p.q over its nodes; the blocks' partials are combined in block order and
+// the last block takes the CG curvature step.  Launched on at most
+// kMaxBlocks blocks (one completion ticket per block).
+__global__ void __launch_bounds__(256, 4) k_etile_gather3_dot(Geom g,
+                                                              const float4* __restrict__ part,
+                                                              const float* __restrict__ p,
+                                                              float* __restrict__ y, CgCtrl* c,
+                                                              double* partials,
+                                                              unsigned* counter) {
+  if (c->done) return;
+  constexpr int T = 8;
+  const int tx = (g.ne[0] + T - 1) / T, ty = (g.ne[1] + T - 1) / T, tz = (g.ne[2] + T - 1) / T;
+  const long long N = g.N;
+  float pq = 0.f;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const float p0 = p[n], p1 = p[N + n], p2 = p[2 * N + n], p3 = p[3 * N + n];
+    const float4 sum = etile_node_sum(g, part, n, tx, ty, tz);
+    y[n] = sum.x;
+    y[N + n] = sum.y;
+    y[2 * N + n] = sum.z;
+    y[3 * N + n] = sum.w;
+    pq += p0 * sum.x + p1 * sum.y + p2 * sum.z + p3 * sum.w;
+  }
+  double acc[1] = {double(pq)};
+  auto fin = [c](double(&a)[1]) { cg_take_curvature(c, a[0]); };
+  grid_finish_fn<1, OpSum>(acc, partials, counter, fin);
 }
 
 long long etile_part_count(const Geom& g) {
@@ -566,6 +625,24 @@ static bool etile_eligible(const Geom& g) {
 
 int hessvec32_launches(const Geom& g, const void* part) {
   return part && etile_eligible(g) ? 2 : 1;
+}
+
+bool hessvec32_dot_fused(const Geom& g, const void* part) {
+  return part && etile_eligible(g) && g.dim == 3;
+}
+
+cudaError_t elem_hessvec32_dot(const Geom& g, const Mat<double>& m, const float* x,
+                               const float* p, float* q, CgCtrl* c, double* partials,
+                               unsigned* counter, void* part, const float* p_dev,
+                               cudaStream_t st) {
+  if (!hessvec32_dot_fused(g, part)) return cudaErrorNotSupported;
+  const dim3 be((g.ne[0] + 7) / 8, (g.ne[1] + 7) / 8, (g.ne[2] + 7) / 8);
+  float4* pp = static_cast<float4*>(part);
+  k_hess_etile3<float><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, p, pp, &c->done, p_dev);
+  // kMaxBlocks = two waves of 4 blocks per SM
+  const int nb = int(std::min<long long>((g.N + 255) / 256, kMaxBlocks));
+  k_etile_gather3_dot<<<nb, 256, 0, st>>>(g, pp, p, q, c, partials, counter);
+  return cudaGetLastError();
 }
 
 template <class TV>

@@ -291,16 +291,7 @@ __global__ void __launch_bounds__(256) k_cg_dot4(long long n4, const float* __re
     pq += p1.x * q1.x + p1.y * q1.y + p1.z * q1.z + p1.w * q1.w;
   }
   double acc[1] = {double(pq)};
-  auto fin = [c](double(&a)[1]) {
-    c->kappa = a[0];
-    c->used += 1;
-    if (a[0] <= 0.0) {
-      c->done = 1;
-      c->state = CG_NEGCURV;
-    } else {
-      c->alpha = c->rz / a[0];
-    }
-  };
+  auto fin = [c](double(&a)[1]) { cg_take_curvature(c, a[0]); };
   grid_finish_fn<1, OpSum>(acc, partials, counter, fin);
 }
 
@@ -717,25 +708,37 @@ struct Solver {
   };
 
   // One projected-CG iteration on FP32 vectors with float4 passes (n a
-  // multiple of 4) on stream s: q = H p, p.q and alpha, the update with its
-  // tests and beta, the direction.  No-ops once the control block is done.
-  void cg_iter4(int l, const float* p, float* q, const float* ga, const float* gb,
-                const float* mi, float* w, float* r, bool pc, cudaStream_t s) {
+  // multiple of 4) on stream s: q = H p, p.q and alpha (in the product's
+  // gather pass where it has one), the update with its tests and beta, the
+  // direction.  No-ops once the control block is done.  Returns the
+  // launches.
+  int cg_iter4(int l, const float* p, float* q, const float* ga, const float* gb,
+               const float* mi, float* w, float* r, bool pc, cudaStream_t s) {
     LevelBuf& B = H->lv[l];
     CgCtrl* c = H->ctrl;
     const long long n4 = pad4(B.n) / 4;
-    ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done, H->etile_part,
-                    H->p_dev),
-       "hessvec32");
-    k_cg_dot4<<<resident_grid(k_cg_dot4, n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials,
-                                                            H->scratch.counter);
-    ck(cudaGetLastError(), "cg_dot");
+    int launches = 2;
+    if (hessvec32_dot_fused(H->geo[l], H->etile_part)) {
+      ck(elem_hessvec32_dot(H->geo[l], H->mat[l], B.xlag32, p, q, c, H->scratch.partials,
+                            H->scratch.counter, H->etile_part, H->p_dev, s),
+         "hessvec32_dot");
+      launches += 2;
+    } else {
+      ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done, H->etile_part,
+                      H->p_dev),
+         "hessvec32");
+      k_cg_dot4<<<resident_grid(k_cg_dot4, n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials,
+                                                              H->scratch.counter);
+      ck(cudaGetLastError(), "cg_dot");
+      launches += 1 + hessvec32_launches(H->geo[l], H->etile_part);
+    }
     k_cg_update4<<<resident_grid(k_cg_update4, n4), 256, 0, s>>>(
         n4, ga, gb, q, p, mi, pc, w, r, c, H->scratch.partials, H->scratch.counter);
     ck(cudaGetLastError(), "cg_update");
     k_cg_dir4<<<resident_grid(k_cg_dir4, n4), 256, 0, s>>>(n4, ga, r, mi, pc, const_cast<float*>(p),
                                                             c);
     ck(cudaGetLastError(), "cg_dir");
+    return launches;
   }
 
   // One projected-CG iteration on level l on the solver's stream: q = H p,
@@ -748,22 +751,12 @@ struct Solver {
     const int* skip = &H->ctrl->done;
     const V Z = V(0);
     if constexpr (std::is_same<V, float>::value) {
-      cg_iter4(l, p, q, ga, gb, mi, w, r, pc, st);
-      S.launches += 3 + hessvec32_launches(H->geo[l], H->etile_part);
+      S.launches += cg_iter4(l, p, q, ga, gb, mi, w, r, pc, st);
       return;
     }
     hv<V>(l, p, q, skip, false);
     red_fin<1, OpSum, V>(n, [=] __device__(long long i, V(&o)[1]) { o[0] = p[i] * q[i]; },
-                         [=] __device__(double(&a)[1]) {
-      c->kappa = a[0];
-      c->used += 1;
-      if (a[0] <= 0.0) {
-        c->done = 1;
-        c->state = CG_NEGCURV;
-      } else {
-        c->alpha = c->rz / a[0];
-      }
-    }, skip);
+                         [=] __device__(double(&a)[1]) { cg_take_curvature(c, a[0]); }, skip);
     red_fin<3, OpSum, V>(n, [=] __device__(long long i, V(&o)[3]) {
       const V al = V(c->alpha);
       const V a = ga[i];
