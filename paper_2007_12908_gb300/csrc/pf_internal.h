@@ -43,6 +43,21 @@ struct CgCtrl {
 };
 enum { CG_RUNNING = 0, CG_NEGCURV = 1, CG_LEAVE = 2, CG_CONV = 3, CG_BUDGET = 4 };
 
+// The CG direction of one dof, M^-1 r + beta p (mi = 1 without a
+// preconditioner), rounded the same way wherever it is formed.
+__device__ __forceinline__ float cg_direction(float mi, float r, float beta, float p) {
+  return __fmaf_rn(beta, p, __fmul_rn(mi, r));
+}
+
+// Inputs of the direction update fused into the FP32 CG product: the
+// product's operand becomes p = M^-1 r + beta p (beta from the control
+// block), formed where the operand is read and stored back by the gather
+// pass.  mi null: no preconditioner.
+struct CgDirIn {
+  const float* r;
+  const float* mi;
+};
+
 // The curvature step of a CG iteration from kappa = p.Hp: counts the
 // product, then alpha = r.M^-1 r / kappa, or a stop on non-positive
 // curvature.  Run by the last block of the p.Hp reduction.
@@ -118,10 +133,12 @@ int hessvec32_launches(const Geom& g, const void* part);
 // cg_take_curvature on c.  Returns cudaErrorNotSupported, launching
 // nothing, where that path does not apply (the caller then takes p.q in a
 // pass of its own).  partials needs kMaxBlocks doubles.
-cudaError_t elem_hessvec32_dot(const Geom& g, const Mat<double>& m, const float* x,
-                               const float* p, float* q, CgCtrl* c, double* partials,
-                               unsigned* counter, void* part, const float* p_dev,
-                               cudaStream_t st);
+// With dir.r set, p is first replaced by M^-1 r + beta p (beta =
+// c->beta), the direction update of the previous iteration; the product and
+// p.q use the new p.
+cudaError_t elem_hessvec32_dot(const Geom& g, const Mat<double>& m, const float* x, float* p,
+                               float* q, CgCtrl* c, double* partials, unsigned* counter,
+                               void* part, const float* p_dev, CgDirIn dir, cudaStream_t st);
 bool hessvec32_dot_fused(const Geom& g, const void* part);
 // FP64 lagged Hessian: Gauss-point coefficients of x (coef holds
 // NE * 2^d * (2 + d(d+1)/2) doubles), the input of the stencil assembly.

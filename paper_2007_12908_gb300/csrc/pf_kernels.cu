@@ -453,13 +453,16 @@ cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, vo
 // corner nodes of x_lag and v, sums the corner contributions into those
 // nodes in the colour phases of k_hess_tile3, and writes the 9^3 node sums
 // to part (one block of 729 float4 per tile).
+// With dir.r set (FP32 CG), v is the previous direction and the staged
+// operand is M^-1 r + beta v, beta = *beta.
 template <class TV>
 __global__ void __launch_bounds__(256, 2)
     k_hess_etile3(Geom g, Mat<float> m, const float* __restrict__ x, const TV* __restrict__ v,
                   float4* __restrict__ part, const int* __restrict__ skip,
-                  const float* __restrict__ p_dev) {
+                  const float* __restrict__ p_dev, CgDirIn dir, const double* beta) {
   if (skip && *skip) return;
   if (p_dev) m.p = *p_dev;
+  const float be = dir.r ? float(*beta) : 0.f;
   constexpr int T = 8, NN = T + 1, NH = NN * NN * NN, NT = 256;
   __shared__ float4 xs[NH], vs[NH], acc[NH];
   const int ox = blockIdx.x * T, oy = blockIdx.y * T, oz = blockIdx.z * T;
@@ -473,6 +476,16 @@ __global__ void __launch_bounds__(256, 2)
       const long long idx = gx + (long long)nx0 * (gy + (long long)ny0 * gz);
       a = make_float4(x[idx], x[N + idx], x[2 * N + idx], x[3 * N + idx]);
       b = make_float4(float(v[idx]), float(v[N + idx]), float(v[2 * N + idx]), float(v[3 * N + idx]));
+      if (dir.r) {
+        const float* r = dir.r;
+        const float4 m4 = dir.mi ? make_float4(dir.mi[idx], dir.mi[N + idx], dir.mi[2 * N + idx],
+                                               dir.mi[3 * N + idx])
+                                 : make_float4(1.f, 1.f, 1.f, 1.f);
+        b = make_float4(cg_direction(m4.x, r[idx], be, b.x),
+                        cg_direction(m4.y, r[N + idx], be, b.y),
+                        cg_direction(m4.z, r[2 * N + idx], be, b.z),
+                        cg_direction(m4.w, r[3 * N + idx], be, b.w));
+      }
     }
     xs[j] = a;
     vs[j] = b;
@@ -586,20 +599,37 @@ __global__ void __launch_bounds__(256) k_etile_gather3(Geom g, const float4* __r
 // p.q over its nodes; the blocks' partials are combined in block order and
 // the last block takes the CG curvature step.  Launched on at most
 // kMaxBlocks blocks (one completion ticket per block).
+// With dir.r set, p is first replaced by M^-1 r + beta p (the operand the
+// element pass formed) and stored back.
 __global__ void __launch_bounds__(256, 4) k_etile_gather3_dot(Geom g,
                                                               const float4* __restrict__ part,
-                                                              const float* __restrict__ p,
+                                                              float* __restrict__ p,
                                                               float* __restrict__ y, CgCtrl* c,
                                                               double* partials,
-                                                              unsigned* counter) {
+                                                              unsigned* counter, CgDirIn dir) {
   if (c->done) return;
   constexpr int T = 8;
   const int tx = (g.ne[0] + T - 1) / T, ty = (g.ne[1] + T - 1) / T, tz = (g.ne[2] + T - 1) / T;
   const long long N = g.N;
+  const float be = dir.r ? float(c->beta) : 0.f;
   float pq = 0.f;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
-    const float p0 = p[n], p1 = p[N + n], p2 = p[2 * N + n], p3 = p[3 * N + n];
+    float p0 = p[n], p1 = p[N + n], p2 = p[2 * N + n], p3 = p[3 * N + n];
+    if (dir.r) {
+      const float* r = dir.r;
+      const float4 m4 = dir.mi ? make_float4(dir.mi[n], dir.mi[N + n], dir.mi[2 * N + n],
+                                             dir.mi[3 * N + n])
+                               : make_float4(1.f, 1.f, 1.f, 1.f);
+      p0 = cg_direction(m4.x, r[n], be, p0);
+      p1 = cg_direction(m4.y, r[N + n], be, p1);
+      p2 = cg_direction(m4.z, r[2 * N + n], be, p2);
+      p3 = cg_direction(m4.w, r[3 * N + n], be, p3);
+      p[n] = p0;
+      p[N + n] = p1;
+      p[2 * N + n] = p2;
+      p[3 * N + n] = p3;
+    }
     const float4 sum = etile_node_sum(g, part, n, tx, ty, tz);
     y[n] = sum.x;
     y[N + n] = sum.y;
@@ -631,17 +661,17 @@ bool hessvec32_dot_fused(const Geom& g, const void* part) {
   return part && etile_eligible(g) && g.dim == 3;
 }
 
-cudaError_t elem_hessvec32_dot(const Geom& g, const Mat<double>& m, const float* x,
-                               const float* p, float* q, CgCtrl* c, double* partials,
-                               unsigned* counter, void* part, const float* p_dev,
-                               cudaStream_t st) {
+cudaError_t elem_hessvec32_dot(const Geom& g, const Mat<double>& m, const float* x, float* p,
+                               float* q, CgCtrl* c, double* partials, unsigned* counter,
+                               void* part, const float* p_dev, CgDirIn dir, cudaStream_t st) {
   if (!hessvec32_dot_fused(g, part)) return cudaErrorNotSupported;
   const dim3 be((g.ne[0] + 7) / 8, (g.ne[1] + 7) / 8, (g.ne[2] + 7) / 8);
   float4* pp = static_cast<float4*>(part);
-  k_hess_etile3<float><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, p, pp, &c->done, p_dev);
+  k_hess_etile3<float><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, p, pp, &c->done, p_dev, dir,
+                                           &c->beta);
   // kMaxBlocks = two waves of 4 blocks per SM
   const int nb = int(std::min<long long>((g.N + 255) / 256, kMaxBlocks));
-  k_etile_gather3_dot<<<nb, 256, 0, st>>>(g, pp, p, q, c, partials, counter);
+  k_etile_gather3_dot<<<nb, 256, 0, st>>>(g, pp, p, q, c, partials, counter, dir);
   return cudaGetLastError();
 }
 
@@ -655,7 +685,8 @@ static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const 
   if (part && etile_eligible(g)) {
     const dim3 be((g.ne[0] + 7) / 8, (g.ne[1] + 7) / 8, (g.ne[2] + 7) / 8);
     float4* pp = static_cast<float4*>(part);
-    k_hess_etile3<TV><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, v, pp, skip, p_dev);
+    k_hess_etile3<TV><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, v, pp, skip, p_dev,
+                                          CgDirIn{nullptr, nullptr}, nullptr);
     const int nb = int(std::min<long long>((g.N + 255) / 256, 8LL * 1216));
     k_etile_gather3<TV><<<nb, 256, 0, st>>>(g, pp, y, skip);
     return cudaGetLastError();

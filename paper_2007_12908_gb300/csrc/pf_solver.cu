@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(256) k_cg_dir4(long long n4, const float* __re
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const float4 m4 = mm[k], r4 = rv[k], p4 = pp[k];
-      pp[k] = make_float4(m4.x * r4.x + be * p4.x, m4.y * r4.y + be * p4.y,
-                          m4.z * r4.z + be * p4.z, m4.w * r4.w + be * p4.w);
+      pp[k] = make_float4(cg_direction(m4.x, r4.x, be, p4.x), cg_direction(m4.y, r4.y, be, p4.y),
+                          cg_direction(m4.z, r4.z, be, p4.z), cg_direction(m4.w, r4.w, be, p4.w));
     }
     if (f0) st4(p, j0, pp[0]);
     if (f1) st4(p, j1, pp[1]);
@@ -717,13 +717,20 @@ struct Solver {
     LevelBuf& B = H->lv[l];
     CgCtrl* c = H->ctrl;
     const long long n4 = pad4(B.n) / 4;
-    int launches = 2;
     if (hessvec32_dot_fused(H->geo[l], H->etile_part)) {
-      ck(elem_hessvec32_dot(H->geo[l], H->mat[l], B.xlag32, p, q, c, H->scratch.partials,
-                            H->scratch.counter, H->etile_part, H->p_dev, s),
+      // the direction update of the previous iteration (beta = 0 after a
+      // restart, where p = M^-1 r already) is formed inside the product
+      ck(elem_hessvec32_dot(H->geo[l], H->mat[l], B.xlag32, const_cast<float*>(p), q, c,
+                            H->scratch.partials, H->scratch.counter, H->etile_part, H->p_dev,
+                            CgDirIn{r, pc ? mi : nullptr}, s),
          "hessvec32_dot");
-      launches += 2;
-    } else {
+      k_cg_update4<<<resident_grid(k_cg_update4, n4), 256, 0, s>>>(
+          n4, ga, gb, q, p, mi, pc, w, r, c, H->scratch.partials, H->scratch.counter);
+      ck(cudaGetLastError(), "cg_update");
+      return 3;
+    }
+    int launches = 2;
+    {
       ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done, H->etile_part,
                       H->p_dev),
          "hessvec32");
