@@ -43,7 +43,7 @@ METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same G
 # DRAM bytes (read + write) per launch of the roofline kernels on this
 # workload from one ncu capture (profiles/elem_kernels_3d_129cubed_ncu.md);
 # to be re-captured whenever those kernels change.
-TRAFFIC_HESSVEC_FP32 = (69.041e6 + 18.728e6) + (47.788e6 + 1.013e6)  # element pass + gather
+TRAFFIC_HESSVEC_FP32 = (68.733e6 + 16.743e6) + (47.790e6 + 1.079e6)  # element pass + gather
 TRAFFIC_HESSVEC_FP64 = 7595.291e6 + 86.475e6
 UNIT = "s/load-step"
 # FP32 flops of one element of the 3D FP32 Hessian product (the paired-FMA

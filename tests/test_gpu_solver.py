@@ -193,6 +193,37 @@ def test_3d_workload_load_step_properties(pf):
     assert abs(O.energy(g, Ho.prm, xg) - st["energy"]) <= ENERGY_TOL * abs(st["energy"])
 
 
+def test_mixed_load_step_element_owned_cg(pf):
+    """A mixed-precision load step on a 65^3 three-level hierarchy with 20
+    discs (p = 5e-4).  Its finest level has 9^3 element tiles of 8^3, so the
+    FP32 CG there runs three launches per iteration: the element-owned
+    Hessian with the direction update formed in its operand, the gather with
+    p.Hp and alpha, and the update.  The step converges inside the box, to the
+    FP64 solver's energy, and the oracle's projected gradient at the result is
+    below the stopping tolerance."""
+    import torch
+    H, Ho = pair(3, (17, 17, 17), 3, 1 / 16, nu=0.25, p=5e-4)
+    g = Ho.fine
+    assert g.n == (65, 65, 65)
+    rows = PI.disc_network_3d(PI.SEED_3D_PLAIN, 20)
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    pf.fractures_set(H, pf.PF_DISC3D, rows, g.h, x)
+    x64 = x.clone()
+    c0 = host(x)[3 * g.N:].copy()
+    s64 = pf.rmtr_load_step(H, x64, pf.default_params())
+    s32 = pf.rmtr_load_step(H, x, pf.default_params(precision=pf.PF_FP32))
+    assert s64["converged"] == 1 and s32["converged"] == 1
+    assert abs(s32["energy"] - s64["energy"]) <= 1e-8 * abs(s64["energy"])
+    xg = host(x)
+    c = xg[3 * g.N:]
+    assert np.all(c >= c0) and np.all(c <= 1.0)
+    Ho.c_prev = c0
+    lb, ub = Ho.fine_bounds()
+    pg = O.projected_gradient_norm(xg, O.gradient(g, Ho.prm, xg), lb, ub)
+    assert pg <= 1e-9 * s32["pg0"]
+    assert abs(O.energy(g, Ho.prm, xg) - s32["energy"]) <= ENERGY_TOL * abs(s32["energy"])
+
+
 def test_mixed_precision_reaches_fp64_energy(pf):
     H, Ho, x, _ = _sneddon_setup(pf, O.FIRST_ORDER)
     x2 = x.clone()
