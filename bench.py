@@ -40,16 +40,16 @@ WORKLOAD = {
 }
 METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same GB300"
 
-# DRAM bytes (read + write) per launch of the roofline kernels on this
-# workload from one ncu capture (profiles/elem_kernels_3d_129cubed_ncu.md);
-# to be re-captured whenever those kernels change.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# roofline kernels on this workload, from one ncu capture of
+# `bench.py --kernels-only`; to be re-captured whenever those kernels change.
 TRAFFIC_HESSVEC_FP32 = (68.733e6 + 16.743e6) + (47.790e6 + 1.079e6)  # element pass + gather
 TRAFFIC_HESSVEC_FP64 = 7595.291e6 + 86.475e6
 UNIT = "s/load-step"
 # FP32 flops of one element of the 3D FP32 Hessian product (the paired-FMA
 # element algebra and its corner sums), from the FP32 instruction counts of
-# one ncu capture (FFMA2 x4, FFMA x2, FADD2/FMUL2 x2, FADD/FMUL x1) divided by
-# the element evaluations of the launch (profiles/elem_kernels_3d_129cubed_ncu.md).
+# one ncu capture (FFMA2 x4, FFMA x2, FADD2/FMUL2 x2, FADD/FMUL x1): 6,135 M
+# flop over the 144^3 element evaluations of an owner-computes launch.
 FLOP32_PER_ELEMENT = 2055
 # FP32 peak of one GB300 from its unit counts and clock: 152 SMs x 128 FP32
 # lanes x 2 flop (FMA) x 2.07 GHz.
@@ -374,7 +374,7 @@ def run_ours(args):
               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
               "frac": flops32 / t32 / 1e12 / FP32_PEAK_TFLOPS,
               # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
-              # the product's two kernels (profiles/elem_kernels_3d_129cubed_ncu.md)
+              # the product's two kernels
               "traffic": TRAFFIC_HESSVEC_FP32,
               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
               "fp32_fma_probe_tflops": fma32 / 1e12,
