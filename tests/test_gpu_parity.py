@@ -73,6 +73,27 @@ def test_hessvec_fp32(pf, dim, nc, L, hc):
     assert relinf(host(gr), O.gradient(g, Ho.prm, x)) <= TOL32
 
 
+def test_hessvec_fp32_element_owned_ragged(pf):
+    """The element-owned 3D FP32 product on ragged tiles: a 69 x 73 x 77
+    grid (68 x 72 x 76 elements, so the last tile along x and along z is
+    part-filled) has 9 x 9 x 10 element tiles of 8^3, enough for the
+    element-owned path.  In full against the oracle, plain and lagged, and
+    the same bits on a second call."""
+    import torch
+    H, Ho = pair(3, (18, 19, 20), 3, 1 / 17, nu=0.25, p=2e-3)
+    g = Ho.grids[-1]
+    assert g.n == (69, 73, 77)
+    x = PI.random_state(51, 3, g.N, u_scale=1e-2)
+    v = PI.random_direction(52, x.size)
+    x32, v32 = dev(x, torch.float32), dev(v, torch.float32)
+    ho = O.hessvec(g, Ho.prm, x, v)
+    h1 = host(pf.hessvec(H, 2, x32, v32))
+    assert relinf(h1, ho) <= TOL32
+    assert np.array_equal(h1, host(pf.hessvec(H, 2, x32, v32)))
+    pf.hessvec_lag_set(H, 2, x32)
+    assert relinf(host(pf.hessvec_lagged(H, 2, v32)), ho) <= TOL32
+
+
 @pytest.mark.parametrize("dim,nc,L,hc", SMALL[:2])
 @pytest.mark.parametrize("k_res", [0.0, 0.01])
 @pytest.mark.parametrize("scale", [0.1, 1e-6])
