@@ -350,6 +350,87 @@ def test_level_model_coherence():
     assert abs(mid.diff(x0c + s, s) - (mid.value(x0c + 2 * s) - mid.value(x0c + s))) < 1e-12
 
 
+# ---------------------------------------------------------------- subproblem
+# Closed forms of the box-constrained quadratic subproblem
+# min g.s + 1/2 s.Hs over lo <= s <= hi (the TR subproblem of Sec. 3):
+# with H = diag(h), h > 0, the problem separates and its minimiser is
+# clamp(-g/h, lo, hi) coordinate by coordinate.
+def _diag_qp(seed, n):
+    r = PI.rng(seed)
+    h = r.uniform(0.5, 4.0, n)
+    g = r.normal(0.0, 1.0, n)
+    lo = -r.uniform(0.05, 1.0, n)
+    hi = r.uniform(0.05, 1.0, n)
+    return g, h, lo, hi
+
+
+@pytest.mark.parametrize("g,h,lo,hi", [
+    (1.0, 2.0, -1.0, 1.0),    # interior minimiser -0.5
+    (-3.0, 1.0, -1.0, 2.0),   # interior minimiser 3 cut at hi = 2
+    (4.0, 0.5, -1.5, 0.3),    # minimiser -8 cut at lo = -1.5
+    (0.2, 10.0, -1.0, 1.0),   # small step -0.02
+])
+def test_subproblem_1d_closed_form(g, h, lo, hi):
+    tr = O.TRParams()
+    s = O.solve_subproblem(np.array([g]), lambda v: h * v, np.array([lo]), np.array([hi]),
+                           delta=10.0, cg_max=10, tr=tr)
+    assert abs(s[0] - min(max(-g / h, lo), hi)) <= 1e-14
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_subproblem_separable_box_minimiser(seed):
+    """Diagonal H, bounds wider than the radius delta, some unconstrained
+    minimisers outside the box.  The Cauchy point -delta g / max|g| is then
+    interior; one Jacobi-preconditioned CG iteration (M^-1 H = I) reaches
+    -g/h and leaves the box; the projected search clamps it, which is the
+    exact separable minimiser; the restart finds a zero residual on the free
+    set.  (A coordinate that reaches a bound stays fixed for the rest of the
+    subproblem, so the bounds are kept clear of the Cauchy point.)"""
+    n = 24
+    r = PI.rng(seed)
+    h = r.uniform(0.5, 4.0, n)
+    g = r.normal(0.0, 1.0, n)
+    delta = 0.01
+    lo = -r.uniform(0.05, 1.0, n)
+    hi = r.uniform(0.05, 1.0, n)
+    exact = np.clip(-g / h, lo, hi)
+    assert 3 <= np.sum(exact != -g / h) <= n - 3
+    s = O.solve_subproblem(g, lambda v: h * v, lo, hi, delta=delta, cg_max=500, tr=O.TRParams(),
+                           minv=1.0 / h)
+    assert np.all(s >= lo) and np.all(s <= hi)
+    assert np.max(np.abs(s - exact)) <= 1e-12
+
+
+def test_subproblem_backtracks_a_bent_cauchy_path():
+    """SPD H = [[1, -0.9], [-0.9, 1]], g = (1, 1), lo = (-10, -0.1): the
+    curvature along -g gives t = 10, and projecting -t g onto the box bends
+    the path so that the model rises (m = 39 at t = 10, 7.0 at 5, 0.3 at
+    2.5); backtracking accepts t = 1.25, and CG on the one free coordinate
+    then reaches the KKT point (-1.09, -0.1): d m / d s_0 = 0 there, and
+    s_1 sits on its lower bound with d m / d s_1 = 1.881 > 0."""
+    H = np.array([[1.0, -0.9], [-0.9, 1.0]])
+    g = np.array([1.0, 1.0])
+    lo, hi = np.array([-10.0, -0.1]), np.array([10.0, 10.0])
+    s = O.solve_subproblem(g, lambda v: H @ v, lo, hi, delta=100.0, cg_max=50, tr=O.TRParams(),
+                           minv=np.ones(2))
+    assert np.max(np.abs(s - np.array([-1.09, -0.1]))) <= 1e-12
+    assert g @ s + 0.5 * s @ H @ s < 0.0
+
+
+def test_subproblem_radius_caps_the_cauchy_step():
+    """A box tighter than the unconstrained step (the TR radius delta enters
+    as the box |s_i| <= delta): every coordinate ends on the bound that -g
+    points to, as the separable minimiser says."""
+    g, h, _, _ = _diag_qp(5, 16)
+    delta = 1e-3
+    lo, hi = -delta * np.ones(16), delta * np.ones(16)
+    s = O.solve_subproblem(g, lambda v: h * v, lo, hi, delta=delta, cg_max=50, tr=O.TRParams(),
+                           minv=1.0 / h)
+    exact = np.clip(-g / h, lo, hi)
+    assert np.all(np.abs(-g / h) > delta)  # every step is cut
+    assert np.max(np.abs(s - exact)) <= 1e-15
+
+
 # ---------------------------------------------------------------- planted mistakes
 def test_pins_catch_a_planted_sign_error(monkeypatch):
     g = O.Grid(2, (4, 4), 0.25)
@@ -383,3 +464,18 @@ def test_pins_catch_a_dropped_pressure_term(monkeypatch):
     e = np.zeros(x.size)
     e[2 * g.N + 4] = 1.0
     assert np.max(np.abs(O.hessvec(g, prm, x, e) - D[:, 2 * g.N + 4])) > 1e-4
+
+
+def test_pins_catch_a_planted_model_sign_error(monkeypatch):
+    """The subproblem's acceptance tests with the quadratic term of the model
+    negated accept the first, rising trial of the bent Cauchy path."""
+    monkeypatch.setattr(O, "_model", lambda g, s, Hs: float(g @ s) - 0.5 * float(s @ Hs))
+    with pytest.raises(AssertionError):
+        test_subproblem_backtracks_a_bent_cauchy_path()
+
+
+def test_pins_catch_a_planted_projection_error(monkeypatch):
+    """A projection that forgets the upper bounds fails the separable pin."""
+    monkeypatch.setattr(O, "proj_box", lambda s, lo, hi: np.maximum(s, lo))
+    with pytest.raises(AssertionError):
+        test_subproblem_separable_box_minimiser(1)
