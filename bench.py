@@ -93,6 +93,21 @@ def rank_info():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def job_seconds_per_load_step(rank_seconds, dist=None, device="cpu"):
+    """Seconds per load step of N replicas (one per rank): each rank times its
+    own load steps, the job lasts as long as its slowest rank, and in that
+    time the N replicas complete N load steps.  Returns (the slowest rank's
+    seconds per step, the whole job's seconds per load step); a collective
+    call, made by every rank."""
+    if dist is None:
+        return rank_seconds, rank_seconds
+    import torch
+    t = torch.tensor([float(rank_seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return slowest, slowest / dist.get_world_size()
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -317,11 +332,10 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    slowest_s, job_s = job_seconds_per_load_step(e0.elapsed_time(e1) / args.steps / 1e3, dist,
+                                                 "cuda")
+    ms = slowest_s * 1e3
     if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
 
     # ---- dominant kernel: Hessian-vector product at the finest level
@@ -431,7 +445,7 @@ def run_ours(args):
         for t in range(args.warmup + 1, args.warmup + args.steps + 1):
             pf.pressure_set(H, W["dp"] * t)
             pf.rmtr_load_step_host(H, xn, with_p_prev(prm, t), check=False)
-        e2e_s = (time.perf_counter() - t0) / args.steps
+        _, e2e_s = job_seconds_per_load_step((time.perf_counter() - t0) / args.steps, dist, "cuda")
         e2e = {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
                "d2h_bytes_per_step": 8 * ndof}
 
@@ -447,7 +461,7 @@ def run_ours(args):
                "pass_seconds": pass_s}
 
     launches = int(sum(s["launches"] for s in stats))
-    value = ms / 1e3
+    value = job_s
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
