@@ -183,6 +183,19 @@ def oracle_pass_seconds(budget_s=20.0):
     return {k: min(v) for k, v in times.items()}, g
 
 
+def workload_config(W, args, world):
+    """The workload both arms report: grid, sizes, the timed pressures and the
+    GPU arm's solver settings."""
+    n = [(c - 1) * (1 << (W["levels"] - 1)) + 1 for c in W["n_coarse"]]
+    return {"workload": W["workload"], "grid": n, "levels": W["levels"],
+            "dofs": (W["dim"] + 1) * int(np.prod(n)), "fractures": W["fractures"],
+            "pressure_steps": [W["dp"] * t
+                               for t in range(args.warmup + 1, args.warmup + args.steps + 1)],
+            "precision": args.precision, "coarse_model": args.coarse_model, "start": args.start,
+            "parallelism": f"replicas{world}",
+            "l2": "working set > L2 (FP64 vectors 69 MB each, >20 resident)"}
+
+
 def oracle_seconds_per_load_step(pass_s, work):
     return (pass_s["hessvec"] * work["fe_hessvec"] + pass_s["gradient"] * work["fe_gradient"]
             + pass_s["energy"] * work["fe_energy"])
@@ -212,7 +225,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {k: WORKLOAD[k] for k in ("workload", "n_coarse", "levels", "fractures")},
+        "data": "synthetic", "config": workload_config(WORKLOAD, args, world),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                          "sample": ("one FP64 numpy oracle pass each of hessvec, gradient and energy "
                                     "difference on the full 129^3 state per step, scaled by the CUDA path's "
@@ -469,13 +482,7 @@ def run_ours(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": W["workload"], "grid": list(g_n), "levels": W["levels"],
-                       "dofs": ndof, "fractures": W["fractures"], "pressure_steps": [
-                           W["dp"] * t for t in range(args.warmup + 1, args.warmup + args.steps + 1)],
-                       "precision": args.precision, "coarse_model": args.coarse_model,
-                       "start": args.start,
-                       "parallelism": f"replicas{world}",
-                       "l2": "working set > L2 (FP64 vectors 69 MB each, >20 resident)"},
+            "config": workload_config(W, args, world),
             "roofline": roofline,
             "roofline_other": roof32 if roofline is roof64 else roof64,
             "hessvec_gdofs": {"fp64": ndof / t64 / 1e9, "fp32": ndof / t32 / 1e9},
