@@ -169,7 +169,10 @@ pf_status pf_level_info(const pf_hierarchy* h, int level, int n_out[3],
 pf_status pf_fractures_set(pf_hierarchy* h, int kind, int n, const double* rows_host,
                            double band_half_width, void* x_dev);
 
-/* Uniform pressure p of eq. (pressurized) for all following calls. */
+/* Uniform pressure p of eq. (pressurized) for all following calls.  Also
+ * writes an FP32 copy of p to the device on the hierarchy's stream (the 3D
+ * FP32 Hessian products read it there) and synchronises that stream.
+ * Errors: PF_EINVAL (null handle), PF_ENONFINITE (p not finite), PF_ECUDA. */
 pf_status pf_pressure_set(pf_hierarchy* h, double p);
 
 /* Discrete energy of eq. (pressurized) (AT2, sign reading +p g(c) div u,
@@ -221,7 +224,9 @@ pf_status pf_gradient_step(pf_hierarchy* h, int level, const double* x_dev, cons
 
 /* Hessian of the energy at x_lin_dev applied to v_dev, written to Hv_dev;
  * matrix-free (Sec. 4.2.1 Hessian; applied, not assembled).  All three
- * vectors in precision prec, computed in that precision. */
+ * vectors in precision prec, computed in that precision.  3D FP32 products
+ * on grids of at least 304 element tiles of 8^3 evaluate each element once
+ * and sum a node's tiles in a fixed order; every product is deterministic. */
 pf_status pf_hessvec(pf_hierarchy* h, int level, const void* x_lin_dev, const void* v_dev,
                      void* Hv_dev, int prec);
 
