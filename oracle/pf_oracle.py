@@ -32,9 +32,10 @@ Level index 0 is the coarsest level (the paper's l = 1).
 
 Parity status: energy, gradient and hessvec are pinned by the patch test,
 exact 5-point finite differences, symmetry and an independently assembled
-dense Hessian; transfers by linear reproduction and adjointness; the solver
-by the 1D closed-form phase-field profile, Sneddon's opening and the
-invariants.  The level model's choice of f~^l beyond "the same functional on
+dense Hessian; the Jacobi diagonal by that dense Hessian's diagonal;
+Convergence_control by a hand-written table of Algorithm 3's cases;
+transfers by linear reproduction and adjointness; the solver by the 1D
+closed-form phase-field profile, Sneddon's opening and the invariants.  The level model's choice of f~^l beyond "the same functional on
 the coarse grid" is "parity unpinned" apart from its coherence identities.
 """
 from __future__ import annotations

@@ -17,7 +17,9 @@ are this library's readings (listed in the design notes):
 Tensors are (channels, H, W) float64 arrays, H and W multiples of 8.
 Convolutions are written as im2col followed by one matrix product.
 Parity status: pinned by central finite differences of a scalar loss
-through every parameter tensor and the input (tests/test_unet_oracle.py).
+through every parameter tensor and the input; Adam by its closed-form first
+step from zero moments and a second step worked by hand
+(tests/test_unet_oracle.py).
 """
 from __future__ import annotations
 

@@ -479,3 +479,93 @@ def test_pins_catch_a_planted_projection_error(monkeypatch):
     monkeypatch.setattr(O, "proj_box", lambda s, lo, hi: np.maximum(s, lo))
     with pytest.raises(AssertionError):
         test_subproblem_separable_box_minimiser(1)
+
+
+# ---------------------------------------------------------------- Jacobi diagonal
+@pytest.mark.parametrize("dim,n,k", [(2, (3, 3), 0.0), (2, (4, 4), 0.05), (3, (3, 3, 3), 0.0)])
+def test_hess_diag_is_the_dense_hessian_diagonal(dim, n, k):
+    """The subproblem's Jacobi preconditioner must be the diagonal of the
+    Hessian (eq. model_qp's H): compared with the independently assembled
+    dense Hessian of P4, entry by entry, with the pressure term active."""
+    g = O.Grid(dim, n, 0.5)
+    prm = _prm(k)
+    x = PI.random_state(41, dim, g.N, u_scale=0.3)
+    D = np.diag(O.dense_hessian(g, prm, x))
+    d = O.hess_diag(g, prm, x)
+    assert np.max(np.abs(d - D)) <= 1e-13 * np.max(np.abs(D))
+
+
+def test_pins_catch_a_planted_diagonal_error(monkeypatch):
+    """A Jacobi diagonal that forgets g'' (psi + p div u) in its c entries
+    fails the dense-diagonal pin (the dense Hessian builds its own g'')."""
+    g = O.Grid(2, (3, 3), 0.5)
+    prm = _prm()
+    x = PI.random_state(41, 2, g.N, u_scale=0.3)
+    D = np.diag(O.dense_hessian(g, prm, x))
+    orig = O._degradation
+
+    def no_ddg(prm_, c):
+        gg, dg, ddg = orig(prm_, c)
+        return gg, dg, 0.0 * ddg
+
+    monkeypatch.setattr(O, "_degradation", no_ddg)
+    d = O.hess_diag(g, prm, x)
+    assert np.max(np.abs(d - D)) > 1e-6 * np.max(np.abs(D))
+
+
+# ---------------------------------------------------------------- Algorithm 3
+# Convergence_control with eta1 = 0.1, eta2 = 0.75, gamma1 = 0.5, gamma2 = 2,
+# delta_max = 1: each row is (rho, delta in, accepted?, delta out), the
+# expected radius written out by hand from Algorithm 3's three cases
+# (rho < eta1 shrink, eta1 <= rho <= eta2 keep, rho > eta2 expand, capped).
+RADIUS_TABLE = [
+    (-3.0, 0.4, False, 0.2),     # energy rose: reject, shrink
+    (0.05, 0.4, False, 0.2),     # below eta1: reject, shrink
+    (0.1, 0.4, False, 0.4),      # rho = eta1: not accepted (strict), radius kept
+    (0.3, 0.4, True, 0.4),       # between: accept, keep
+    (0.75, 0.4, True, 0.4),      # rho = eta2: keep
+    (0.9, 0.4, True, 0.8),       # above eta2: accept, expand
+    (1.7, 0.7, True, 1.0),       # expansion capped at delta_max
+    (0.9, 1.0, True, 1.0),       # already at the cap
+]
+
+
+def test_convergence_control_radius_table():
+    tr = O.TRParams()
+    lb = np.array([0.0, -np.inf, 0.2])
+    ub = np.array([1.0, np.inf, 1.0])
+    x = np.array([0.5, 3.0, 0.3])
+    s = np.array([0.7, -1.0, -0.25])  # the first and last leave the box
+    for rho, delta, acc, delta_out in RADIUS_TABLE:
+        xn, dn = O.convergence_control(rho, x, s, delta, lb, ub, tr)
+        assert dn == delta_out, (rho, delta)
+        if acc:
+            assert np.array_equal(xn, np.array([1.0, 2.0, 0.2])), rho
+        else:
+            assert np.array_equal(xn, x), rho
+
+
+def test_pins_catch_swapped_radius_factors(monkeypatch):
+    """Convergence_control with gamma1 and gamma2 exchanged fails the table."""
+    real = O.convergence_control
+
+    def swapped(rho, x, s, delta, lb, ub, tr):
+        t = O.TRParams(**{**tr.__dict__, "gamma1": tr.gamma2, "gamma2": tr.gamma1})
+        return real(rho, x, s, delta, lb, ub, t)
+
+    monkeypatch.setattr(O, "convergence_control", swapped)
+    with pytest.raises(AssertionError):
+        test_convergence_control_radius_table()
+
+
+def test_pins_catch_swapped_thresholds(monkeypatch):
+    """Convergence_control with eta1 and eta2 exchanged fails the table."""
+    real = O.convergence_control
+
+    def swapped(rho, x, s, delta, lb, ub, tr):
+        t = O.TRParams(**{**tr.__dict__, "eta1": tr.eta2, "eta2": tr.eta1})
+        return real(rho, x, s, delta, lb, ub, t)
+
+    monkeypatch.setattr(O, "convergence_control", swapped)
+    with pytest.raises(AssertionError):
+        test_convergence_control_radius_table()

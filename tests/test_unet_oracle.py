@@ -93,3 +93,46 @@ def test_adam_step_decreases_loss():
         grads, _ = U.backward(p, acts, dy, ch=ch)
         U.adam_step(p, grads, st, lr=1e-2)
     assert loss < 0.8 * l0
+
+
+def _adam_pin(adam):
+    """Adam (Kingma & Ba, Algorithm 1) from zero moments: the first step is
+    -lr g / (|g| + eps) for every entry (bias-corrected moments are g and
+    g^2); the second step, for g1 = 0.5 then g2 = -0.25 with lr = 0.1,
+    beta1 = 0.9, beta2 = 0.999, eps = 1e-8, worked by hand:
+    m2 = 0.9*0.05 - 0.1*0.25 = 0.02, m2/(1-0.81) = 0.10526315789473684;
+    v2 = 0.999*0.00025 + 0.001*0.0625 = 0.00031225, v2/(1-0.998001)
+    = 0.1562031015507775, sqrt = 0.3952253807016...;
+    step = -0.1 * 0.10526315789473684 / (0.3952253807016 + 1e-8)... = -0.0266337033..."""
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    p = {"w": np.array([1.0, 1.0, 1.0, 1.0])}
+    st = {}
+    adam(p, {"w": g.copy()}, st, lr=0.1)
+    first = np.array([1.0 - 0.1 * 0.5 / (0.5 + 1e-8), 1.0 + 0.1 * 2.0 / (2.0 + 1e-8),
+                      1.0 - 0.1 * 1e-3 / (1e-3 + 1e-8), 1.0])
+    assert np.max(np.abs(p["w"] - first)) <= 1e-15
+    p2 = {"w": np.array([0.0])}
+    st2 = {}
+    adam(p2, {"w": np.array([0.5])}, st2, lr=0.1)
+    w1 = float(p2["w"][0])
+    adam(p2, {"w": np.array([-0.25])}, st2, lr=0.1)
+    assert abs(w1 - (-0.1 * 0.5 / (0.5 + 1e-8))) <= 1e-15
+    assert abs((float(p2["w"][0]) - w1) - (-0.0266337033)) <= 1e-9
+
+
+def test_adam_first_and_second_step_closed_form():
+    _adam_pin(U.adam_step)
+
+
+def test_pins_catch_a_dropped_bias_correction():
+    """Adam without the bias correction of its moments fails the pin."""
+    def no_bias(params, grads, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        for k in params:
+            m = state.setdefault("m." + k, np.zeros_like(params[k]))
+            v = state.setdefault("v." + k, np.zeros_like(params[k]))
+            m[...] = beta1 * m + (1 - beta1) * grads[k]
+            v[...] = beta2 * v + (1 - beta2) * grads[k] ** 2
+            params[k] -= lr * m / (np.sqrt(v) + eps)
+
+    with pytest.raises(AssertionError):
+        _adam_pin(no_bias)
