@@ -2,6 +2,8 @@
 // device memory.  Its reduction scratch (one partial sum per block and a
 // completion counter) lives in a fixed array in the library's own device
 // memory instead of a buffer obtained from cudaMalloc.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -28,11 +30,46 @@ constexpr size_t kNoAllocBytes = kNoAllocPartials * sizeof(double) + 256;
 // process exits; every device that loads the library holds its own copy.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device addresses of g_noalloc_scratch, looked up once per device.  In host
-// code the symbol names a host-side stand-in, never the device array.
+// Device addresses of g_noalloc_scratch, looked up once per device and
+// context.  In host code the symbol names a host-side stand-in, never the
+// device array.  The address belongs to the context that loaded the module:
+// after cudaDeviceReset (or any teardown of the device's context) the next
+// call sees a new context id and looks the address up again, so no call
+// writes through the address of a context that is gone.
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_dev[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Id of the calling thread's current context (0 if none), through driver
+// entry points obtained from the runtime (the library links no libcuda).
+cudaError_t current_context_id(unsigned long long* id) {
+  *id = 0;
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&g_ctx_get_current,
+                                                     12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess)
+      e = cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&g_ctx_get_id, 12000,
+                                           cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+      g_ctx_get_current = nullptr;
+      g_ctx_get_id = nullptr;
+      return cudaErrorSymbolNotFound;
+    }
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+  if (!ctx) return cudaSuccess;
+  if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+  return cudaSuccess;
+}
 
 cudaError_t scratch_for_current_device(unsigned char** out) {
   int dev = -1;
@@ -40,11 +77,17 @@ cudaError_t scratch_for_current_device(unsigned char** out) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_dev[dev]) {
+  unsigned long long ctx = 0;
+  e = current_context_id(&ctx);
+  if (e != cudaSuccess) return e;
+  if (!g_scratch_dev[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the device's context current
+    if (e != cudaSuccess) return e;
+    e = current_context_id(&ctx);
     if (e != cudaSuccess) return e;
     g_scratch_dev[dev] = static_cast<unsigned char*>(p);
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_dev[dev];
   return cudaSuccess;

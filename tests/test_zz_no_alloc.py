@@ -55,3 +55,25 @@ def test_energy_noalloc_rejects_oversized_grids():
                                    B.PF_FP64, C.c_void_p(out.data_ptr()), None)
     assert rc == B.PF_EINVAL
     assert b"16,777,216" in B.lib().pf_last_error()
+
+
+def test_energy_noalloc_leaves_device_memory_unchanged():
+    """After the first call on the device (which looks up the scratch
+    array's address), further calls change the device's free memory by
+    nothing: the call allocates no device memory of its own."""
+    torch = require_cuda()
+    from paper_2007_12908_gb300 import _binding as B
+    n = (65, 65, 65)
+    N = n[0] * n[1] * n[2]
+    x = dev(PI.random_state(9, 3, N, u_scale=1e-3, c_hi=1.0), torch.float64)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    B.energy_noalloc(3, n, 1 / 64, 1.0, 0.25, 1.0, 2 / 64, 0.0, 1e-3, x, out)
+    torch.cuda.synchronize()
+    first = float(out.item())
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        B.energy_noalloc(3, n, 1 / 64, 1.0, 0.25, 1.0, 2 / 64, 0.0, 1e-3, x, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert float(out.item()) == first  # fixed-order reduction: the same value every call
