@@ -39,6 +39,7 @@ typedef int pf_status;
 #define PF_ENOTCONV 5    /* rmtr_load_step hit max_cycles                    */
 #define PF_ETIMEOUT 6    /* a bounded device wait ran out                    */
 #define PF_ESTATE 7      /* call order violated (e.g. no fractures set)      */
+#define PF_EIO 8         /* a state file could not be read or written        */
 
 #define PF_FP64 0
 #define PF_FP32 1
@@ -151,6 +152,9 @@ const char* pf_last_error(void);
 
 /* Builds the level grids, Gauss/shape tables, transfer stencils and per-level
  * work buffers (Sec. 4.1 steps 2-4 and 6).  *out receives an owned handle.
+ * The device memory all of it needs is compared with the device's free
+ * memory before the first allocation: a hierarchy that does not fit (with
+ * 1 GB kept in reserve) is refused with PF_ENOMEM and nothing allocated.
  * Errors: PF_EINVAL for a bad descriptor, PF_ENOMEM, PF_ECUDA. */
 pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* desc, pf_hierarchy** out);
 pf_status pf_mesh_hierarchy_destroy(pf_hierarchy* h);
@@ -263,7 +267,9 @@ pf_status pf_coarse_bounds(pf_hierarchy* h, int coarse, const double* lo_f_dev,
  * precision or coarse model change, and held by the hierarchy until
  * pf_mesh_hierarchy_destroy.  The call synchronises the hierarchy's stream
  * (it reads scalars back) and cannot itself be captured into a graph.
- * Errors: PF_ENOTCONV (x still updated), PF_ENONFINITE, PF_ECUDA. */
+ * Errors: PF_ENOTCONV (x still updated), PF_ENONFINITE (a NaN/Inf in x on
+ * entry, or a non-finite projected gradient during the step: x, c_prev and
+ * the last converged pressure are left as they were on entry), PF_ECUDA. */
 pf_status pf_rmtr_load_step(pf_hierarchy* h, void* x_dev, const pf_rmtr_params* params,
                             pf_rmtr_stats* stats);
 
@@ -293,6 +299,26 @@ pf_status pf_rmtr_load_step_batch(int n, pf_hierarchy* const* hs, double* const*
 /* Copies the finest-level c_prev (FP64, N values) to c_prev_dev. */
 pf_status pf_get_c_prev(pf_hierarchy* h, double* c_prev_dev);
 
+/* Checkpoint and resume (Sec. 4.1 workflow: the state is exported after
+ * every pseudo-time step).  pf_state_save writes the finest FP64 state x_dev
+ * ((dim+1) N values), the hierarchy's c_prev, the current pressure and the
+ * last converged pressure (the extrapolated start's base) to the file
+ * `path`, with the grid and material in its header and an FNV-1a checksum
+ * of the payload; it writes `path`.tmp and renames it, so a reader never
+ * sees a partial file.  pf_state_load restores all of that into a hierarchy
+ * of the same grid and material (x_dev receives the state; the pressure is
+ * set as by pf_pressure_set), after which the next load step reproduces the
+ * uninterrupted run bit for bit.  The per-level trust-region radius and the
+ * lagged Hessians are not state: every load step starts them afresh.
+ * Both synchronise the hierarchy's stream.  Errors: PF_EINVAL (null
+ * argument; a file for another grid or material, of another version or byte
+ * order, or with a wrong checksum), PF_EIO (file cannot be opened, read or
+ * written, or its size disagrees with its header), PF_ENONFINITE (a
+ * non-finite value in the state or file), PF_ECUDA.  pf_state_load changes
+ * nothing unless every check passed. */
+pf_status pf_state_save(pf_hierarchy* h, const double* x_dev, const char* path);
+pf_status pf_state_load(pf_hierarchy* h, double* x_dev, const char* path);
+
 /* Energy of pf_energy for callers that cannot allocate device memory.
  * The paper has no counterpart: this exists for callers such as plug-ins
  * that run inside a host application which owns the whole device memory
@@ -311,7 +337,10 @@ pf_status pf_get_c_prev(pf_hierarchy* h, double* c_prev_dev);
  * elements are rejected with PF_EINVAL (use pf_energy for those).
  * The first call on a device looks up that array's device address (with
  * the device current), so make the first call on each device before any
- * stream capture.  Every call shares the one array and clears its counter
+ * stream capture; the lookup is repeated only when the device's context has
+ * changed (after cudaDeviceReset), so make the first call after such a
+ * reset before any stream capture too.  Every call shares the one array and
+ * clears its counter
  * on entry; calls whose kernels overlap on the GPU (two streams, two host
  * threads) race on it and must be serialised by the caller. */
 pf_status pf_energy_noalloc(int dim, const int n[3], double h, double E, double nu, double Gc,

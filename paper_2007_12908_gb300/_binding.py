@@ -13,14 +13,15 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpf.so")
 
-PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ENOTCONV, PF_ETIMEOUT, PF_ESTATE = range(8)
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ENOTCONV, PF_ETIMEOUT, PF_ESTATE, PF_EIO = \
+    range(9)
 PF_FP64, PF_FP32 = 0, 1
 PF_GALERKIN, PF_FIRST_ORDER = 0, 1
 PF_LINE2D, PF_DISC3D = 0, 1
 PF_START_PLAIN, PF_START_EXTRAPOLATE = 0, 1
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ENONFINITE",
-                5: "PF_ENOTCONV", 6: "PF_ETIMEOUT", 7: "PF_ESTATE"}
+                5: "PF_ENOTCONV", 6: "PF_ETIMEOUT", 7: "PF_ESTATE", 8: "PF_EIO"}
 
 # every symbol include/pf.h declares
 EXPORTS = [
@@ -34,6 +35,7 @@ EXPORTS = [
     "pf_unet_backward", "pf_unet_mse", "pf_unet_adam", "pf_learned_features", "pf_learned_target",
     "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient", "pf_rmtr_load_step_batch",
     "pf_energy_diff_mixed", "pf_gradient_step", "pf_gradient_df", "pf_energy_df",
+    "pf_state_save", "pf_state_load",
 ]
 
 
@@ -111,6 +113,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_rmtr_load_step": (i, [vp, vp, C.POINTER(RmtrParams), C.POINTER(RmtrStats)]),
         "pf_rmtr_load_step_host": (i, [vp, vp, C.POINTER(RmtrParams), C.POINTER(RmtrStats)]),
         "pf_get_c_prev": (i, [vp, vp]),
+        "pf_state_save": (i, [vp, vp, C.c_char_p]),
+        "pf_state_load": (i, [vp, vp, C.c_char_p]),
         "pf_probe_fma": (i, [i, C.POINTER(d)]),
         "pf_energy_noalloc": (i, [i, C.POINTER(C.c_int), d, d, d, d, d, d, d, vp, i, vp, vp]),
         "pf_hessvec_lag_set": (i, [vp, i, vp, i]),
@@ -431,6 +435,21 @@ def get_c_prev(H: Hierarchy):
     out = torch.empty(H.nodes(), dtype=torch.float64, device="cuda")
     _check(lib().pf_get_c_prev(H.handle, _dev(out, H.nodes())))
     return out
+
+
+def state_save(H: Hierarchy, x, path):
+    """Checkpoint: the finest state x (float64 CUDA tensor), c_prev and the
+    pressures to the file `path`."""
+    import torch
+    _check(lib().pf_state_save(H.handle, _dev(x, H.ndof(), torch.float64), os.fsencode(path)))
+
+
+def state_load(H: Hierarchy, x, path):
+    """Resume: restores a pf_state_save file into H and the float64 CUDA
+    tensor x (nothing changes unless the file passes every check)."""
+    import torch
+    _check(lib().pf_state_load(H.handle, _dev(x, H.ndof(), torch.float64), os.fsencode(path)))
+    return x
 
 
 def probe_fma(prec: int) -> float:

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -144,16 +145,60 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
     h->mat.push_back(make_mat(h->geo[l], h->E, h->nu, h->Gc, h->ls, h->k_res, 0.0));
   pf_status rc;
   const int F = d->dim + 1;
+  long long part = 0;
+  for (const Geom& g : h->geo) part = std::max(part, etile_part_count(g));
+  {
+    // Everything the hierarchy will hold, checked against the device's free
+    // memory before the first allocation: a hierarchy that cannot fit is
+    // refused with nothing allocated (and nothing to leak).  Each buffer is
+    // counted with 2 MiB of allocation slack, and 1 GiB is left free.
+    const double slack = 2.0 * 1024 * 1024;
+    double need = 0.0;
+    int count = 0;
+    auto add = [&](double bytes) { need += bytes + slack; ++count; };
+    add(8.0 * kMaxSlots * kMaxBlocks);
+    add(4.0);
+    add(8.0 * kMaxSlots);
+    add(8.0 * h->geo.back().N);
+    add(8.0 * h->geo.back().N);
+    add(double(sizeof(CgCtrl)));
+    add(16.0 * part);
+    add(4.0);
+    for (int l = 0; l < h->L; ++l) {
+      const double n = double(F) * double(h->geo[l].N);
+      for (int v = 0; v < 24; ++v) add(8.0 * (n + 4));
+      add(4.0 * n);
+      add(8.0 * double(coef_count(h->geo[l])));
+      add(8.0 * double(stencil_count(h->geo[l])));
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+      delete h;
+      set_error(std::string("mesh_hierarchy_create: cudaMemGetInfo: ") + cudaGetErrorString(e));
+      return PF_ECUDA;
+    }
+    const double headroom = 1024.0 * 1024 * 1024;
+    if (need + headroom > double(free_b)) {
+      delete h;
+      char msg[256];
+      snprintf(msg, sizeof msg,
+               "mesh_hierarchy_create: the hierarchy needs %.3g GB of device memory in %d "
+               "buffers, %.3g GB are free (1 GB kept in reserve); nothing was allocated",
+               need / 1e9, count, double(free_b) / 1e9);
+      set_error(msg);
+      return PF_ENOMEM;
+    }
+  }
   if ((rc = alloc(h, (void**)&h->scratch.partials, sizeof(double) * kMaxSlots * kMaxBlocks)) ||
       (rc = alloc(h, (void**)&h->scratch.counter, sizeof(unsigned))) ||
       (rc = alloc(h, (void**)&h->d_res, sizeof(double) * kMaxSlots)) ||
       (rc = alloc(h, (void**)&h->c_prev, sizeof(double) * h->geo.back().N)) ||
+      (rc = alloc(h, (void**)&h->c_prev_save, sizeof(double) * h->geo.back().N)) ||
       (rc = alloc(h, (void**)&h->ctrl, sizeof(CgCtrl)))) {
     pf_mesh_hierarchy_destroy(h);
     return rc;
   }
-  long long part = 0;
-  for (const Geom& g : h->geo) part = std::max(part, etile_part_count(g));
   if ((part > 0 && (rc = alloc(h, &h->etile_part, sizeof(float4) * part))) ||
       (rc = alloc(h, (void**)&h->p_dev, sizeof(float)))) {
     pf_mesh_hierarchy_destroy(h);

@@ -42,6 +42,7 @@ struct pf_hierarchy {
   double* d_res = nullptr;  // device result slots
   double* h_res = nullptr;  // pinned host mirror
   double* c_prev = nullptr; // finest N values
+  double* c_prev_save = nullptr;  // c_prev at the start of a load step (restored on failure)
   pf::CgCtrl* ctrl = nullptr;    // device CG control block
   pf::CgCtrl* h_ctrl = nullptr;  // pinned host mirror
   void* etile_part = nullptr;  // node sums of the element-owned FP32 Hessian tiles (3D)

@@ -1338,8 +1338,21 @@ struct Solver {
     const long long N = g.N;
     const int dim = H->dim;
     double pg_ref = P.pg_ref;
+    // a non-finite input is refused before anything is touched: x_user,
+    // c_prev and the last converged pressure stay as they were
+    {
+      const double* xu = x_user;
+      double bad_count;
+      reduce<1, OpSum>(B.n, [=] __device__(long long i, double(&v)[1]) {
+        v[0] = isfinite(xu[i]) ? 0.0 : 1.0;
+      }, &bad_count);
+      if (bad_count != 0.0) return PF_ENONFINITE;
+    }
+    // c_prev of the caller's last step, restored if this step fails
+    copy(H->c_prev_save, H->c_prev, N);
     bool g_at_t3 = false;  // B.g holds the FP64 gradient at B.t3 = the plain start
     const double p_before = P.p_prev > 0.0 ? P.p_prev : H->p_last;
+    copy(B.x, x_user, B.n);
     if (P.start == PF_START_EXTRAPOLATE && p_before > 0.0 && H->p != p_before) {
       // the displacement is nearly linear in p: start from u p / p_last, c
       // unchanged, and stop at the accuracy of the plain start
@@ -1348,10 +1361,9 @@ struct Solver {
         g_at_t3 = true;
       }
       const double r = H->p / p_before;
-      double* xu = x_user;
-      map((long long)dim * N, [=] __device__(long long i) { xu[i] *= r; });
+      double* xs = B.x;
+      map((long long)dim * N, [=] __device__(long long i) { xs[i] *= r; });
     }
-    copy(B.x, x_user, B.n);
     // c_prev := c (unless kept from an accepted proposal); finest bounds of
     // eq. (space_pf), clamped displacement
     if (!P.keep_c_prev) copy(H->c_prev, B.x + dim * N, N);
@@ -1395,7 +1407,7 @@ struct Solver {
       pg0 = pg_norm(B.x);
     }
     if (!std::isfinite(pg0)) {
-      copy(x_user, B.x, B.n);
+      copy(H->c_prev, H->c_prev_save, N);
       ck(cudaStreamSynchronize(st), "sync");
       return PF_ENONFINITE;
     }
@@ -1418,10 +1430,15 @@ struct Solver {
     S.pg0 = pg0;
     S.pg = pg;
     S.pg_ref = ref;
+    if (!std::isfinite(pg)) {
+      // an aborted step leaves the caller's state as it was
+      copy(H->c_prev, H->c_prev_save, N);
+      ck(cudaStreamSynchronize(st), "sync");
+      return PF_ENONFINITE;
+    }
     S.energy = energy(L - 1, B.x);
     copy(x_user, B.x, B.n);
     ck(cudaStreamSynchronize(st), "sync");
-    if (!std::isfinite(pg)) return PF_ENONFINITE;
     if (conv) H->p_last = H->p;
     return conv ? PF_OK : PF_ENOTCONV;
   }
@@ -1455,7 +1472,9 @@ pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_para
   }
   S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (rc == PF_ENOTCONV) set_error("rmtr_load_step: max_cycles reached before the tolerance");
-  if (rc == PF_ENONFINITE) set_error("rmtr_load_step: non-finite projected gradient");
+  if (rc == PF_ENONFINITE)
+    set_error("rmtr_load_step: non-finite value in x or in the projected gradient (x and c_prev "
+              "left unchanged)");
   if (stats) *stats = S;
   return rc;
 }

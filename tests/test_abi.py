@@ -102,6 +102,8 @@ def test_defaults_and_validation_on_host(lib):
     assert lib.pf_hessvec(None, 0, None, None, None, 0) == B.PF_EINVAL
     assert lib.pf_rmtr_load_step(None, None, None, None) == B.PF_EINVAL
     assert lib.pf_mesh_hierarchy_destroy(None) == B.PF_OK
+    assert lib.pf_state_save(None, None, b"x") == B.PF_EINVAL
+    assert lib.pf_state_load(None, None, None) == B.PF_EINVAL
 
 
 def test_batch_validation_on_host(lib):
