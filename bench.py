@@ -1,15 +1,24 @@
 #!/usr/bin/env python3
 """RMTR seconds per load step on the 3D 129^3 four-level workload (20
-penny-shaped fractures, pressure ramp p_t = 5e-4 t), plus the Hessian-vector
-product's throughput and roofline, on one GB300.
+penny-shaped fractures, pressure ramp p_t = 5e-4 t, t = 1..10), plus the
+Hessian-vector product's throughput and roofline, on one GB300.
 
 One "step" is one pseudo-time load step: pressure_set + rmtr_load_step (all
 of the hot path: energy, gradient, hessvec, projected CG, TR control,
-transfers, coarse feasible set, level model, V-cycles).  Inputs are seeded
-synthetic fracture networks (no dataset); the state lives in HBM.
+transfers, coarse feasible set, level model, V-cycles).  Run step k solves
+ramp step t = (k - 1) mod 10 + 1 and restarts from the fractured state at
+t = 1, so every timed pressure lies on the 10-step ramp to 5e-3.  Inputs are
+seeded synthetic fracture networks (no dataset); the state lives in HBM.
+
+By default the line also carries the metric's comparison, measured in the
+same run: the same ramp steps from the same warmed state in plain FP64
+(plain start) and in mixed precision with the plain start, with the per-field
+error of the mixed fields against the FP64 fields at every step; and the
+FP64 oracle timed on the host cores (whole load steps of the same workload
+eight times coarser per axis, beside the GPU on those same steps).
 
   python bench.py [--steps K] [--warmup W] [--precision fp64|mixed]
-  python bench.py --impl reference      # the FP64 CPU oracle, bounded sample
+  python bench.py --impl reference      # the FP64 CPU oracle
 
 Multi-GPU: the path does not shard across GPUs here, so N ranks run N
 independent replicas (one workload each; no collective on the data path).
@@ -38,6 +47,16 @@ WORKLOAD = {
     "E": 1.0, "nu": 0.25, "Gc": 1.0, "ls_over_h": 2.0,
     "fractures": 20, "seed": PI.SEED_3D_PLAIN, "dp": 5e-4,
 }
+# The same workload eight times coarser per axis (four levels 3^3 -> 17^3, the
+# same 20 discs, material and ramp): the size on which the FP64 oracle runs
+# whole load steps in seconds, timed beside the GPU on equal work.
+WORKLOAD_SMALL = dict(WORKLOAD, workload="3d_17^3_q1_4level_20discs_ramp", n_coarse=[3, 3, 3],
+                      h_coarse=0.5)
+# The pressure ramp of the 3D workload: p_t = 5e-4 t for t = 1 .. 10 (final
+# 5e-3).  Step k of a run (warm-up and timed steps counted together from 1)
+# is ramp step t = (k - 1) mod 10 + 1; at t = 1 the state restarts from the
+# fractured initial state, so no pressure above 5e-3 is ever solved.
+RAMP = 10
 METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same GB300"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
@@ -51,17 +70,14 @@ UNIT = "s/load-step"
 # one ncu capture (FFMA2 x4, FFMA x2, FADD2/FMUL2 x2, FADD/FMUL x1): 6,135 M
 # flop over the 144^3 element evaluations of an owner-computes launch.
 FLOP32_PER_ELEMENT = 2055
-# FP32 peak of one GB300 from its unit counts and clock: 152 SMs x 128 FP32
-# lanes x 2 flop (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 lanes per SM (Blackwell): the ALU roofline is SMs x lanes x 2 flop
+# (one FMA) x the SM clock sampled while the kernels ran.
+FP32_LANES_PER_SM = 128
 
-# Finest-level-equivalent element passes per load step of the CUDA path on
-# this workload (default configuration: mixed precision, extrapolated
-# start), measured by this script's GPU arm (printed as "work_model"); they
-# scale the oracle's per-pass seconds to seconds per load step for the
-# reference arm.
-REF_WORK_MODEL = {"fe_hessvec": 228.4, "fe_gradient": 9.18, "fe_energy": 8.17}
 
+def ramp_t(k: int) -> int:
+    """Ramp step (1 .. RAMP) of run step k (1-based)."""
+    return (k - 1) % RAMP + 1
 
 
 def parse():
@@ -73,8 +89,11 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--start", choices=["plain", "extrapolate"], default="extrapolate",
                     help="starting iterate of each load step (plain = x_{t-1})")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64-plain and plain-start arms (run by default)")
     ap.add_argument("--compare-fp64", action="store_true",
-                    help="also time the same K load steps in plain FP64")
+                    help="accepted for old command lines; the comparison runs by default")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--kernels-only", action="store_true",
                     help="set up the workload state, launch the element kernels and exit")
     ap.add_argument("--coarse-n", type=int, default=17,
@@ -159,46 +178,12 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- oracle timing
-def oracle_pass_seconds(budget_s=20.0):
-    """Seconds per finest-level hessvec / gradient / energy-difference pass of
-    the FP64 oracle on the 129^3 workload state (one call each, repeated
-    while the budget lasts)."""
-    from oracle import pf_oracle as O
-    W = WORKLOAD
-    H = O.Hierarchy(3, W["n_coarse"], W["h_coarse"], W["levels"],
-                    O.Params(E=W["E"], nu=W["nu"], Gc=W["Gc"], p=W["dp"]))
-    g = H.fine
-    x = np.zeros(4 * g.N)
-    x[3 * g.N:] = O.rasterize(g, O.DISC3D, PI.disc_network_3d(W["seed"], W["fractures"]), g.h)
-    x[:3 * g.N] = PI.random_direction(5, 3 * g.N, 1e-4)
-    v = PI.random_direction(6, x.size, 1e-4)
-    times = {"hessvec": [], "gradient": [], "energy": []}
-    t_end = time.perf_counter() + budget_s
-    while True:
-        t = time.perf_counter(); O.hessvec(g, H.prm, x, v); times["hessvec"].append(time.perf_counter() - t)
-        t = time.perf_counter(); O.gradient(g, H.prm, x); times["gradient"].append(time.perf_counter() - t)
-        t = time.perf_counter(); O.energy_diff(g, H.prm, x, v); times["energy"].append(time.perf_counter() - t)
-        if time.perf_counter() > t_end:
-            break
-    return {k: min(v) for k, v in times.items()}, g
-
-
-def workload_config(W, args, world):
-    """The workload both arms report: grid, sizes, the timed pressures and the
-    GPU arm's solver settings."""
-    n = [(c - 1) * (1 << (W["levels"] - 1)) + 1 for c in W["n_coarse"]]
-    return {"workload": W["workload"], "grid": n, "levels": W["levels"],
-            "dofs": (W["dim"] + 1) * int(np.prod(n)), "fractures": W["fractures"],
-            "pressure_steps": [W["dp"] * t
-                               for t in range(args.warmup + 1, args.warmup + args.steps + 1)],
-            "precision": args.precision, "coarse_model": args.coarse_model, "start": args.start,
-            "parallelism": f"replicas{world}",
-            "l2": "working set > L2 (FP64 vectors 69 MB each, >20 resident)"}
-
-
-def oracle_seconds_per_load_step(pass_s, work):
-    return (pass_s["hessvec"] * work["fe_hessvec"] + pass_s["gradient"] * work["fe_gradient"]
-            + pass_s["energy"] * work["fe_energy"])
+# The FP64 oracle (numpy) is timed in a child process of this script
+# (`bench.py --oracle-worker SPEC`), so that its BLAS/OpenMP thread count can
+# be fixed before numpy loads: once at one thread and once at the default
+# (every core this process may use).  Nothing is scaled: each figure is the
+# wall time of what ran.
+THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
 
 
 def cpu_cores():
@@ -208,29 +193,144 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_state(W):
+    """The fractured initial state of workload W for the oracle."""
+    from oracle import pf_oracle as O
+    H = O.Hierarchy(3, W["n_coarse"], W["h_coarse"], W["levels"],
+                    O.Params(E=W["E"], nu=W["nu"], Gc=W["Gc"], p=W["dp"]),
+                    ls_over_h=W["ls_over_h"])
+    g = H.fine
+    x = np.zeros(4 * g.N)
+    x[3 * g.N:] = O.rasterize(g, O.DISC3D, PI.disc_network_3d(W["seed"], W["fractures"]), g.h)
+    return O, H, x
+
+
+def oracle_worker(spec):
+    """Runs inside the child process.  spec["kind"]:
+    - "load_steps": run steps k = 1 .. warmup untimed and k = warmup+1 ..
+      warmup+steps timed, each one whole oracle load step (Algorithm 1 V-cycles
+      to the stopping test) at ramp pressure dp * ramp_t(k);
+    - "passes": one hessvec, gradient and energy-difference pass each on the
+      full finest state of the workload."""
+    W = WORKLOAD_SMALL if spec["workload"] == "small" else WORKLOAD
+    O, H, x0 = oracle_state(W)
+    out = {"workload": W["workload"], "dofs": int(x0.size)}
+    if spec["kind"] == "load_steps":
+        x = x0.copy()
+        secs, energies, cycles = [], [], []
+        for k in range(1, spec["warmup"] + spec["steps"] + 1):
+            t = ramp_t(k)
+            if t == 1:
+                x = x0.copy()
+            t0 = time.perf_counter()
+            r = O.rmtr_load_step(H, x, p=W["dp"] * t)
+            dt = time.perf_counter() - t0
+            x = r.x
+            if k > spec["warmup"]:
+                secs.append(dt)
+                energies.append(r.energy)
+                cycles.append(r.cycles)
+        out.update(seconds=secs, energy=energies, cycles=cycles,
+                   pressures=[W["dp"] * ramp_t(k) for k in
+                              range(spec["warmup"] + 1, spec["warmup"] + spec["steps"] + 1)])
+    else:
+        g = H.fine
+        x = x0.copy()
+        x[:3 * g.N] = PI.random_direction(5, 3 * g.N, 1e-4)
+        v = PI.random_direction(6, x.size, 1e-4)
+        res = {}
+        for name, fn in (("hessvec", lambda: O.hessvec(g, H.prm, x, v)),
+                         ("gradient", lambda: O.gradient(g, H.prm, x)),
+                         ("energy_diff", lambda: O.energy_diff(g, H.prm, x, v))):
+            if name not in spec.get("passes", ("hessvec", "gradient", "energy_diff")):
+                continue
+            t0 = time.perf_counter()
+            fn()
+            dt = time.perf_counter() - t0
+            res[name] = {"seconds": dt, "gdofs": x.size / dt / 1e9}
+        out["passes"] = res
+    print("ORACLE_RESULT " + json.dumps(out))
+    return 0
+
+
+def run_oracle(spec, threads=None, timeout=1500):
+    """The oracle worker in a fresh child process; threads = 1 pins every
+    BLAS/OpenMP pool to one thread, None leaves the defaults (all cores)."""
+    env = dict(os.environ)
+    for k in THREAD_ENV:
+        env.pop(k, None)
+        if threads is not None:
+            env[k] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", json.dumps(spec)],
+                       env=env, capture_output=True, text=True, timeout=timeout)
+    for line in r.stdout.splitlines():
+        if line.startswith("ORACLE_RESULT "):
+            out = json.loads(line[len("ORACLE_RESULT "):])
+            out["threads"] = threads if threads is not None else cpu_cores()
+            return out
+    raise RuntimeError(f"oracle worker failed (rc {r.returncode}): {r.stderr[-2000:]}")
+
+
+def workload_config(W, args, world, **extra):
+    """The workload a line reports: grid, sizes, the timed pressures and the
+    solver settings."""
+    n = [(c - 1) * (1 << (W["levels"] - 1)) + 1 for c in W["n_coarse"]]
+    cfg = {"workload": W["workload"], "grid": n, "levels": W["levels"],
+           "dofs": (W["dim"] + 1) * int(np.prod(n)), "fractures": W["fractures"],
+           "ramp": f"p_t = {W['dp']} t, t = 1..{RAMP}; run step k solves t = (k-1) mod {RAMP} + 1, "
+                   "restarting from the fractured state at t = 1",
+           "pressure_steps": [W["dp"] * ramp_t(k)
+                              for k in range(args.warmup + 1, args.warmup + args.steps + 1)],
+           "parallelism": f"replicas{world}",
+           "l2": "working set > L2 (FP64 vectors 69 MB each, >20 resident)"}
+    cfg.update(extra)
+    return cfg
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper ships no code), run as it
+    stands on this machine's host cores.  A whole oracle load step of the
+    129^3 workload takes hours, so every step here is one whole oracle load
+    step of the same workload eight times coarser per axis (17^3, four
+    levels, the same discs, material and ramp), timed as it ran."""
     rank, world, _ = rank_info()
     if rank != 0:
         return 0
-    vals = []
-    sample = None
-    for _ in range(args.warmup):
-        oracle_pass_seconds(budget_s=0.0)
-    for _ in range(args.steps):
-        pass_s, g = oracle_pass_seconds(budget_s=0.0)
-        vals.append(oracle_seconds_per_load_step(pass_s, REF_WORK_MODEL))
-        sample = pass_s
-    v = statistics.median(vals)
+    W = WORKLOAD_SMALL
+    allc = run_oracle({"kind": "load_steps", "workload": "small", "warmup": args.warmup,
+                       "steps": args.steps})
+    one = run_oracle({"kind": "load_steps", "workload": "small", "warmup": 0, "steps": 2}, threads=1)
+    passes = run_oracle({"kind": "passes", "workload": "full"})
+    v = sum(allc["seconds"]) / args.steps
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(WORKLOAD, args, world),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                         "sample": ("one FP64 numpy oracle pass each of hessvec, gradient and energy "
-                                    "difference on the full 129^3 state per step, scaled by the CUDA path's "
-                                    f"finest-equivalent passes per load step {REF_WORK_MODEL}"),
-                         "pass_seconds": sample},
+        "data": "synthetic",
+        "config": workload_config(W, args, world, precision="fp64", start="plain",
+                                  coarse_model="first_order", solver="FP64 numpy oracle",
+                                  l2="host CPU run (no GPU)"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": allc["threads"], "kind": "oracle",
+                         "cpu": cpu_model(), "nproc": os.cpu_count(),
+                         "sample": (f"{args.steps} whole oracle load steps (after {args.warmup} untimed) of "
+                                    f"{W['workload']} ({allc['dofs']} dofs), default BLAS threads; "
+                                    "nothing scaled"),
+                         "seconds": allc["seconds"], "cycles": allc["cycles"],
+                         "one_thread": {"seconds": one["seconds"], "pressures": one["pressures"],
+                                        "value": sum(one["seconds"]) / len(one["seconds"])},
+                         "passes_129": {"threads": passes["threads"], **passes["passes"]}},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -289,6 +389,47 @@ def nvtx_range(name):
         return contextlib.nullcontext()
 
 
+def undetermined_nodes(c, n):
+    """Nodes whose every element has c = 1 at all eight corners: g(c) = 0 at
+    every Gauss point around them, so their displacements carry no energy
+    and any value minimises (such dofs are left out of field comparisons)."""
+    import torch
+    full = (c.view(n[2], n[1], n[0]) == 1.0)
+    e = torch.ones(n[2] + 1, n[1] + 1, n[0] + 1, dtype=torch.bool, device=c.device)
+    inner = full[:-1, :-1, :-1].clone()
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                inner &= full[dz:dz + n[2] - 1, dy:dy + n[1] - 1, dx:dx + n[0] - 1]
+    e[1:-1, 1:-1, 1:-1] = inner
+    und = torch.ones(n[2], n[1], n[0], dtype=torch.bool, device=c.device)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                und &= e[dz:dz + n[2], dy:dy + n[1], dx:dx + n[0]]
+    return und.reshape(-1)
+
+
+def field_errors(xm, xf, n):
+    """Per-field error of the state xm against the FP64 state xf: the largest
+    absolute difference, that over the field's max-norm, and the relative L2
+    error, on every determined dof (undetermined displacements excluded)."""
+    N = int(np.prod(n))
+    und = undetermined_nodes(xf[3 * N:], n)
+    out = {"undetermined_nodes": int(und.sum())}
+    for f, name in enumerate(("u_x", "u_y", "u_z", "c")):
+        a, b = xm[f * N:(f + 1) * N], xf[f * N:(f + 1) * N]
+        d = (a - b)
+        if f < 3:
+            d = d.masked_fill(und, 0.0)
+            b = b.masked_fill(und, 0.0)
+        bmax = float(b.abs().max())
+        dmax = float(d.abs().max())
+        out[name] = {"max_abs": dmax, "max_rel": dmax / bmax if bmax > 0 else dmax,
+                     "rel_l2": float(d.norm()) / max(float(b.norm()), 1e-300)}
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = rank_info()
@@ -307,81 +448,104 @@ def run_ours(args):
         W["n_coarse"] = [args.coarse_n] * 3
         W["h_coarse"] = 1.0 / (args.coarse_n - 1)
         W["workload"] = f"3d_{8 * (args.coarse_n - 1) + 1}^3_q1_4level_20discs_ramp"
-    prm = pf.default_params(
-        precision=pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64,
-        coarse_model=pf.PF_GALERKIN if args.coarse_model == "galerkin" else pf.PF_FIRST_ORDER,
-        start=pf.PF_START_EXTRAPOLATE if args.start == "extrapolate" else pf.PF_START_PLAIN)
-    H = pf.mesh_hierarchy_create(3, W["n_coarse"], W["levels"], W["h_coarse"], E=W["E"],
-                                 nu=W["nu"], Gc=W["Gc"], ls_over_h=W["ls_over_h"])
+    prec = pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64
+    cmodel = pf.PF_GALERKIN if args.coarse_model == "galerkin" else pf.PF_FIRST_ORDER
+    start = pf.PF_START_EXTRAPOLATE if args.start == "extrapolate" else pf.PF_START_PLAIN
+
+    def make(Wx):
+        Hx = pf.mesh_hierarchy_create(3, Wx["n_coarse"], Wx["levels"], Wx["h_coarse"], E=Wx["E"],
+                                      nu=Wx["nu"], Gc=Wx["Gc"], ls_over_h=Wx["ls_over_h"])
+        xx = torch.zeros(Hx.ndof(), dtype=torch.float64, device="cuda")
+        pf.fractures_set(Hx, pf.PF_DISC3D, PI.disc_network_3d(Wx["seed"], Wx["fractures"]),
+                         Hx.levels[-1][1], xx)
+        return Hx, xx
+
+    H, x = make(W)
     g_n, g_h, N = H.levels[-1]
     ndof = H.ndof()
-    x = torch.zeros(ndof, dtype=torch.float64, device="cuda")
-    rows = PI.disc_network_3d(W["seed"], W["fractures"])
-    pf.fractures_set(H, pf.PF_DISC3D, rows, g_h, x)
+    x_frac = x.clone()  # the fractured initial state every ramp starts from
     stream = torch.cuda.current_stream()
 
     if args.kernels_only:
         return kernels_only(pf, B, H, x, W)
 
-    def load_step(t, xx):
-        pf.pressure_set(H, W["dp"] * t)
-        return pf.rmtr_load_step(H, xx, prm, check=False)
+    def params(precision, st, t, dp):
+        """Parameters of ramp step t: the previous ramp pressure names the
+        extrapolation's base, so every arm extrapolates alike."""
+        return pf.default_params(precision=precision, coarse_model=cmodel, start=st,
+                                 p_prev=dp * (t - 1) if t > 1 else 0.0)
 
-    for t in range(1, args.warmup + 1):
-        st = load_step(t, x)
+    def load_step(Hx, xx, xfrac, k, precision, st, dp):
+        t = ramp_t(k)
+        if t == 1:
+            xx.copy_(xfrac)
+        pf.pressure_set(Hx, dp * t)
+        return pf.rmtr_load_step(Hx, xx, params(precision, st, t, dp), check=False)
+
+    first, last = args.warmup + 1, args.warmup + args.steps
+    for k in range(1, args.warmup + 1):
+        load_step(H, x, x_frac, k, prec, start, W["dp"])
     x_after_warmup = x.clone()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     stats = []
-    e0.record(stream)
+    ev[0].record(stream)
     with nvtx_range("timed_load_steps"):  # ncu --nvtx-include "timed_load_steps/"
-        for t in range(args.warmup + 1, args.warmup + args.steps + 1):
-            stats.append(load_step(t, x))
-    e1.record(stream)
+        for j, k in enumerate(range(first, last + 1)):
+            stats.append(load_step(H, x, x_frac, k, prec, start, W["dp"]))
+            ev[j + 1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    slowest_s, job_s = job_seconds_per_load_step(e0.elapsed_time(e1) / args.steps / 1e3, dist,
-                                                 "cuda")
+    step_s = [ev[j].elapsed_time(ev[j + 1]) * 1e-3 for j in range(args.steps)]
+    slowest_s, job_s = job_seconds_per_load_step(ev[0].elapsed_time(ev[-1]) / args.steps / 1e3,
+                                                 dist, "cuda")
     ms = slowest_s * 1e3
     if dist:
         dist.barrier()
 
-    # ---- dominant kernel: Hessian-vector product at the finest level
-    v = torch.from_numpy(PI.random_direction(77, ndof, 1e-3)).cuda()
-    out = torch.empty_like(v)
+    # ---- dominant kernel: Hessian-vector product at the finest level.
+    # Launches rotate over four independent operand sets (together well
+    # above L2), so no launch finds its inputs in L2.
+    level = W["levels"] - 1
+    vs = [torch.from_numpy(PI.random_direction(77 + i, ndof, 1e-3)).cuda() for i in range(4)]
+    outs = [torch.empty_like(vs[0]) for _ in range(4)]
+    xs32 = [(x + 1e-6 * vs[(i + 1) % 4]).float() for i in range(4)]
+    vs32 = [v.float() for v in vs]
+    os32 = [torch.empty_like(vs32[0]) for _ in range(4)]
 
     def time_kernel(fn, reps=20):
-        for _ in range(3):
-            fn()
+        for i in range(4):
+            fn(i)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(reps):
-            fn()
+        for r in range(reps):
+            fn(r % 4)
         b.record(stream)
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps * 1e-3
 
-    level = W["levels"] - 1
     pf.hessvec_lag_set(H, level, x)  # the solver's FP64 operator: stored lagged coefficients
-    t64 = time_kernel(lambda: pf.hessvec_lagged(H, level, v, out))
-    x32, v32 = x.float(), v.float()
-    o32 = torch.empty_like(v32)
-    t32 = time_kernel(lambda: pf.hessvec(H, level, x32, v32, o32))
-    t_grad = time_kernel(lambda: pf.gradient(H, level, x, out))
+    kclocks = Clocks(local)
+    kclocks.start()
+    t64 = time_kernel(lambda i: pf.hessvec_lagged(H, level, vs[i], outs[i]))
+    t32 = time_kernel(lambda i: pf.hessvec(H, level, xs32[i], vs32[i], os32[i]), reps=40)
+    t_grad = time_kernel(lambda i: pf.gradient(H, level, x, outs[i]))
+    kclk = kclocks.stop()
     fma64 = B.probe_fma(pf.PF_FP64)
     fma32 = B.probe_fma(pf.PF_FP32)
-    hbm = None
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
         hbm_src = "measured"
     except (OSError, KeyError, ValueError):
         hbm, hbm_src = 6800.0, "fallback"
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = kclk["sm_mhz"] or clk["sm_mhz"] or 2070.0
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     # FP64 lagged Hessian = the assembled 27-point block stencil: it reads the
     # stencil (27 x 4 x 4 doubles per node) and v, and writes Hv
     bytes64 = (27 * 16 * 8 + 2 * 4 * 8) * N
@@ -393,85 +557,151 @@ def run_ours(args):
               "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
               "flop_per_node": 864, "fp64_fma_peak_tflops": fma64 / 1e12,
               "gdofs": ndof / t64 / 1e9, "us_per_launch": t64 * 1e6}
-    # The FP32 product is bound by FP32 issue (FMA pipe ~67 % busy, DRAM ~10 %):
-    # ALU roofline, algorithmic flops = FLOP32_PER_ELEMENT x elements
+    # The FP32 product is bound by FP32 issue: ALU roofline, algorithmic
+    # flops = FLOP32_PER_ELEMENT x elements
     ne = (g_n[0] - 1) * (g_n[1] - 1) * (g_n[2] - 1)
     flops32 = FLOP32_PER_ELEMENT * ne
     roof32 = {"kernel": "hessvec_fp32", "bound": "alu", "achieved": flops32 / t32 / 1e12,
-              "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-              "frac": flops32 / t32 / 1e12 / FP32_PEAK_TFLOPS,
+              "peak": fp32_peak, "unit": "TFLOP/s",
+              "frac": flops32 / t32 / 1e12 / fp32_peak,
               # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
               # the product's two kernels
               "traffic": TRAFFIC_HESSVEC_FP32,
-              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+              "peak_source": (f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                              f"{sm_mhz:.0f} MHz (median SM clock sampled while the kernels ran)"),
               "fp32_fma_probe_tflops": fma32 / 1e12,
               "flop_per_element": FLOP32_PER_ELEMENT,
               "hbm_achieved_gbs": bytes32 / t32 / 1e9, "hbm_peak_gbs": hbm,
-              "gdofs": ndof / t32 / 1e9, "us_per_launch": t32 * 1e6}
+              "hbm_frac": bytes32 / t32 / 1e9 / hbm,
+              "gdofs": ndof / t32 / 1e9, "us_per_launch": t32 * 1e6,
+              "operands": "4 rotating operand sets (x_lag, v, Hv), 412 MB, above L2"}
     roofline = roof64 if args.precision == "fp64" else roof32
 
-    def with_p_prev(p_src, t):
-        """Parameters of timed step t: the first one names the warm-up's last
-        pressure so an extrapolated start scales as in the timed run."""
-        q = pf.default_params(**{k: getattr(p_src, k) for k, _ in p_src._fields_})
-        if t == args.warmup + 1:
-            q.p_prev = W["dp"] * args.warmup
-        return q
+    # ---- the metric's comparison: the same ramp steps from the same warmed
+    # state in plain FP64 (plain start) and in mixed precision with the plain
+    # start, beside a re-run of the headline's own steps (bitwise the same
+    # solves: the solver is deterministic) whose states give the per-field
+    # error of the mixed fields against the FP64 fields at every step.
+    cmp = None
+    if not args.no_compare:
+        n_cmp = min(args.steps, RAMP)
+        ks = list(range(first, first + n_cmp))
 
-    def compare(p_cmp):
-        """The same K timed load steps from the same warmed-up state with
-        other parameters."""
-        xc = x_after_warmup.clone()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sc = []
-        for t in range(args.warmup + 1, args.warmup + args.steps + 1):
-            pf.pressure_set(H, W["dp"] * t)
-            sc.append(pf.rmtr_load_step(H, xc, with_p_prev(p_cmp, t), check=False))
-        b.record(stream)
-        torch.cuda.synchronize()
-        ec = [s["energy"] for s in sc]
-        eh = [s["energy"] for s in stats]
-        return {"value": a.elapsed_time(b) / args.steps / 1e3, "unit": UNIT,
-                "speedup_of_headline": a.elapsed_time(b) / args.steps / ms,
-                "energy_rel_diff": max(abs(p - q) / abs(q) for p, q in zip(eh, ec)),
-                "cycles": [s["cycles"] for s in sc], "status": [s["status"] for s in sc]}
+        def arm(precision, st, keep=False):
+            xx = x_after_warmup.clone()
+            torch.cuda.synchronize()
+            secs, sts, states = [], [], []
+            for k in ks:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sts.append(load_step(H, xx, x_frac, k, precision, st, W["dp"]))
+                b.record(stream)
+                torch.cuda.synchronize()
+                secs.append(a.elapsed_time(b) * 1e-3)
+                if keep:
+                    states.append(xx.clone())
+            return secs, sts, states, xx
 
-    fp64_cmp = mixed_plain = None
-    if args.compare_fp64:
-        fp64_cmp = compare(pf.default_params(precision=pf.PF_FP64, coarse_model=prm.coarse_model,
-                                             start=pf.PF_START_PLAIN))
-        if args.precision == "mixed" and args.start != "plain":
-            mixed_plain = compare(pf.default_params(precision=pf.PF_FP32, coarse_model=prm.coarse_model,
-                                                    start=pf.PF_START_PLAIN))
+        m_s, m_st, m_states, _ = arm(prec, start, keep=True)
+        f_s, f_st, f_states, _ = arm(pf.PF_FP64, pf.PF_START_PLAIN, keep=True)
+        p_s, p_st, _, _ = arm(pf.PF_FP32, pf.PF_START_PLAIN)
+        errs = [field_errors(a, b, g_n) for a, b in zip(m_states, f_states)]
+        del m_states, f_states
+        worst = {f: {m: max(e[f][m] for e in errs) for m in ("max_abs", "max_rel", "rel_l2")}
+                 for f in ("u_x", "u_y", "u_z", "c")}
+        mixed_mean = sum(m_s) / n_cmp
+        fp64_mean = sum(f_s) / n_cmp
+        cmp = {
+            "steps": ks, "pressures": [W["dp"] * ramp_t(k) for k in ks],
+            "fp64_plain": {"value": fp64_mean, "unit": UNIT, "seconds": f_s,
+                           "cycles": [s["cycles"] for s in f_st], "status": [s["status"] for s in f_st],
+                           "energy": [s["energy"] for s in f_st]},
+            "mixed_plain_start": {"value": sum(p_s) / n_cmp, "unit": UNIT, "seconds": p_s,
+                                  "cycles": [s["cycles"] for s in p_st]},
+            "headline_same_steps": {"value": mixed_mean, "unit": UNIT, "seconds": m_s,
+                                    "cycles": [s["cycles"] for s in m_st],
+                                    "bitwise_as_timed": all(a["energy"] == b["energy"]
+                                                            for a, b in zip(m_st, stats))},
+            "fp64_plain_over_headline": fp64_mean / mixed_mean,
+            "energy_rel_diff": max(abs(a["energy"] - b["energy"]) / abs(b["energy"])
+                                   for a, b in zip(m_st, f_st)),
+            "field_error_vs_fp64": {"per_step": errs, "worst": worst},
+        }
 
     # ---- end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
         xh = torch.empty(ndof, dtype=torch.float64, pin_memory=True)
         xh.copy_(x_after_warmup.cpu())
+        xfh = x_frac.cpu().numpy()
         xn = xh.numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for t in range(args.warmup + 1, args.warmup + args.steps + 1):
+        for k in range(first, last + 1):
+            t = ramp_t(k)
+            if t == 1:
+                xn[:] = xfh
             pf.pressure_set(H, W["dp"] * t)
-            pf.rmtr_load_step_host(H, xn, with_p_prev(prm, t), check=False)
+            pf.rmtr_load_step_host(H, xn, params(prec, start, t, W["dp"]), check=False)
         _, e2e_s = job_seconds_per_load_step((time.perf_counter() - t0) / args.steps, dist, "cuda")
         e2e = {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * ndof,
                "d2h_bytes_per_step": 8 * ndof}
 
-    work = {k: statistics.mean(s[k] for s in stats) for k in ("fe_hessvec", "fe_gradient", "fe_energy")}
+    # ---- the FP64 oracle on this machine's host cores (rank 0 at N = 1):
+    # whole oracle load steps of the 17^3 workload and one pass each at
+    # 129^3, timed as they ran, beside the GPU on the same 17^3 steps
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pass_s, _ = oracle_pass_seconds(budget_s=10.0)
-        cpu = {"value": oracle_seconds_per_load_step(pass_s, work), "unit": UNIT,
-               "cores": cpu_cores(), "kind": "oracle",
-               "sample": ("FP64 numpy oracle: one hessvec, gradient and energy-difference pass on the "
-                          "full 129^3 state (best of repeats within 10 s), scaled by this run's "
-                          "finest-equivalent passes per load step"),
-               "pass_seconds": pass_s}
+        n_s = 3
+        allc = run_oracle({"kind": "load_steps", "workload": "small", "warmup": 0, "steps": n_s})
+        one = run_oracle({"kind": "load_steps", "workload": "small", "warmup": 0, "steps": 1},
+                         threads=1)
+        pass_all = run_oracle({"kind": "passes", "workload": "full"})
+        pass_one = run_oracle({"kind": "passes", "workload": "full", "passes": ["hessvec"]},
+                              threads=1)
+        Hs, xs_ = make(WORKLOAD_SMALL)
+        xs_frac = xs_.clone()
+        gpu_small = {}
+        for name, pr, st in (("headline", prec, start), ("fp64_plain", pf.PF_FP64, pf.PF_START_PLAIN)):
+            for k in range(1, n_s + 1):  # warm-up: graphs and lag buffers of this hierarchy
+                load_step(Hs, xs_, xs_frac, k, pr, st, WORKLOAD_SMALL["dp"])
+            secs, en = [], []
+            for k in range(1, n_s + 1):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s_ = load_step(Hs, xs_, xs_frac, k, pr, st, WORKLOAD_SMALL["dp"])
+                b.record(stream)
+                torch.cuda.synchronize()
+                secs.append(a.elapsed_time(b) * 1e-3)
+                en.append(s_["energy"])
+            gpu_small[name] = {"seconds": secs, "value": sum(secs) / n_s, "energy": en}
+        Hs.close()
+        v_or = sum(allc["seconds"]) / n_s
+        cpu = {"value": v_or, "unit": UNIT, "cores": allc["threads"], "kind": "oracle",
+               "cpu": cpu_model(), "nproc": os.cpu_count(),
+               "sample": (f"whole FP64 oracle load steps t = 1..{n_s} of {WORKLOAD_SMALL['workload']} "
+                          f"({allc['dofs']} dofs: the timed workload eight times coarser per axis), "
+                          "default BLAS threads, timed as they ran (nothing scaled); plus one "
+                          "hessvec / gradient / energy-difference pass on the full 129^3 state"),
+               "seconds": allc["seconds"], "cycles": allc["cycles"],
+               "one_thread": {"seconds": one["seconds"], "value": one["seconds"][0]},
+               "passes_129": {"all_cores": {"threads": pass_all["threads"], **pass_all["passes"]},
+                              "one_thread": pass_one["passes"]},
+               "equal_work_17": {
+                   "workload": WORKLOAD_SMALL["workload"], "pressures": allc["pressures"],
+                   "oracle": v_or, "gpu_headline": gpu_small["headline"]["value"],
+                   "gpu_fp64_plain": gpu_small["fp64_plain"]["value"],
+                   "oracle_over_gpu_headline": v_or / gpu_small["headline"]["value"],
+                   "oracle_over_gpu_fp64_plain": v_or / gpu_small["fp64_plain"]["value"],
+                   "fp64_energy_rel_diff_vs_oracle": max(
+                       abs(a - b) / abs(b) for a, b in zip(gpu_small["fp64_plain"]["energy"],
+                                                            allc["energy"])),
+                   "headline_energy_rel_diff_vs_oracle": max(
+                       abs(a - b) / abs(b) for a, b in zip(gpu_small["headline"]["energy"],
+                                                            allc["energy"]))},
+               "hessvec_129_gpu_fp32_over_oracle": (pass_all["passes"]["hessvec"]["seconds"] / t32)}
 
     launches = int(sum(s["launches"] for s in stats))
     value = job_s
@@ -482,18 +712,22 @@ def run_ours(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f64+f32",
             "data": "synthetic",
-            "config": workload_config(W, args, world),
+            "config": workload_config(
+                W, args, world, precision=args.precision, coarse_model=args.coarse_model,
+                start=args.start if args.start == "plain" else
+                "extrapolate (the learned iterate's zero-output predictor; the network is 2D)"),
+            "seconds_per_step": step_s,
             "roofline": roofline,
             "roofline_other": roof32 if roofline is roof64 else roof64,
             "hessvec_gdofs": {"fp64": ndof / t64 / 1e9, "fp32": ndof / t32 / 1e9},
             "gradient_fp64_us": t_grad * 1e6,
-            "fp64_plain": fp64_cmp,
-            "mixed_plain_start": mixed_plain,
+            "fp64_plain": cmp["fp64_plain"] if cmp else None,
+            "compare": cmp,
             "clocks": clk,
+            "kernel_clocks": kclk,
             "e2e": e2e,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
-            "work_model": work,
             "solver": {k: [s[k] for s in stats] for k in ("cycles", "converged", "cg", "tr_its",
                                                           "tr_rejected", "coarse_rejected", "status",
                                                           "hv_cauchy", "hv_search", "cg_restarts",
@@ -571,6 +805,8 @@ def run_batched(args):
 
 def main():
     args = parse()
+    if args.oracle_worker:
+        return oracle_worker(json.loads(args.oracle_worker))
     if args.impl == "reference":
         return run_reference(args)
     if args.batched:
