@@ -892,6 +892,31 @@ def vcycle(H: Hierarchy, level, model: LevelModel, x0, lb, ub, delta0, tr: TRPar
     return x, delta
 
 
+def trust_region_gate(H: Hierarchy, x, xhat, eta):
+    """Acceptance of a proposed iterate xhat at the current pressure by the
+    trust-region ratio of eq. (rho_tr) and Algorithm 3's acceptance test
+    (rho > eta1), as the learned initial iterate uses it (the paper has no
+    learned part; the ratio and the test are the paper's):
+    c_prev := c of x; s = P_F(xhat) - x with F the feasible set of
+    eq. (space_pf) (c_prev <= c <= 1, clamped u); actual = E(x) - E(x + s),
+    evaluated as the exact quartic expansion along s like every ratio here
+    (the plain difference of two energies of size 1 loses the digits of a
+    reduction of size 1e-7); predicted = -(grad E(x).s + s.H(x)s / 2);
+    rho = actual / predicted
+    (-inf when predicted <= 0); accepted when rho > eta and actual > 0.
+    Returns (rho, accepted, the new x)."""
+    d, N = H.dim, H.fine.N
+    H.c_prev = x[d * N:].copy()
+    lb, ub = H.fine_bounds()
+    s = np.minimum(np.maximum(xhat, lb), ub) - x
+    g = H.fine
+    actual = -energy_diff(g, H.prm, x, s)
+    pred = -(float(gradient(g, H.prm, x) @ s) + 0.5 * float(s @ hessvec(g, H.prm, x, s)))
+    rho = actual / pred if pred > 0.0 else -math.inf
+    acc = bool(rho > eta and actual > 0.0)
+    return rho, acc, (x + s if acc else x.copy())
+
+
 def projected_gradient_norm(x, g, lb, ub) -> float:
     """|| x - proj_F(x - grad f(x)) ||_2, the first-order criticality measure."""
     return float(np.linalg.norm(x - np.minimum(np.maximum(x - g, lb), ub)))

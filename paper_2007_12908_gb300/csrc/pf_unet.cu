@@ -1,7 +1,11 @@
 // Learned initial iterate: a 2D U-Net (4 levels, two 3x3 convolutions +
 // ReLU per level, 2x2 average pooling down, nearest 2x up, skip
-// concatenation, 1x1 head).  BF16 weights and activations, FP32 arithmetic
-// and accumulation, FP32 master weights and Adam moments.
+// concatenation, 1x1 head).  BF16 weights and activations, FP32 master
+// weights and Adam moments.  Every convolution (forward, data gradient,
+// weight gradient) is an implicit GEMM on the tensor cores with BF16
+// operands and FP32 accumulation; the data-gradient and weight-gradient
+// operand dL/d(out) (FP32) is staged as a BF16 pair hi + lo and multiplied
+// twice, keeping about 16 significant bits of the gradient.
 //
 // Convolutions read their input through a fused transform: the first
 // operand may be pooled (it lives at twice the resolution) or upsampled (it
@@ -51,188 +55,335 @@ __device__ __forceinline__ float conv_in(const ConvIn& in, int c, int y, int x, 
   return __bfloat162float(in.b[((long long)(c - in.ca) * H + y) * W + x]);
 }
 
-constexpr int TILE = 16, COB = 16, CIB = 8;
+// ---------------------------------------------------------------- tensor cores
+// The convolutions are implicit GEMMs on the tensor cores: BF16 operands,
+// FP32 accumulation, mma.sync.m16n8k16 (one warp-wide 16x8x16 product per
+// instruction).
+//
+// Forward:  out[co](p)  = sum_{ci, tap} w[co][ci][tap] in[ci](p + off(tap))
+//           (M = co, N = pixels, K = ci for each tap)
+// Data gradient: din[ci](p) = sum_{co, tap} w[co][ci][KK-1-tap] dpre[co](p + off(tap))
+//           (the same form with the weights transposed and flipped)
+// Weight gradient: dw[co][ci][tap] = sum_p dpre[co](p) in[ci](p + off(tap))
+//           (M = co, N = ci, K = pixels)
 
-// y[co] = relu?(b[co] + sum_ci sum_k w[co][ci][k] in[ci](y + dy, x + dx))
-// grid: (W/16, H/16, ceil(CO/16)), block 256 threads, one pixel each.
-template <int K>
-__global__ void __launch_bounds__(256) k_conv_fwd(ConvIn in, int H, int W, int CO,
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// 16 channels of one pixel (or one GEMM row) are 8 32-bit words; words 4..7
+// of rows whose bit 2 is set are swapped with words 0..3, so that the eight
+// rows a fragment load touches fall in distinct banks.
+__device__ __forceinline__ int swz(int row, int word) { return row * 8 + (word ^ (((row >> 2) & 1) << 2)); }
+
+// Operand sources of the forward / data-gradient kernel.
+struct MmaIn {
+  ConvIn conv;                     // forward: the fused input transform
+  const float* dout;               // data gradient: dL/d(out) (FP32) ...
+  const __nv_bfloat16* out;        // ... masked by out > 0 when relu
+  int relu;
+};
+
+template <bool DGRAD>
+__device__ __forceinline__ float mma_in_value(const MmaIn& s, int c, int Kc, int y, int x, int H,
+                                              int W) {
+  if (c >= Kc) return 0.f;
+  if constexpr (!DGRAD) {
+    return conv_in(s.conv, c, y, x, H, W);
+  } else {
+    if (y < 0 || y >= H || x < 0 || x >= W) return 0.f;
+    const long long o = ((long long)c * H + y) * W + x;
+    float v = s.dout[o];
+    if (s.relu && !(__bfloat162float(s.out[o]) > 0.f)) v = 0.f;
+    return v;
+  }
+}
+
+// grid: (W/16, H/16, ceil(M/MB)); 256 threads = 8 warps, warp w owns pixel
+// rows 2w, 2w+1 of the 16 x 16 tile (four 8-pixel n-tiles) and all MB rows.
+// Forward (DGRAD = false): M = CO rows co, Kc = CI, A[co][ci] =
+// w[co][ci][tap]; epilogue bias + ReLU, BF16 and/or FP32 output.
+// Data gradient: M = CI rows ci, Kc = CO, A[ci][co] = w[co][ci][KK-1-tap];
+// FP32 output, no bias.
+// The data gradient's operand dpre is FP32: it is staged as a BF16 pair
+// hi + lo (hi = bf16(v), lo = bf16(v - hi), about 16 significant bits) and
+// multiplied twice, so that the gradient keeps more than BF16 precision
+// through the layers; activations and weights are BF16 already.
+template <int K, int MB, bool DGRAD>
+__global__ void __launch_bounds__(256) k_conv_mma(MmaIn src, int H, int W, int M, int Kc, int CIw,
                                                   const __nv_bfloat16* __restrict__ w,
                                                   const float* __restrict__ bias, int relu,
                                                   __nv_bfloat16* __restrict__ out_bf,
                                                   float* __restrict__ out_f) {
-  constexpr int R = K / 2, T = TILE + 2 * R;
-  __shared__ float tile[CIB][T][T];
-  __shared__ float ws[COB][CIB][K * K];
-  const int CI = in.ca + in.cb;
-  const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
-  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE, co0 = blockIdx.z * COB;
-  float acc[COB];
+  constexpr int R = K / 2, T = 16 + 2 * R, KK = K * K, MT = MB / 16, NS = DGRAD ? 2 : 1;
+  __shared__ unsigned s_in[NS][T * T * 8];  // [pixel][16 channels] BF16 pairs, swizzled
+  __shared__ unsigned s_w[KK * MB * 8];     // [tap][row][16 channels]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int x0 = blockIdx.x * 16, y0 = blockIdx.y * 16, m0 = blockIdx.z * MB;
+  float acc[MT][4][4];
 #pragma unroll
-  for (int c = 0; c < COB; ++c) acc[c] = 0.f;
-  for (int ci0 = 0; ci0 < CI; ci0 += CIB) {
-    for (int i = threadIdx.x; i < CIB * T * T; i += 256) {
-      const int c = i / (T * T), r = i % (T * T);
-      const int yy = y0 + r / T - R, xx = x0 + r % T - R;
-      tile[c][r / T][r % T] = (ci0 + c < CI) ? conv_in(in, ci0 + c, yy, xx, H, W) : 0.f;
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  for (int k0 = 0; k0 < Kc; k0 += 16) {
+    for (int i = threadIdx.x; i < T * T * 8; i += 256) {
+      const int q = i % (T * T), j = i / (T * T);
+      const int yy = y0 - R + q / T, xx = x0 - R + q % T;
+      const float v0 = mma_in_value<DGRAD>(src, k0 + 2 * j, Kc, yy, xx, H, W);
+      const float v1 = mma_in_value<DGRAD>(src, k0 + 2 * j + 1, Kc, yy, xx, H, W);
+      s_in[0][swz(q, j)] = pack_bf16(v0, v1);
+      if constexpr (DGRAD)
+        s_in[1][swz(q, j)] = pack_bf16(v0 - __bfloat162float(__float2bfloat16(v0)),
+                                       v1 - __bfloat162float(__float2bfloat16(v1)));
     }
-    for (int i = threadIdx.x; i < COB * CIB * K * K; i += 256) {
-      const int co = i / (CIB * K * K), rem = i % (CIB * K * K);
-      const int c = rem / (K * K), k = rem % (K * K);
-      ws[co][c][k] = (co0 + co < CO && ci0 + c < CI)
-                         ? __bfloat162float(w[((long long)(co0 + co) * CI + ci0 + c) * K * K + k])
-                         : 0.f;
-    }
-    __syncthreads();
+    for (int i = threadIdx.x; i < KK * MB * 8; i += 256) {
+      const int j = i & 7, row = (i >> 3) % MB, tap = i / (8 * MB);
+      const int m = m0 + row;
+      float v[2];
 #pragma unroll
-    for (int c = 0; c < CIB; ++c)
-#pragma unroll
-      for (int k = 0; k < K * K; ++k) {
-        const float v = tile[c][ty + k / K][tx + k % K];
-#pragma unroll
-        for (int co = 0; co < COB; ++co) acc[co] = fmaf(ws[co][c][k], v, acc[co]);
+      for (int h = 0; h < 2; ++h) {
+        const int kc = k0 + 2 * j + h;
+        v[h] = 0.f;
+        if (m < M && kc < Kc) {
+          // forward: w[m][kc][tap]; data gradient: w[kc][m][KK-1-tap]
+          const long long o = DGRAD ? ((long long)kc * CIw + m) * KK + (KK - 1 - tap)
+                                    : ((long long)m * CIw + kc) * KK + tap;
+          v[h] = __bfloat162float(w[o]);
+        }
       }
+      s_w[tap * MB * 8 + swz(row, j)] = pack_bf16(v[0], v[1]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int tap = 0; tap < KK; ++tap) {
+      const int ky = tap / K, kx = tap % K;
+#pragma unroll
+      for (int part = 0; part < NS; ++part) {
+        unsigned bfr[4][2];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const int py = 2 * warp + (nt >> 1), px = (nt & 1) * 8 + g;
+          const int q = (py + ky) * T + px + kx;
+          bfr[nt][0] = s_in[part][swz(q, t4)];
+          bfr[nt][1] = s_in[part][swz(q, t4 + 4)];
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          const unsigned* sw = s_w + tap * MB * 8;
+          const int r0 = mt * 16 + g, r1 = r0 + 8;
+          const unsigned a[4] = {sw[swz(r0, t4)], sw[swz(r1, t4)], sw[swz(r0, t4 + 4)],
+                                 sw[swz(r1, t4 + 4)]};
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a, bfr[nt][0], bfr[nt][1]);
+        }
+      }
+    }
     __syncthreads();
   }
-  const int y = y0 + ty, x = x0 + tx;
-  if (y >= H || x >= W) return;
+  // epilogue: c0 (row g, pixel 2t), c1 (row g, 2t+1), c2 (row g+8, 2t), c3 (row g+8, 2t+1)
 #pragma unroll
-  for (int co = 0; co < COB; ++co) {
-    if (co0 + co >= CO) break;
-    float v = acc[co] + bias[co0 + co];
-    if (relu) v = fmaxf(v, 0.f);
-    const long long o = ((long long)(co0 + co) * H + y) * W + x;
-    if (out_bf) out_bf[o] = __float2bfloat16(v);
-    if (out_f) out_f[o] = v;
-  }
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int y = y0 + 2 * warp + (nt >> 1);
+      const int xb = x0 + (nt & 1) * 8 + 2 * t4;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = m0 + mt * 16 + g + 8 * h;
+        if (m >= M || y >= H) continue;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int x = xb + e;
+          if (x >= W) continue;
+          float v = acc[mt][nt][2 * h + e];
+          if (!DGRAD) {
+            v += bias[m];
+            if (relu) v = fmaxf(v, 0.f);
+          }
+          const long long o = ((long long)m * H + y) * W + x;
+          if (out_bf) out_bf[o] = __float2bfloat16(v);
+          if (out_f) out_f[o] = v;
+        }
+      }
+    }
 }
 
-// Data gradient: dIn[ci](y, x) = sum_co sum_k w[co][ci][k] dpre[co](y - dy, x - dx),
-// dpre = dout * (out > 0) when the layer has a ReLU.  Written FP32 on the
-// conv's own grid (the virtual concatenated input).
-template <int K>
-__global__ void __launch_bounds__(256) k_conv_dgrad(const float* __restrict__ dout,
-                                                    const __nv_bfloat16* __restrict__ out, int relu,
-                                                    int H, int W, int CO, int CI,
-                                                    const __nv_bfloat16* __restrict__ w,
-                                                    float* __restrict__ din) {
-  constexpr int R = K / 2, T = TILE + 2 * R;
-  __shared__ float tile[CIB][T][T];
-  __shared__ float ws[COB][CIB][K * K];  // [ci][co][k], flipped taps
-  const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
-  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE, ci0 = blockIdx.z * COB;
-  float acc[COB];
-#pragma unroll
-  for (int c = 0; c < COB; ++c) acc[c] = 0.f;
-  for (int co0 = 0; co0 < CO; co0 += CIB) {
-    for (int i = threadIdx.x; i < CIB * T * T; i += 256) {
-      const int c = i / (T * T), r = i % (T * T);
-      const int yy = y0 + r / T - R, xx = x0 + r % T - R;
-      float v = 0.f;
-      if (co0 + c < CO && yy >= 0 && yy < H && xx >= 0 && xx < W) {
-        const long long o = ((long long)(co0 + c) * H + yy) * W + xx;
-        v = dout[o];
-        if (relu && !(__bfloat162float(out[o]) > 0.f)) v = 0.f;
-      }
-      tile[c][r / T][r % T] = v;
-    }
-    for (int i = threadIdx.x; i < COB * CIB * K * K; i += 256) {
-      const int ci = i / (CIB * K * K), rem = i % (CIB * K * K);
-      const int c = rem / (K * K), k = rem % (K * K);
-      ws[ci][c][k] = (ci0 + ci < CI && co0 + c < CO)
-                         ? __bfloat162float(w[((long long)(co0 + c) * CI + ci0 + ci) * K * K + (K * K - 1 - k)])
-                         : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < CIB; ++c)
-#pragma unroll
-      for (int k = 0; k < K * K; ++k) {
-        const float v = tile[c][ty + k / K][tx + k % K];
-#pragma unroll
-        for (int ci = 0; ci < COB; ++ci) acc[ci] = fmaf(ws[ci][c][k], v, acc[ci]);
-      }
-    __syncthreads();
-  }
-  const int y = y0 + ty, x = x0 + tx;
-  if (y >= H || x >= W) return;
-#pragma unroll
-  for (int ci = 0; ci < COB; ++ci) {
-    if (ci0 + ci >= CI) break;
-    din[((long long)(ci0 + ci) * H + y) * W + x] = acc[ci];
-  }
-}
+// Weight gradient partials on the tensor cores.  grid: (ceil(CI/NB),
+// ceil(CO/MB), P); chunk p covers pixel rows [p rows_per, (p+1) rows_per).
+// The CTA stages, per 16 x 16 pixel tile, dpre for its MB output channels
+// (A rows; K = the 16 pixels of a tile row) and the fused input for its NB
+// input channels (three copies shifted by kx, so that every pixel pair a
+// fragment reads is 4-byte aligned).  Per-channel strides are padded by 4
+// words so the eight rows of a fragment fall in distinct banks.  Warp w
+// accumulates the (m-tile, n-tile, tap) products w, w+8, ...; the bias
+// gradient sums the FP32 dpre of each channel (warp w: channels w, w+8, ...)
+// lane-wise and by a fixed shuffle tree.  Every sum runs over the pixels in
+// a fixed order, so the partials are deterministic.
+template <int K, int MB, int NB>
+struct WgradSmem {
+  static constexpr int R = K / 2, YT = 16 + 2 * R;
+  static constexpr int SD = 16 * 8 + 4, SX = YT * 8 + 4;
+  static constexpr size_t bytes = sizeof(unsigned) * (2 * size_t(MB) * SD + size_t(K) * NB * SX);
+};
 
-// Weight gradient partials: part[p][co][ci][k] = sum over the pixel rows of
-// chunk p of dpre[co](y, x) in[ci](y + dy, x + dx), and part_b[p][co] = sum
-// of dpre.  grid: (ceil(CI/8), ceil(CO/8), P) blocks of 256 threads; the
-// 8 x 8 x K*K (co, ci, tap) triples of a block are dealt round-robin to the
-// threads (up to NT each), and every sum runs over pixels in a fixed order.
-constexpr int WG_C = 8;
-template <int K>
-__global__ void __launch_bounds__(256) k_conv_wgrad(const float* __restrict__ dout,
-                                                    const __nv_bfloat16* __restrict__ out, int relu,
-                                                    ConvIn in, int H, int W, int CO, int rows_per,
-                                                    float* __restrict__ part, float* __restrict__ part_b) {
-  constexpr int R = K / 2, T = TILE + 2 * R;
-  constexpr int NTRI = WG_C * WG_C * K * K, NT = (NTRI + 255) / 256;
+template <int K, int MB, int NB>
+__global__ void __launch_bounds__(256) k_conv_wgrad_mma(const float* __restrict__ dout,
+                                                        const __nv_bfloat16* __restrict__ out,
+                                                        int relu, ConvIn in, int H, int W, int CO,
+                                                        int rows_per, float* __restrict__ part,
+                                                        float* __restrict__ part_b) {
+  using S = WgradSmem<K, MB, NB>;
+  constexpr int R = S::R, YT = S::YT, SD = S::SD, SX = S::SX, KK = K * K;
+  constexpr int MT = MB / 16, NT = NB / 8;
+  constexpr int COMBOS = MT * NT * KK, PER = (COMBOS + 7) / 8, BPW = MB / 8;
+  extern __shared__ unsigned smem_u[];
+  unsigned* s_d = smem_u;             // [2][MB][SD] (hi, lo): row r, pixel pair wd at r * 8 + wd
+  unsigned* s_x = s_d + 2 * MB * SD;  // [K][NB][SX]: row r, pixel pair wd at r * 8 + wd
   const int CI = in.ca + in.cb;
-  const int ci0 = blockIdx.x * WG_C, co0 = blockIdx.y * WG_C, p = blockIdx.z;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  const int n0 = blockIdx.x * NB, m0 = blockIdx.y * MB, p = blockIdx.z;
   const int y_lo = p * rows_per, y_hi = min(H, y_lo + rows_per);
-  __shared__ float sd[WG_C][TILE * TILE];
-  __shared__ float sx[WG_C][T * T];
-  const int t = threadIdx.x;
-  float acc[NT];
+  float acc[PER][4];
 #pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j] = 0.f;
-  float accb = 0.f;  // bias sum of output channel co0 + t (threads t < 8)
-  for (int yb = y_lo; yb < y_hi; yb += TILE)
-    for (int xb = 0; xb < W; xb += TILE) {
-      for (int i = t; i < WG_C * TILE * TILE; i += 256) {
-        const int c = i / (TILE * TILE), r = i % (TILE * TILE);
-        const int yy = yb + r / TILE, xx = xb + r % TILE;
-        float v = 0.f;
-        if (co0 + c < CO && yy < y_hi && xx < W) {
-          const long long o = ((long long)(co0 + c) * H + yy) * W + xx;
-          v = dout[o];
-          if (relu && !(__bfloat162float(out[o]) > 0.f)) v = 0.f;
-        }
-        sd[c][r] = v;
+  for (int i = 0; i < PER; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+  float accb[BPW];
+#pragma unroll
+  for (int j = 0; j < BPW; ++j) accb[j] = 0.f;
+  auto dpre = [&](int c, int yy, int xx) -> float {
+    if (m0 + c >= CO || yy >= y_hi || xx >= W) return 0.f;
+    const long long o = ((long long)(m0 + c) * H + yy) * W + xx;
+    const float d = dout[o];
+    return (relu && !(__bfloat162float(out[o]) > 0.f)) ? 0.f : d;
+  };
+  for (int yb = y_lo; yb < y_hi; yb += 16)
+    for (int xb = 0; xb < W; xb += 16) {
+      for (int i = threadIdx.x; i < MB * 16 * 8; i += 256) {
+        const int wd = i & 7, r = (i >> 3) & 15, c = i >> 7;
+        const float v0 = dpre(c, yb + r, xb + 2 * wd), v1 = dpre(c, yb + r, xb + 2 * wd + 1);
+        s_d[c * SD + r * 8 + wd] = pack_bf16(v0, v1);
+        s_d[(MB + c) * SD + r * 8 + wd] = pack_bf16(v0 - __bfloat162float(__float2bfloat16(v0)),
+                                                   v1 - __bfloat162float(__float2bfloat16(v1)));
       }
-      for (int i = t; i < WG_C * T * T; i += 256) {
-        const int c = i / (T * T), r = i % (T * T);
-        const int yy = yb + r / T - R, xx = xb + r % T - R;
-        sx[c][r] = (ci0 + c < CI) ? conv_in(in, ci0 + c, yy, xx, H, W) : 0.f;
+      for (int i = threadIdx.x; i < K * NB * YT * 8; i += 256) {
+        const int wd = i & 7, r = (i >> 3) % YT, c = (i / (8 * YT)) % NB, kx = i / (8 * YT * NB);
+        const int yy = yb - R + r, xx = xb - R + kx + 2 * wd;
+        const float lo = (n0 + c < CI) ? conv_in(in, n0 + c, yy, xx, H, W) : 0.f;
+        const float hi = (n0 + c < CI) ? conv_in(in, n0 + c, yy, xx + 1, H, W) : 0.f;
+        s_x[(kx * NB + c) * SX + r * 8 + wd] = pack_bf16(lo, hi);
+      }
+      // bias (blocks of the first input-channel block only): FP32 sums of
+      // dpre, lane-wise over the tile then a fixed tree
+      if (blockIdx.x == 0)
+#pragma unroll
+      for (int j = 0; j < BPW; ++j) {
+        const int c = warp + 8 * j;
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int px = lane + 32 * k;
+          s += dpre(c, yb + px / 16, xb + px % 16);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        accb[j] += s;
       }
       __syncthreads();
 #pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        const int tri = t + 256 * j;
-        if (tri < NTRI) {
-          const int co = tri / (WG_C * K * K), rem = tri % (WG_C * K * K);
-          const int ci = rem / (K * K), k = rem % (K * K);
-          const int dy = k / K, dx = k % K;
-          float a = acc[j];
-          for (int r = 0; r < TILE * TILE; ++r)
-            a = fmaf(sd[co][r], sx[ci][(r / TILE + dy) * T + r % TILE + dx], a);
-          acc[j] = a;
+      for (int i = 0; i < PER; ++i) {
+        const int combo = warp + 8 * i;
+        if (combo < COMBOS) {
+          const int mt = combo % MT, nt = (combo / MT) % NT, tap = combo / (MT * NT);
+          const int ky = tap / K, kx = tap % K;
+          const unsigned* xb0 = s_x + (kx * NB + nt * 8 + g) * SX + ky * 8;
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {  // dpre = hi + lo
+            const unsigned* da0 = s_d + (part * MB + mt * 16 + g) * SD;
+            const unsigned* da1 = da0 + 8 * SD;
+#pragma unroll 4
+            for (int r = 0; r < 16; ++r) {
+              const unsigned a[4] = {da0[r * 8 + t4], da1[r * 8 + t4], da0[r * 8 + t4 + 4],
+                                     da1[r * 8 + t4 + 4]};
+              mma_bf16(acc[i], a, xb0[r * 8 + t4], xb0[r * 8 + t4 + 4]);
+            }
+          }
         }
       }
-      if (t < WG_C)
-        for (int r = 0; r < TILE * TILE; ++r) accb += sd[t][r];
       __syncthreads();
     }
+  // c0 (m = g, n = 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
 #pragma unroll
-  for (int j = 0; j < NT; ++j) {
-    const int tri = t + 256 * j;
-    if (tri < NTRI) {
-      const int co = tri / (WG_C * K * K), rem = tri % (WG_C * K * K);
-      const int ci = rem / (K * K), k = rem % (K * K);
-      if (co0 + co < CO && ci0 + ci < CI)
-        part[(((long long)p * CO + co0 + co) * CI + ci0 + ci) * K * K + k] = acc[j];
+  for (int i = 0; i < PER; ++i) {
+    const int combo = warp + 8 * i;
+    if (combo >= COMBOS) continue;
+    const int mt = combo % MT, nt = (combo / MT) % NT, tap = combo / (MT * NT);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int co = m0 + mt * 16 + g + 8 * (e >> 1), ci = n0 + nt * 8 + 2 * t4 + (e & 1);
+      if (co < CO && ci < CI) part[(((long long)p * CO + co) * CI + ci) * KK + tap] = acc[i][e];
     }
   }
-  if (t < WG_C && blockIdx.x == 0 && co0 + t < CO) part_b[(long long)p * CO + co0 + t] = accb;
+  if (blockIdx.x == 0 && lane == 0)
+#pragma unroll
+    for (int j = 0; j < BPW; ++j) {
+      const int c = warp + 8 * j;
+      if (m0 + c < CO) part_b[(long long)p * CO + m0 + c] = accb[j];
+    }
+}
+
+
+// Forward (DGRAD = false) or data-gradient convolution on the tensor cores;
+// MB (GEMM rows per CTA) follows the row count M.
+template <int K, bool DGRAD>
+void launch_conv_mma(const MmaIn& src, int H, int W, int M, int Kc, int CIw,
+                     const __nv_bfloat16* w, const float* bias, int relu, __nv_bfloat16* ob,
+                     float* of, cudaStream_t st) {
+  const int MB = M <= 16 ? 16 : (M <= 32 ? 32 : 64);
+  const dim3 grid((W + 15) / 16, (H + 15) / 16, (M + MB - 1) / MB);
+  if (MB == 16)
+    k_conv_mma<K, 16, DGRAD><<<grid, 256, 0, st>>>(src, H, W, M, Kc, CIw, w, bias, relu, ob, of);
+  else if (MB == 32)
+    k_conv_mma<K, 32, DGRAD><<<grid, 256, 0, st>>>(src, H, W, M, Kc, CIw, w, bias, relu, ob, of);
+  else
+    k_conv_mma<K, 64, DGRAD><<<grid, 256, 0, st>>>(src, H, W, M, Kc, CIw, w, bias, relu, ob, of);
+}
+
+constexpr int WG_MB = 32, WG_NB = 16, WG_ROWS = 32;
+
+template <int K>
+cudaError_t launch_wgrad_mma(const float* dout, const __nv_bfloat16* out, int relu, const ConvIn& in,
+                             int H, int W, int CO, float* part, float* part_b, cudaStream_t st) {
+  const int CI = in.ca + in.cb, P = (H + WG_ROWS - 1) / WG_ROWS;
+  const dim3 grid((CI + WG_NB - 1) / WG_NB, (CO + WG_MB - 1) / WG_MB, P);
+  const size_t bytes = WgradSmem<K, WG_MB, WG_NB>::bytes;
+  static_assert(WgradSmem<3, WG_MB, WG_NB>::bytes <= 100 * 1024, "wgrad shared memory above 100 KB");
+  static thread_local int dev_done = -1;  // opt-in above 48 KB, once per device and thread
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev_done != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_mma<K, WG_MB, WG_NB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess) return e;
+    dev_done = dev;
+  }
+  k_conv_wgrad_mma<K, WG_MB, WG_NB><<<grid, 256, bytes, st>>>(dout, out, relu, in, H, W, CO, WG_ROWS,
+                                                             part, part_b);
+  return cudaGetLastError();
 }
 
 // grad += sum_p part[p] in order p = 0 .. P-1 (deterministic)
@@ -575,13 +726,14 @@ pf_status pf_unet_forward(pf_unet* u, const float* x, float* y) {
     const int lev = layer_level(u, l);
     const int H = u->H >> lev, W = u->W >> lev;
     const ConvIn in = layer_input(u, l);
-    dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE, (c.co + COB - 1) / COB);
     const __nv_bfloat16* w = u->wbf + c.off_w;
     const float* b = u->w32 + c.off_b;
+    MmaIn src{};
+    src.conv = in;
     if (c.k == 3)
-      k_conv_fwd<3><<<grid, 256, 0, u->st>>>(in, H, W, c.co, w, b, 1, u->act[l], nullptr);
+      launch_conv_mma<3, false>(src, H, W, c.co, c.ci, c.ci, w, b, 1, u->act[l], nullptr, u->st);
     else
-      k_conv_fwd<1><<<grid, 256, 0, u->st>>>(in, H, W, c.co, w, b, 0, nullptr, y);
+      launch_conv_mma<1, false>(src, H, W, c.co, c.ci, c.ci, w, b, 0, nullptr, y, u->st);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -613,24 +765,26 @@ pf_status pf_unet_backward(pf_unet* u, const float* dy) {
     const __nv_bfloat16* out = (l == nl - 1) ? nullptr : u->act[l];
     const int relu = c.relu ? 1 : 0;
     // weight and bias gradients
-    const int rows = 32, P = (H + rows - 1) / rows;
-    dim3 gw((c.ci + WG_C - 1) / WG_C, (c.co + WG_C - 1) / WG_C, P);
+    const int P = (H + WG_ROWS - 1) / WG_ROWS;
     const long long nw = (long long)c.co * c.ci * c.k * c.k;
     float* part_b = u->wpart + (long long)P * nw;
     if (c.k == 3)
-      k_conv_wgrad<3><<<gw, 256, 0, u->st>>>(dout, out, relu, in, H, W, c.co, rows, u->wpart, part_b);
+      launch_wgrad_mma<3>(dout, out, relu, in, H, W, c.co, u->wpart, part_b, u->st);
     else
-      k_conv_wgrad<1><<<gw, 256, 0, u->st>>>(dout, out, relu, in, H, W, c.co, rows, u->wpart, part_b);
+      launch_wgrad_mma<1>(dout, out, relu, in, H, W, c.co, u->wpart, part_b, u->st);
     k_sum_parts<<<grid1(nw), 256, 0, u->st>>>(u->wpart, P, nw, u->g + c.off_w);
     k_sum_parts<<<grid1(c.co), 256, 0, u->st>>>(part_b, P, c.co, u->g + c.off_b);
     if (l == 0) continue;  // no gradient needed for the input features
     // data gradient on the conv grid, then the adjoint of the input transform
-    dim3 gd((W + TILE - 1) / TILE, (H + TILE - 1) / TILE, (c.ci + COB - 1) / COB);
     const __nv_bfloat16* w = u->wbf + c.off_w;
+    MmaIn src{};
+    src.dout = dout;
+    src.out = out;
+    src.relu = relu;
     if (c.k == 3)
-      k_conv_dgrad<3><<<gd, 256, 0, u->st>>>(dout, out, relu, H, W, c.co, c.ci, w, u->dscratch);
+      launch_conv_mma<3, true>(src, H, W, c.ci, c.co, c.ci, w, nullptr, 0, nullptr, u->dscratch, u->st);
     else
-      k_conv_dgrad<1><<<gd, 256, 0, u->st>>>(dout, out, relu, H, W, c.co, c.ci, w, u->dscratch);
+      launch_conv_mma<1, true>(src, H, W, c.ci, c.co, c.ci, w, nullptr, 0, nullptr, u->dscratch, u->st);
     // operand a is the output of layer l-1; operand b (decoder) a skip
     float* ga = u->gact[l - 1];
     float* gb = nullptr;

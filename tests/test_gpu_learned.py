@@ -51,5 +51,13 @@ def test_learned_iterate_trains_and_is_gated():
         for ra, rb in zip(a, b):
             assert abs(ra["energy"] - rb["energy"]) <= 1e-8 * abs(ra["energy"])
     assert np.mean(acc) >= 0.5
-    assert cyc["learned"] <= cyc["plain"]
-    assert cyc["learned"] <= cyc["extrapolated"] + 0.5
+    # the gain of the learned start over each start without the network, in
+    # V-cycles per load step: it must beat the plain start and may not lose
+    # to the extrapolation it starts from; a zero gain over the
+    # extrapolation is reported as such (the network then adds nothing)
+    gain_plain = cyc["plain"] - cyc["learned"]
+    gain_extrap = cyc["extrapolated"] - cyc["learned"]
+    print(f"gain over plain {gain_plain:+.2f}, over extrapolated {gain_extrap:+.2f} V-cycles per step"
+          + (" (the network adds nothing over the extrapolation)" if gain_extrap == 0 else ""))
+    assert gain_plain > 0
+    assert gain_extrap >= 0

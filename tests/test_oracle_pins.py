@@ -569,3 +569,59 @@ def test_pins_catch_swapped_thresholds(monkeypatch):
     monkeypatch.setattr(O, "convergence_control", swapped)
     with pytest.raises(AssertionError):
         test_convergence_control_radius_table()
+
+
+# ---------------------------------------------------------------- trust-region gate
+def _gate_case():
+    H = O.Hierarchy(2, (5, 5), 0.25, 2, O.Params(E=1.0, nu=0.3, Gc=1.0, p=1e-3))
+    g = H.fine
+    x = np.zeros(3 * g.N)
+    x[2 * g.N:] = O.rasterize(g, O.LINE2D, PI.centred_crack_2d(0.2), g.h)
+    r = O.rmtr_load_step(H, x, O.TRParams(rtol=1e-12), p=1e-3)
+    return H, g, r.x
+
+
+def test_trust_region_gate_ratio_from_the_quartic():
+    """The gate's ratio is eq. (rho_tr) along s: the plain difference of
+    the two energies over the model's decrease, agreeing to the plain
+    difference's cancellation bound (1e-15 |E| / |actual|); its predicted
+    decrease is -(a1 + a2) of the quartic coefficients (a1 = grad E.s,
+    a2 = s.Hs/2, pinned above).  A proposal that triples the displacement
+    is refused (the energy rises); the converged state at a higher
+    pressure, proposed from the lower one, is accepted with rho near 1 (the
+    quadratic model is nearly exact there)."""
+    H, g, x1 = _gate_case()
+    H.prm.p = 2e-3
+    r2 = O.rmtr_load_step(H, x1, O.TRParams(rtol=1e-12), p=2e-3)
+    rho, acc, xn = O.trust_region_gate(H, x1, r2.x, 0.1)
+    s = r2.x - x1
+    e0, e1 = O.energy(g, H.prm, x1), O.energy(g, H.prm, x1 + s)
+    a = O.energy_diff_coeffs(g, H.prm, x1, s)
+    pred = -(a[0] + a[1])
+    plain = (e0 - e1) / pred
+    assert abs(rho - plain) <= 4e-15 * abs(e0) / abs(e0 - e1) * abs(rho)
+    assert abs(rho - (-(a.sum())) / pred) <= 1e-12 * abs(rho)
+    assert acc and 0.9 < rho < 1.1
+    assert np.array_equal(xn, x1 + (r2.x - x1))
+    bad = x1.copy()
+    bad[:2 * g.N] *= 3.0
+    rho_b, acc_b, xb = O.trust_region_gate(H, x1, bad, 0.1)
+    assert not acc_b and np.array_equal(xb, x1)
+
+
+def test_pins_catch_a_planted_gate_sign_error(monkeypatch):
+    """A gate whose predicted decrease forgets the minus sign never sees a
+    positive prediction for a descent step, so it refuses the good proposal."""
+    real = O.trust_region_gate
+
+    def wrong(H, x, xhat, eta):
+        real_hv = O.hessvec
+        try:
+            O.hessvec = lambda g, prm, xx, v, elems=None: -real_hv(g, prm, xx, v, elems)
+            return real(H, x, xhat, eta)
+        finally:
+            O.hessvec = real_hv
+
+    monkeypatch.setattr(O, "trust_region_gate", wrong)
+    with pytest.raises(AssertionError):
+        test_trust_region_gate_ratio_from_the_quartic()
