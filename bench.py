@@ -57,6 +57,16 @@ WORKLOAD_SMALL = dict(WORKLOAD, workload="3d_17^3_q1_4level_20discs_ramp", n_coa
 # is ramp step t = (k - 1) mod 10 + 1; at t = 1 the state restarts from the
 # fractured initial state, so no pressure above 5e-3 is ever solved.
 RAMP = 10
+# The paper's own 3D scenario at its own size (Sec. 5.2, three-dimensional
+# scenarios): unit cube, 50^3 coarse grid and four levels (393^3 nodes,
+# 242,793,828 dofs), 100 fractures as rectangular plates, granite-like
+# lambda = mu = 1e5 (E = 2.5e5, nu = 0.25), G_c = 1, clamped boundary, and
+# the pressure p_k = p0 + k dt p_c with p0 = 0.01, dt = 0.05, p_c = 1.
+PAPER_SCALE = {
+    "workload": "3d_393^3_q1_4level_100plates_paper", "dim": 3, "n_coarse": [50, 50, 50],
+    "levels": 4, "h_coarse": 1.0 / 49, "E": 2.5e5, "nu": 0.25, "Gc": 1.0, "ls_over_h": 2.0,
+    "fractures": 100, "seed": PI.SEED_3D_PAPER, "p0": 0.01, "dp": 0.05,
+}
 METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same GB300"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
@@ -102,6 +112,8 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the uneven 2D batch (64 instances, 129^2 .. 1025^2) instead of the 3D workload")
     ap.add_argument("--batch-threads", type=int, default=0)
+    ap.add_argument("--paper-scale", action="store_true",
+                    help="the paper's 3D scenario at its size (393^3, 242.8M dofs, 100 plates)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -741,6 +753,82 @@ def run_ours(args):
     return 0
 
 
+def run_paper_scale(args):
+    """Load steps of the paper's 242.8M-dof 3D scenario on one GPU (mixed
+    precision, extrapolated start): W untimed steps k = 0 .. W-1, then K
+    timed steps, each timed with CUDA events; plus the FP32 Hessian
+    product's time at this size."""
+    import torch
+    from paper_2007_12908_gb300 import build
+    build.build()
+    import paper_2007_12908_gb300 as pf
+    W = PAPER_SCALE
+    H = pf.mesh_hierarchy_create(3, W["n_coarse"], W["levels"], W["h_coarse"], E=W["E"], nu=W["nu"],
+                                 Gc=W["Gc"], ls_over_h=W["ls_over_h"])
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    g_n, g_h, N = H.levels[-1]
+    pf.fractures_set(H, pf.PF_BOX3D, PI.box_network_3d(W["seed"], W["fractures"]), g_h, x)
+    stream = torch.cuda.current_stream()
+    prec = pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64
+
+    def step(k):
+        p = W["p0"] + k * W["dp"]
+        pf.pressure_set(H, p)
+        prm = pf.default_params(precision=prec, start=pf.PF_START_EXTRAPOLATE,
+                                p_prev=(W["p0"] + (k - 1) * W["dp"]) if k > 0 else 0.0)
+        return pf.rmtr_load_step(H, x, prm, check=False)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    stats = []
+    ev[0].record(stream)
+    for j, k in enumerate(range(args.warmup, args.warmup + args.steps)):
+        stats.append(step(k))
+        ev[j + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    secs = [ev[j].elapsed_time(ev[j + 1]) * 1e-3 for j in range(args.steps)]
+    level = W["levels"] - 1
+    ndof = H.ndof()
+    v32 = torch.from_numpy(PI.random_direction(78, ndof, 1e-3)).cuda().float()
+    x32, o32 = x.float(), torch.empty_like(v32)
+    for _ in range(3):
+        pf.hessvec(H, level, x32, v32, o32)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(10):
+        pf.hessvec(H, level, x32, v32, o32)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t32 = a.elapsed_time(b) / 10 * 1e-3
+    ne = (g_n[0] - 1) * (g_n[1] - 1) * (g_n[2] - 1)
+    free_b, total_b = torch.cuda.mem_get_info()
+    line = {
+        "metric": "RMTR s/load-step at the paper's 3D size", "value": sum(secs) / args.steps,
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "dtype": "f64+f32" if prec == pf.PF_FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": W["workload"], "grid": list(g_n), "levels": W["levels"], "dofs": ndof,
+                   "fractures": W["fractures"], "E": W["E"], "nu": W["nu"], "Gc": W["Gc"],
+                   "pressures": [W["p0"] + k * W["dp"] for k in range(args.warmup, args.warmup + args.steps)],
+                   "precision": args.precision, "start": "extrapolate"},
+        "seconds_per_step": secs,
+        "solver": {k: [s_[k] for s_ in stats] for k in ("cycles", "converged", "cg", "status", "energy")},
+        "hessvec_fp32": {"us_per_launch": t32 * 1e6, "gdofs": ndof / t32 / 1e9,
+                         "tflops": FLOP32_PER_ELEMENT * ne / t32 / 1e12},
+        "device_memory_used_gb": (total_b - free_b) / 1e9,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    H.close()
+    return 0
+
+
 def run_batched(args):
     """Load steps of 64 uneven 2D instances (16 each of 129^2, 257^2, 513^2,
     1025^2 nodes; 10-1000 line fractures, +-30 deg families) run
@@ -811,6 +899,8 @@ def main():
         return run_reference(args)
     if args.batched:
         return run_batched(args)
+    if args.paper_scale:
+        return run_paper_scale(args)
     return run_ours(args)
 
 

@@ -49,6 +49,10 @@ typedef int pf_status;
 
 #define PF_LINE2D 0 /* rows [cx, cy, theta, half_length]                      */
 #define PF_DISC3D 1 /* rows [cx, cy, cz, nx, ny, nz, radius], |n| = 1         */
+#define PF_BOX3D 2  /* rows [cx, cy, cz, nx, ny, nz, ax, ay, az, bx, by, bz,
+                       half_a, half_b]: a rectangular plate (the paper's
+                       "smooth parallelepiped" before its band width) with
+                       unit normal n and unit in-plane axes a, b           */
 
 typedef struct pf_hierarchy pf_hierarchy;
 
@@ -155,6 +159,11 @@ const char* pf_last_error(void);
  * The device memory all of it needs is compared with the device's free
  * memory before the first allocation: a hierarchy that does not fit (with
  * 1 GB kept in reserve) is refused with PF_ENOMEM and nothing allocated.
+ * Not counted there: a level's assembled FP64 Hessian stencil (27 x 16
+ * doubles per node in 3D), allocated on the level's first FP64 lag (an
+ * FP64-precision load step, a GALERKIN coarse level, or
+ * pf_hessvec_lag_set with PF_FP64); if it does not fit, that call returns
+ * PF_ENOMEM.
  * Errors: PF_EINVAL for a bad descriptor, PF_ENOMEM, PF_ECUDA. */
 pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* desc, pf_hierarchy** out);
 pf_status pf_mesh_hierarchy_destroy(pf_hierarchy* h);
@@ -165,11 +174,13 @@ pf_status pf_level_info(const pf_hierarchy* h, int level, int n_out[3],
 
 /* Fracture initialisation (Sec. 5): the c plane of the finest-level FP64
  * state x_dev is set to 1 at nodes within band_half_width of a fracture's
- * mid-line (PF_LINE2D) or mid-disc (PF_DISC3D) and inside its extent, else 0
- * (union over rows).  u planes are not touched.  c_prev := c.
- * rows_host: n rows of 4 (LINE2D) or 7 (DISC3D) doubles.  Node coordinates
- * are i*h in FP64; comparisons are inclusive.
- * Errors: PF_EINVAL (kind/dim mismatch, n < 0, band <= 0). */
+ * mid-line (PF_LINE2D), mid-disc (PF_DISC3D) or mid-rectangle (PF_BOX3D)
+ * and inside its extent, else 0 (union over rows).  u planes are not
+ * touched.  c_prev := c.
+ * rows_host: n rows of 4 (LINE2D), 7 (DISC3D) or 14 (BOX3D) doubles.  Node
+ * coordinates are i*h in FP64; comparisons are inclusive.
+ * Errors: PF_EINVAL (kind/dim mismatch, n < 0, band <= 0), PF_ENONFINITE
+ * (a non-finite value in a row; nothing is changed). */
 pf_status pf_fractures_set(pf_hierarchy* h, int kind, int n, const double* rows_host,
                            double band_half_width, void* x_dev);
 

@@ -49,6 +49,7 @@ import scipy.sparse as sp
 
 LINE2D = 0
 DISC3D = 1
+BOX3D = 2
 
 GALERKIN = 0
 FIRST_ORDER = 1
@@ -212,6 +213,20 @@ def rasterize(grid: Grid, kind: int, rows: np.ndarray, band_half_width: float) -
             py = dy - dn * nv[1]
             pz = dz - dn * nv[2]
             inside = (np.abs(dn) <= band_half_width) & (px * px + py * py + pz * pz <= rad * rad)
+        elif kind == BOX3D:
+            # a rectangular plate: centre, unit normal n, unit in-plane axes
+            # a and b, half-lengths along a and b (the "smooth
+            # parallelepipeds" of Sec. 5.2 are these plates widened to the
+            # band)
+            cen, nv, av, bv = r[0:3], r[3:6], r[6:9], r[9:12]
+            ha, hb = r[12], r[13]
+            dx = ij[0] - cen[0]
+            dy = ij[1] - cen[1]
+            dz = ij[2] - cen[2]
+            dn = nv[0] * dx + nv[1] * dy + nv[2] * dz
+            da = av[0] * dx + av[1] * dy + av[2] * dz
+            db = bv[0] * dx + bv[1] * dy + bv[2] * dz
+            inside = (np.abs(dn) <= band_half_width) & (np.abs(da) <= ha) & (np.abs(db) <= hb)
         else:
             raise ValueError("unknown fracture kind")
         c[inside] = 1.0

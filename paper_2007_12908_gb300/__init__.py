@@ -6,7 +6,7 @@ declared in include/pf.h); this package is its thin ctypes binding.  There
 is no CPU fallback: calls raise if the library is not built or no CUDA
 device is present."""
 from ._binding import (  # noqa: F401
-    PF_DISC3D, PF_FIRST_ORDER, PF_FP32, PF_FP64, PF_GALERKIN, PF_LINE2D, PF_START_EXTRAPOLATE,
+    PF_BOX3D, PF_DISC3D, PF_FIRST_ORDER, PF_FP32, PF_FP64, PF_GALERKIN, PF_LINE2D, PF_START_EXTRAPOLATE,
     PF_START_PLAIN, PfError,
     coarse_bounds, default_params, energy, energy_diff, fractures_set, get_c_prev, gradient,
     hessvec, hessvec_lag_set, hessvec_lagged, mesh_hierarchy_create, pressure_set, project, prolong, restrict, rmtr_load_step,

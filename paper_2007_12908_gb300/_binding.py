@@ -17,7 +17,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ENOTCONV, PF_ETIMEOUT, 
     range(9)
 PF_FP64, PF_FP32 = 0, 1
 PF_GALERKIN, PF_FIRST_ORDER = 0, 1
-PF_LINE2D, PF_DISC3D = 0, 1
+PF_LINE2D, PF_DISC3D, PF_BOX3D = 0, 1, 2
 PF_START_PLAIN, PF_START_EXTRAPOLATE = 0, 1
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ENONFINITE",
@@ -247,7 +247,7 @@ def mesh_hierarchy_create(dim, n_coarse, n_levels, h_coarse, E=1.0, nu=0.3, Gc=1
 def fractures_set(H: Hierarchy, kind: int, rows, band_half_width: float, x):
     import torch
     rows = np.ascontiguousarray(np.atleast_2d(np.asarray(rows, dtype=np.float64)))
-    width = 4 if kind == PF_LINE2D else 7
+    width = {PF_LINE2D: 4, PF_DISC3D: 7, PF_BOX3D: 14}.get(kind, 0)
     if rows.size and rows.shape[1] != width:
         raise ValueError(f"fracture rows must have {width} columns")
     n = rows.shape[0] if rows.size else 0

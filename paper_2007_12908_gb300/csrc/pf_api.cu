@@ -36,6 +36,19 @@ static pf_status bad(const char* msg) {
   return PF_EINVAL;
 }
 
+namespace pf {
+cudaError_t ensure_stencil(pf_hierarchy* h, int l) {
+  LevelBuf& B = h->lv[l];
+  if (B.stencil) return cudaSuccess;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(double) * stencil_count(h->geo[l]));
+  if (e != cudaSuccess) return e;
+  h->allocations.push_back(p);
+  B.stencil = static_cast<double*>(p);
+  return cudaSuccess;
+}
+}  // namespace pf
+
 template <class T>
 __global__ void k_fma_probe(T* out, int reps, T a, T b) {
   T v[8];
@@ -169,7 +182,6 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
       for (int v = 0; v < 24; ++v) add(8.0 * (n + 4));
       add(4.0 * n);
       add(8.0 * double(coef_count(h->geo[l])));
-      add(8.0 * double(stencil_count(h->geo[l])));
     }
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
@@ -234,8 +246,10 @@ pf_status pf_mesh_hierarchy_create(const pf_mesh_desc* d, pf_hierarchy** out) {
         pf_mesh_hierarchy_destroy(h);
         return rc;
       }
-    if ((rc = alloc(h, (void**)&B.coef, sizeof(double) * coef_count(h->geo[l]))) ||
-        (rc = alloc(h, (void**)&B.stencil, sizeof(double) * stencil_count(h->geo[l])))) {
+    // the FP64 stencil (27 x 16 doubles per node in 3D) is allocated on a
+    // level's first FP64 lag (ensure_stencil): mixed-precision runs never
+    // hold it on their FIRST_ORDER levels
+    if ((rc = alloc(h, (void**)&B.coef, sizeof(double) * coef_count(h->geo[l])))) {
       pf_mesh_hierarchy_destroy(h);
       return rc;
     }
@@ -265,24 +279,26 @@ pf_status pf_fractures_set(pf_hierarchy* h, int kind, int n, const double* rows,
   if (!h || !x_dev) return bad("fractures_set: null argument");
   if (n < 0 || (n > 0 && !rows)) return bad("fractures_set: bad row count");
   if (!(band_half_width > 0)) return bad("fractures_set: band_half_width must be > 0");
-  if ((kind == PF_LINE2D && h->dim != 2) || (kind == PF_DISC3D && h->dim != 3) ||
-      (kind != PF_LINE2D && kind != PF_DISC3D))
+  if ((kind == PF_LINE2D && h->dim != 2) || ((kind == PF_DISC3D || kind == PF_BOX3D) && h->dim != 3) ||
+      (kind != PF_LINE2D && kind != PF_DISC3D && kind != PF_BOX3D))
     return bad("fractures_set: kind does not match the dimension");
   const Geom& g = h->geo.back();
-  // device rows: LINE2D [cx, cy, cos, sin, -sin, cos, half_length]
-  //              DISC3D [cx, cy, cz, nx, ny, nz, radius]
-  double* pack = new double[7 * (n > 0 ? n : 1)];
+  // device rows of kRasterRow doubles:
+  //   LINE2D [cx, cy, cos, sin, -sin, cos, half_length]
+  //   DISC3D [cx, cy, cz, nx, ny, nz, radius]
+  //   BOX3D  [cx, cy, cz, nx, ny, nz, ax, ay, az, bx, by, bz, half_a, half_b]
+  const int width = kind == PF_LINE2D ? 4 : (kind == PF_DISC3D ? 7 : 14);
+  double* pack = new double[kRasterRow * (n > 0 ? n : 1)]();
   for (int k = 0; k < n; ++k) {
-    double* q = pack + 7 * k;
+    double* q = pack + kRasterRow * k;
+    const double* r = rows + width * k;
     if (kind == PF_LINE2D) {
-      const double* r = rows + 4 * k;
       const double c = std::cos(r[2]), s = std::sin(r[2]);
       q[0] = r[0]; q[1] = r[1]; q[2] = c; q[3] = s; q[4] = -s; q[5] = c; q[6] = r[3];
     } else {
-      const double* r = rows + 7 * k;
-      for (int j = 0; j < 7; ++j) q[j] = r[j];
+      for (int j = 0; j < width; ++j) q[j] = r[j];
     }
-    for (int j = 0; j < 7; ++j)
+    for (int j = 0; j < kRasterRow; ++j)
       if (!std::isfinite(q[j])) {
         delete[] pack;
         set_error("fractures_set: non-finite fracture row");
@@ -290,13 +306,13 @@ pf_status pf_fractures_set(pf_hierarchy* h, int kind, int n, const double* rows,
       }
   }
   double* rows_dev = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&rows_dev, sizeof(double) * 7 * (n > 0 ? n : 1), h->st);
+  cudaError_t e = cudaMallocAsync((void**)&rows_dev, sizeof(double) * kRasterRow * (n > 0 ? n : 1), h->st);
   if (e != cudaSuccess) {
     delete[] pack;
     set_error("fractures_set: allocation failed");
     return PF_ENOMEM;
   }
-  e = cudaMemcpyAsync(rows_dev, pack, sizeof(double) * 7 * n, cudaMemcpyHostToDevice, h->st);
+  e = cudaMemcpyAsync(rows_dev, pack, sizeof(double) * kRasterRow * n, cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess)
     e = rasterize(g, kind, n, rows_dev, band_half_width,
                   static_cast<double*>(x_dev) + h->dim * g.N, h->c_prev, h->st);
@@ -427,6 +443,7 @@ pf_status pf_hessvec_lag_set(pf_hierarchy* h, int level, const void* x, int prec
   if (prec == PF_FP64) {
     PF_TRY_CUDA(cudaMemcpyAsync(B.xlag, x, sizeof(double) * B.n, cudaMemcpyDeviceToDevice, h->st),
                 "hessvec_lag_set");
+    PF_TRY_CUDA(ensure_stencil(h, level), "hessvec_lag_set: FP64 stencil");
     PF_TRY_CUDA(elem_hess_coef(h->geo[level], h->mat[level], B.xlag, B.coef, h->st), "hessvec_lag_set");
     PF_TRY_CUDA(stencil_assemble(h->geo[level], h->mat[level], B.coef, B.stencil, h->st),
                 "hessvec_lag_set");
@@ -441,6 +458,10 @@ pf_status pf_hessvec_lagged(pf_hierarchy* h, int level, const void* v, void* Hv,
   if (!valid_level(h, level) || !v || !Hv) return bad("hessvec_lagged: bad argument");
   if (check_prec(prec)) return PF_EINVAL;
   LevelBuf& B = h->lv[level];
+  if (prec == PF_FP64 && !B.stencil) {
+    set_error("hessvec_lagged: no FP64 lag set on this level");
+    return PF_ESTATE;
+  }
   if (prec == PF_FP64)
     PF_TRY_CUDA(stencil_apply(h->geo[level], B.stencil, static_cast<const double*>(v),
                               static_cast<double*>(Hv), h->st),

@@ -72,4 +72,6 @@ pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_para
                               pf_rmtr_stats* stats);
 pf_status projected_gradient_impl(pf_hierarchy* H, const double* x_dev, double* out);
 void refresh_pressure(pf_hierarchy* H);
+// Allocates level l's FP64 stencil on first use (held until destroy).
+cudaError_t ensure_stencil(pf_hierarchy* H, int l);
 }  // namespace pf

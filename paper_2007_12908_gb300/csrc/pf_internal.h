@@ -169,7 +169,9 @@ cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float*
                                const float* p_dev = nullptr);
 
 // Fracture band rasterisation into the c plane (FP64) of x and c_prev.
-// rows: device array of precomputed shape rows (see pf_kernels.cu).
+// rows: device array of precomputed shape rows of kRasterRow doubles (see
+// pf_fractures_set); kind 0 line (2D), 1 disc, 2 rectangle (3D).
+constexpr int kRasterRow = 14;
 cudaError_t rasterize(const Geom& g, int kind, int n, const double* rows_dev, double band,
                       double* c_plane, double* c_prev, cudaStream_t st);
 

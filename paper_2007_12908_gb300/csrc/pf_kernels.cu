@@ -1324,13 +1324,13 @@ __global__ void k_raster(Geom g, int kind, int nrows, const double* __restrict__
                  Z = __dmul_rn(double(iz), g.h);
     bool in = false;
     for (int k = 0; k < nrows && !in; ++k) {
-      const double* q = rows + 7 * k;
+      const double* q = rows + kRasterRow * k;
       if (kind == 0) {
         const double dx = __dadd_rn(X, -q[0]), dy = __dadd_rn(Y, -q[1]);
         const double dn = fabs(__dadd_rn(__dmul_rn(q[4], dx), __dmul_rn(q[5], dy)));
         const double dt = fabs(__dadd_rn(__dmul_rn(q[2], dx), __dmul_rn(q[3], dy)));
         in = dn <= band && dt <= q[6];
-      } else {
+      } else if (kind == 1) {
         const double dx = __dadd_rn(X, -q[0]), dy = __dadd_rn(Y, -q[1]), dz = __dadd_rn(Z, -q[2]);
         const double dn = __dadd_rn(__dadd_rn(__dmul_rn(q[3], dx), __dmul_rn(q[4], dy)),
                                     __dmul_rn(q[5], dz));
@@ -1339,6 +1339,16 @@ __global__ void k_raster(Geom g, int kind, int nrows, const double* __restrict__
         const double pz = __dadd_rn(dz, -__dmul_rn(dn, q[5]));
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
         in = fabs(dn) <= band && r2 <= __dmul_rn(q[6], q[6]);
+      } else if (kind == 2) {
+        // rectangle: |d.n| <= band, |d.a| <= half_a, |d.b| <= half_b
+        const double dx = __dadd_rn(X, -q[0]), dy = __dadd_rn(Y, -q[1]), dz = __dadd_rn(Z, -q[2]);
+        const double dn = __dadd_rn(__dadd_rn(__dmul_rn(q[3], dx), __dmul_rn(q[4], dy)),
+                                    __dmul_rn(q[5], dz));
+        const double da = __dadd_rn(__dadd_rn(__dmul_rn(q[6], dx), __dmul_rn(q[7], dy)),
+                                    __dmul_rn(q[8], dz));
+        const double db = __dadd_rn(__dadd_rn(__dmul_rn(q[9], dx), __dmul_rn(q[10], dy)),
+                                    __dmul_rn(q[11], dz));
+        in = fabs(dn) <= band && fabs(da) <= q[12] && fabs(db) <= q[13];
       }
     }
     const double val = in ? 1.0 : 0.0;

@@ -520,6 +520,7 @@ struct Solver {
     }
     if (!mixed32(l) || galerkin(l)) {
       // FP64 Hessian of this level: Gauss-point coefficients, once per lag
+      ck(ensure_stencil(H, l), "FP64 stencil allocation");
       ck(elem_hess_coef(H->geo[l], H->mat[l], B.xlag, B.coef, st), "hess_coef");
       ck(stencil_assemble(H->geo[l], H->mat[l], B.coef, B.stencil, st), "assemble");
       S.launches += 2;
@@ -1468,7 +1469,7 @@ pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_para
     rc = solver.run(x_dev);
   } catch (const CudaFail& f) {
     set_error(std::string("CUDA error in ") + f.where + ": " + cudaGetErrorString(f.e));
-    return PF_ECUDA;
+    return f.e == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA;
   }
   S.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (rc == PF_ENOTCONV) set_error("rmtr_load_step: max_cycles reached before the tolerance");

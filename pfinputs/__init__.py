@@ -11,6 +11,10 @@ Fracture rows (host arrays, float64):
   the 2D "smooth rectangle" of Sec. 5.2 before regularisation.
 * ``DISC3D``  -> ``[cx, cy, cz, nx, ny, nz, radius]``: a penny-shaped crack
   with unit normal ``n`` (the 3D workload's fracture shape).
+* ``BOX3D``   -> ``[cx, cy, cz, nx, ny, nz, ax, ay, az, bx, by, bz, ha, hb]``:
+  a rectangular plate with unit normal ``n``, orthonormal in-plane axes
+  ``a``, ``b`` and half-lengths ``ha``, ``hb`` (the paper's 3D "smooth
+  parallelepipeds" once widened to the band).
 
 Workload recipes (Sec. 5.2 describes the paper's generator: uniform
 hypocentres, bounded orientations, power-law lengths; the sizes here are the
@@ -28,6 +32,7 @@ import numpy as np
 
 LINE2D = 0
 DISC3D = 1
+BOX3D = 2
 
 # seed convention: 1000 + 100 * workload + instance
 SEED_2D_PLAIN = 1000
@@ -35,6 +40,7 @@ SEED_3D_PLAIN = 1100
 SEED_3D_MIXED = 1200
 SEED_2D_BATCHED = 1300
 SEED_2D_LEARNED = 1400
+SEED_3D_PAPER = 1500
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -57,6 +63,39 @@ def disc_network_3d(seed: int, n: int, rmin: float = 0.03, rmax: float = 0.1) ->
         out[k, 0:3] = cen
         out[k, 3:6] = nv
         out[k, 6] = r
+    return out
+
+
+def box_network_3d(seed: int, n: int, lmin: float = 0.05, lmax: float = 0.25,
+                   exponent: float = 2.0) -> np.ndarray:
+    """n rectangular plates: centre U[0,1]^3, normal uniform on the sphere
+    (normalised Gaussian triple), in-plane axis at a uniform angle, side
+    length from the power law p(l) ~ l^-exponent on [lmin, lmax] (inverse
+    transform), second side U[0.5, 1] times the first."""
+    g = rng(seed)
+    out = np.empty((n, 14), dtype=np.float64)
+    for k in range(n):
+        cen = g.uniform(0.0, 1.0, size=3)
+        nv = g.standard_normal(3)
+        nv = nv / np.sqrt(np.dot(nv, nv))
+        # an orthonormal pair in the plane, then a uniform rotation in it
+        helper = np.array([1.0, 0.0, 0.0]) if abs(nv[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+        e1 = helper - np.dot(helper, nv) * nv
+        e1 = e1 / np.sqrt(np.dot(e1, e1))
+        e2 = np.cross(nv, e1)
+        phi = g.uniform(0.0, np.pi)
+        av = np.cos(phi) * e1 + np.sin(phi) * e2
+        bv = np.cross(nv, av)
+        u = g.uniform()
+        a1 = 1.0 - exponent
+        length = (lmin ** a1 + u * (lmax ** a1 - lmin ** a1)) ** (1.0 / a1)
+        width = length * g.uniform(0.5, 1.0)
+        out[k, 0:3] = cen
+        out[k, 3:6] = nv
+        out[k, 6:9] = av
+        out[k, 9:12] = bv
+        out[k, 12] = 0.5 * length
+        out[k, 13] = 0.5 * width
     return out
 
 

@@ -195,6 +195,13 @@ def test_raster_discs_full_size(pf):
     assert c.sum() > 1000
 
 
+def test_raster_boxes_full_size(pf):
+    """100 plates of the paper-scale network on the 129^3 grid, bit-exact."""
+    rows = PI.box_network_3d(PI.SEED_3D_PAPER, 100)
+    c = _raster_pair(pf, 3, (17, 17, 17), 4, 1 / 16, pf.PF_BOX3D, rows)
+    assert c.sum() > 10000
+
+
 def _sampled_nodes(g, n, seed):
     r = PI.rng(seed)
     nodes = r.choice(g.N, size=n, replace=False)

@@ -237,6 +237,30 @@ def test_disc_rasterisation_counts_lattice_points():
     assert c.sum() == 26
 
 
+def test_box_rasterisation_counts_lattice_points():
+    """An axis-aligned plate (normal z, sides along x and y) centred on a
+    node of the 1/64 grid: the band |dz| <= h holds 3 planes, |dx| <= 0.1
+    holds 2 floor(6.4) + 1 = 13 columns and |dy| <= 0.05 holds
+    2 floor(3.2) + 1 = 7 rows: 273 nodes.  Rotating the in-plane axes by 90
+    degrees exchanges the two extents (same count, transposed footprint);
+    tilting the plate onto the x-z plane moves the band to 3 y-rows."""
+    g = O.Grid(3, (65, 65, 65), 1 / 64)
+    box = np.array([[0.5, 0.5, 0.5, 0, 0, 1, 1, 0, 0, 0, 1, 0, 0.1, 0.05]], dtype=float)
+    c = O.rasterize(g, O.BOX3D, box, g.h).reshape(65, 65, 65)  # [z, y, x]
+    assert c.sum() == 273
+    assert list(np.where(c.any(axis=(1, 2)))[0]) == [31, 32, 33]
+    assert list(np.where(c.any(axis=(0, 1)))[0]) == list(range(26, 39))
+    assert list(np.where(c.any(axis=(0, 2)))[0]) == list(range(29, 36))
+    rot = box.copy()
+    rot[0, 6:12] = [0, 1, 0, -1, 0, 0]
+    cr = O.rasterize(g, O.BOX3D, rot, g.h).reshape(65, 65, 65)
+    assert cr.sum() == 273 and np.array_equal(cr, np.transpose(c, (0, 2, 1)))
+    tilt = box.copy()
+    tilt[0, 3:12] = [0, 1, 0, 1, 0, 0, 0, 0, 1]
+    ct = O.rasterize(g, O.BOX3D, tilt, g.h).reshape(65, 65, 65)
+    assert ct.sum() == 273 and list(np.where(ct.any(axis=(0, 2)))[0]) == [31, 32, 33]
+
+
 # ---------------------------------------------------------------- solver pins
 def _closed_form_profile(m, h, ls):
     """Exact minimiser of the 1D Q1 AT2 energy right of a c = 1 band:
