@@ -256,6 +256,24 @@ pf_status pf_hessvec(pf_hierarchy* h, int level, const void* x_lin_dev, const vo
 pf_status pf_hessvec_lag_set(pf_hierarchy* h, int level, const void* x_lag_dev, int prec);
 pf_status pf_hessvec_lagged(pf_hierarchy* h, int level, const void* v_dev, void* Hv_dev, int prec);
 
+/* Stored Galerkin coarse operators (eq. (second_order_consistency) with
+ * eq. (delta_terms) under Hessian lagging, Sec. 4.2.1): the model Hessian of
+ * coarse level l is G^l = R G^{l+1} I, G^{L-1} = H(x_lag) of the finest
+ * level.  pf_galerkin_set builds every coarse level's G^l from the finest
+ * lag point x_lag_fine_dev (FP32, (dim+1) N_finest values) as an FP32
+ * 3^d-point block stencil: element matrices of the next-to-finest level by
+ * integrating the coarse Q1 basis against the fine Gauss-point Hessian
+ * density of x_lag, then I^T K I element by element for coarser levels,
+ * then a fixed-order assembly (deterministic).  The mixed-precision solver
+ * builds them itself once per V-cycle when coarse_model = PF_GALERKIN.
+ * pf_galerkin_apply applies level's G^l (level < n_levels-1) to v_dev
+ * (precision prec; FP32 sums for FP32 vectors, FP64 sums of the FP32
+ * entries for FP64).  Memory: per coarse level 4 (2^d (d+1))^2 bytes per
+ * element and 4 (3^d (d+1)^2) bytes per node, allocated on first use.
+ * Errors: PF_EINVAL, PF_ESTATE (apply before set), PF_ENOMEM, PF_ECUDA. */
+pf_status pf_galerkin_set(pf_hierarchy* h, const float* x_lag_fine_dev);
+pf_status pf_galerkin_apply(pf_hierarchy* h, int level, const void* v_dev, void* Hv_dev, int prec);
+
 /* Transfers between level `coarse` and coarse+1 (Sec. 3), per plane:
  * prolong: Q1 interpolation I (fine = I coarse);
  * restrict: R = I^T (coarse = R fine);

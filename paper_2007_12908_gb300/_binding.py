@@ -35,7 +35,7 @@ EXPORTS = [
     "pf_unet_backward", "pf_unet_mse", "pf_unet_adam", "pf_learned_features", "pf_learned_target",
     "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient", "pf_rmtr_load_step_batch",
     "pf_energy_diff_mixed", "pf_gradient_step", "pf_gradient_df", "pf_energy_df",
-    "pf_state_save", "pf_state_load",
+    "pf_state_save", "pf_state_load", "pf_galerkin_set", "pf_galerkin_apply",
 ]
 
 
@@ -115,6 +115,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_get_c_prev": (i, [vp, vp]),
         "pf_state_save": (i, [vp, vp, C.c_char_p]),
         "pf_state_load": (i, [vp, vp, C.c_char_p]),
+        "pf_galerkin_set": (i, [vp, vp]),
+        "pf_galerkin_apply": (i, [vp, i, vp, vp, i]),
         "pf_probe_fma": (i, [i, C.POINTER(d)]),
         "pf_energy_noalloc": (i, [i, C.POINTER(C.c_int), d, d, d, d, d, d, d, vp, i, vp, vp]),
         "pf_hessvec_lag_set": (i, [vp, i, vp, i]),
@@ -450,6 +452,23 @@ def state_load(H: Hierarchy, x, path):
     import torch
     _check(lib().pf_state_load(H.handle, _dev(x, H.ndof(), torch.float64), os.fsencode(path)))
     return x
+
+
+def galerkin_set(H: Hierarchy, x_lag_fine):
+    """Builds the stored FP32 Galerkin operators R G I of every coarse level
+    from the finest level's lag point (a float32 CUDA tensor)."""
+    import torch
+    _check(lib().pf_galerkin_set(H.handle, _dev(x_lag_fine, H.ndof(), torch.float32)))
+
+
+def galerkin_apply(H: Hierarchy, level: int, v, out=None):
+    """The stored Galerkin operator of coarse level `level` applied to v
+    (float32 or float64 CUDA tensor of that level's size)."""
+    import torch
+    n = H.ndof(level)
+    out = torch.empty_like(v) if out is None else out
+    _check(lib().pf_galerkin_apply(H.handle, level, _dev(v, n), _dev(out, n, v.dtype), _prec(v)))
+    return out
 
 
 def probe_fma(prec: int) -> float:

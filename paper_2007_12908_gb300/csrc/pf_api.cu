@@ -47,6 +47,34 @@ cudaError_t ensure_stencil(pf_hierarchy* h, int l) {
   B.stencil = static_cast<double*>(p);
   return cudaSuccess;
 }
+cudaError_t ensure_galerkin(pf_hierarchy* h, int l) {
+  LevelBuf& B = h->lv[l];
+  if (B.gs) return cudaSuccess;
+  void *k = nullptr, *sg = nullptr;
+  cudaError_t e = cudaMalloc(&k, sizeof(float) * galerkin_elem_count(h->geo[l]));
+  if (e != cudaSuccess) return e;
+  h->allocations.push_back(k);
+  e = cudaMalloc(&sg, sizeof(float) * galerkin_stencil_count(h->geo[l]));
+  if (e != cudaSuccess) return e;
+  h->allocations.push_back(sg);
+  B.gk = static_cast<float*>(k);
+  B.gs = static_cast<float*>(sg);
+  return cudaSuccess;
+}
+
+cudaError_t galerkin_build(pf_hierarchy* h, const float* x_fine, cudaStream_t st) {
+  const int L = h->L;
+  for (int l = 0; l < L - 1; ++l) {
+    cudaError_t e = ensure_galerkin(h, l);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = galerkin_fine(h->geo[L - 2], h->geo[L - 1], h->mat[L - 1], x_fine, h->lv[L - 2].gk, st);
+  for (int l = L - 3; l >= 0 && e == cudaSuccess; --l)
+    e = galerkin_rap(h->geo[l], h->geo[l + 1], h->lv[l + 1].gk, h->lv[l].gk, st);
+  for (int l = 0; l <= L - 2 && e == cudaSuccess; ++l)
+    e = galerkin_assemble(h->geo[l], h->lv[l].gk, h->lv[l].gs, st);
+  return e;
+}
 }  // namespace pf
 
 template <class T>
@@ -451,6 +479,26 @@ pf_status pf_hessvec_lag_set(pf_hierarchy* h, int level, const void* x, int prec
     PF_TRY_CUDA(cudaMemcpyAsync(B.xlag32, x, sizeof(float) * B.n, cudaMemcpyDeviceToDevice, h->st),
                 "hessvec_lag_set");
   }
+  return PF_OK;
+}
+
+pf_status pf_galerkin_set(pf_hierarchy* h, const float* x_lag_fine) {
+  if (!h || !x_lag_fine) return bad("galerkin_set: null argument");
+  if (h->L < 2) return bad("galerkin_set: the hierarchy has no coarse level");
+  PF_TRY_CUDA(galerkin_build(h, x_lag_fine, h->st), "galerkin_set");
+  PF_TRY_CUDA(cudaStreamSynchronize(h->st), "galerkin_set");
+  return PF_OK;
+}
+
+pf_status pf_galerkin_apply(pf_hierarchy* h, int level, const void* v, void* Hv, int prec) {
+  if (!valid_level(h, level) || level >= h->L - 1 || !v || !Hv)
+    return bad("galerkin_apply: bad argument (level must be a coarse level)");
+  if (check_prec(prec)) return PF_EINVAL;
+  if (!h->lv[level].gs) {
+    set_error("galerkin_apply: no Galerkin operator built (pf_galerkin_set)");
+    return PF_ESTATE;
+  }
+  PF_TRY_CUDA(galerkin_apply(h->geo[level], h->lv[level].gs, v, Hv, prec, h->st), "galerkin_apply");
   return PF_OK;
 }
 

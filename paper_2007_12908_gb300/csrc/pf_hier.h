@@ -24,6 +24,8 @@ struct LevelBuf {
   float* xlag32 = nullptr;  // FP32 copy of x_lag (mixed precision)
   double* coef = nullptr;   // lagged Gauss-point coefficients (FP64 Hessian)
   double* stencil = nullptr;  // assembled lagged FP64 Hessian (3^d block stencil)
+  float* gk = nullptr;        // FP32 Galerkin element matrices (mixed GALERKIN coarse levels)
+  float* gs = nullptr;        // FP32 Galerkin operator as a 3^d block stencil
 };
 
 
@@ -74,4 +76,9 @@ pf_status projected_gradient_impl(pf_hierarchy* H, const double* x_dev, double* 
 void refresh_pressure(pf_hierarchy* H);
 // Allocates level l's FP64 stencil on first use (held until destroy).
 cudaError_t ensure_stencil(pf_hierarchy* H, int l);
+// Allocates level l's Galerkin element matrices and FP32 stencil on first
+// use, and builds the FP32 Galerkin operators of every coarse level from
+// the finest level's FP32 lag x (R G I chain, see pf_galerkin.cu).
+cudaError_t ensure_galerkin(pf_hierarchy* H, int l);
+cudaError_t galerkin_build(pf_hierarchy* H, const float* x_fine, cudaStream_t st);
 }  // namespace pf

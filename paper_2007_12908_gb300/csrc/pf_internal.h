@@ -168,6 +168,19 @@ cudaError_t elem_hessvec_mixed(const Geom& g, const Mat<double>& m, const float*
                                const int* skip = nullptr, void* part = nullptr,
                                const float* p_dev = nullptr);
 
+// Stored Galerkin coarse operators (pf_galerkin.cu): FP32 element
+// matrices of the next-to-finest level gc from the finest FP32 lag, their
+// element-wise coarsening, the 3^d-point FP32 stencil of a level, and its
+// product with FP32 (prec PF_FP32) or FP64 vectors.
+long long galerkin_elem_count(const Geom& g);
+long long galerkin_stencil_count(const Geom& g);
+cudaError_t galerkin_fine(const Geom& gc, const Geom& gf, const Mat<double>& mf, const float* x_fine,
+                          float* K, cudaStream_t st);
+cudaError_t galerkin_rap(const Geom& gc, const Geom& gf, const float* Kf, float* Kc, cudaStream_t st);
+cudaError_t galerkin_assemble(const Geom& g, const float* K, float* S, cudaStream_t st);
+cudaError_t galerkin_apply(const Geom& g, const float* S, const void* v, void* y, int prec,
+                           cudaStream_t st, const int* skip = nullptr);
+
 // Fracture band rasterisation into the c plane (FP64) of x and c_prev.
 // rows: device array of precomputed shape rows of kRasterRow doubles (see
 // pf_fractures_set); kind 0 line (2D), 1 disc, 2 rectangle (3D).

@@ -518,7 +518,7 @@ struct Solver {
       const double* src = B.xlag;
       map(B.n, [=] __device__(long long i) { d[i] = float(src[i]); });
     }
-    if (!mixed32(l) || galerkin(l)) {
+    if (!mixed32(l)) {
       // FP64 Hessian of this level: Gauss-point coefficients, once per lag
       ck(ensure_stencil(H, l), "FP64 stencil allocation");
       ck(elem_hess_coef(H->geo[l], H->mat[l], B.xlag, B.coef, st), "hess_coef");
@@ -559,13 +559,28 @@ struct Solver {
   // mixed precision: FP32 Hessian (and FP32 subproblem) on every level
   bool mixed32(int l) const { return mixed; }
 
+  // GALERKIN levels of the mixed mode apply their model Hessian R G^{l+1} I
+  // as a stored FP32 stencil built once per finest lag (galerkin_build)
+  bool gstored(int l) const { return mixed && galerkin(l); }
+
   // finest-level units of one application of the lagged model Hessian
-  double hlag_units(int l) const { return galerkin(l) ? hlag_units(l + 1) : frac(l); }
+  double hlag_units(int l) const {
+    return galerkin(l) && !gstored(l) ? hlag_units(l + 1) : frac(l);
+  }
 
   // Lagged model Hessian: finest / FIRST_ORDER: Hessian at x_lag of the level;
   // GALERKIN: R H_{l+1} I.  With skip, a no-op once *skip is set; count
   // false leaves the work counters to the caller.
   void Hlag(int l, const double* v, double* out, const int* skip = nullptr, bool count = true) {
+    if (gstored(l)) {
+      ck(galerkin_apply(H->geo[l], H->lv[l].gs, v, out, PF_FP64, st, skip), "galerkin_apply");
+      S.launches += 1;
+      if (count) {
+        S.hessvecs += 1;
+        S.fe_hessvec += frac(l);
+      }
+      return;
+    }
     if (!galerkin(l)) {
       LevelBuf& B = H->lv[l];
       if (mixed32(l))
@@ -593,9 +608,17 @@ struct Solver {
   void dH(int l, const double* v, double* out) {
     LevelBuf& B = H->lv[l];
     Hlag(l, v, out);
-    // the level's own Hessian at x0 (= its lag point): the assembled stencil
-    ck(stencil_apply(H->geo[l], B.stencil, v, B.dh, st), "hessvec");
-    S.launches += 1;
+    // the level's own Hessian at x0 (= its lag point): the assembled FP64
+    // stencil, or in the mixed mode the FP32 matrix-free product at x0
+    if (mixed32(l)) {
+      ck(elem_hessvec_mixed(H->geo[l], H->mat[l], B.xlag32, v, B.dh, st, nullptr, H->etile_part,
+                            H->p_dev),
+         "hessvec32");
+      S.launches += hessvec32_launches(H->geo[l], H->etile_part);
+    } else {
+      ck(stencil_apply(H->geo[l], B.stencil, v, B.dh, st), "hessvec");
+      S.launches += 1;
+    }
     S.hessvecs += 1;
     S.fe_hessvec += frac(l);
     const double* t = B.dh;
@@ -680,13 +703,20 @@ struct Solver {
   // Levels whose subproblem runs on FP32 vectors: the FP32-Hessian levels of
   // the mixed mode (GALERKIN levels apply their operator through FP64
   // transfers and keep FP64 vectors).
-  bool sub32(int l) const { return mixed32(l) && !galerkin(l); }
+  bool sub32(int l) const { return mixed32(l) && (!galerkin(l) || gstored(l)); }
 
   // The lagged model Hessian on vectors of precision V.
   template <class V>
   void hv(int l, const V* v, V* out, const int* skip = nullptr, bool count = true) {
     if constexpr (std::is_same<V, double>::value) {
       Hlag(l, v, out, skip, count);
+    } else if (gstored(l)) {
+      ck(galerkin_apply(H->geo[l], H->lv[l].gs, v, out, PF_FP32, st, skip), "galerkin_apply");
+      S.launches += 1;
+      if (count) {
+        S.hessvecs += 1;
+        S.fe_hessvec += frac(l);
+      }
     } else {
       ck(elem_hessvec(H->geo[l], H->mat[l], H->lv[l].xlag32, v, out, 1, st, skip, H->etile_part,
                       H->p_dev),
@@ -718,7 +748,7 @@ struct Solver {
     LevelBuf& B = H->lv[l];
     CgCtrl* c = H->ctrl;
     const long long n4 = pad4(B.n) / 4;
-    if (hessvec32_dot_fused(H->geo[l], H->etile_part)) {
+    if (!gstored(l) && hessvec32_dot_fused(H->geo[l], H->etile_part)) {
       // the direction update of the previous iteration (beta = 0 after a
       // restart, where p = M^-1 r already) is formed inside the product
       ck(elem_hessvec32_dot(H->geo[l], H->mat[l], B.xlag32, const_cast<float*>(p), q, c,
@@ -732,13 +762,17 @@ struct Solver {
     }
     int launches = 2;
     {
-      ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done, H->etile_part,
-                      H->p_dev),
-         "hessvec32");
+      if (gstored(l)) {
+        ck(galerkin_apply(H->geo[l], B.gs, p, q, PF_FP32, s, &c->done), "galerkin_apply");
+      } else {
+        ck(elem_hessvec(H->geo[l], H->mat[l], B.xlag32, p, q, 1, s, &c->done, H->etile_part,
+                        H->p_dev),
+           "hessvec32");
+      }
       k_cg_dot4<<<resident_grid(k_cg_dot4, n4), 256, 0, s>>>(n4, p, q, c, H->scratch.partials,
                                                               H->scratch.counter);
       ck(cudaGetLastError(), "cg_dot");
-      launches += 1 + hessvec32_launches(H->geo[l], H->etile_part);
+      launches += 1 + (gstored(l) ? 1 : hessvec32_launches(H->geo[l], H->etile_part));
     }
     k_cg_update4<<<resident_grid(k_cg_update4, n4), 256, 0, s>>>(
         n4, ga, gb, q, p, mi, pc, w, r, c, H->scratch.partials, H->scratch.counter);
@@ -1420,6 +1454,11 @@ struct Solver {
     bool conv = pg0 <= (pg_ref > 0.0 ? target : P.atol);
     while (!conv && cycles < P.max_cycles) {
       set_lag(L - 1, B.x);
+      if (L > 1 && mixed && P.coarse_model == PF_GALERKIN) {
+        // the coarse model Hessians R G I of every level, from this lag
+        ck(galerkin_build(H, B.xlag32, st), "galerkin_build");
+        S.launches += 2 * (L - 1);
+      }
       vcycle(L - 1, delta);
       ++cycles;
       pg = pg_norm(B.x);
