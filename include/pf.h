@@ -113,10 +113,21 @@ typedef struct {
                             start (pg_ref taken at x as given)               */
   double p_prev;         /* > 0: the previous pressure for
                             PF_START_EXTRAPOLATE instead of p_last           */
+  int qp_solver;         /* PF_QP_CG: projected truncated CG on every level
+                            (default); PF_QP_PAPER: the paper's QP solvers
+                            (Sec. 4.2.2): pgs_sweeps symmetric multicolour
+                            projected Gauss-Seidel sweeps on the
+                            non-coarsest levels, MPRGP (cg_coarse products)
+                            on the coarsest; needs precision PF_FP64 and
+                            coarse_model PF_FIRST_ORDER (assembled FP64
+                            Hessians on every level)                        */
+  int pgs_sweeps;        /* symmetric PGS sweeps per TR subproblem (2)      */
 } pf_rmtr_params;
 
 #define PF_START_PLAIN 0
 #define PF_START_EXTRAPOLATE 1
+#define PF_QP_CG 0
+#define PF_QP_PAPER 1
 
 typedef struct {
   int cycles;            /* V-cycles taken                                   */
@@ -273,6 +284,26 @@ pf_status pf_hessvec_lagged(pf_hierarchy* h, int level, const void* v_dev, void*
  * Errors: PF_EINVAL, PF_ESTATE (apply before set), PF_ENOMEM, PF_ECUDA. */
 pf_status pf_galerkin_set(pf_hierarchy* h, const float* x_lag_fine_dev);
 pf_status pf_galerkin_apply(pf_hierarchy* h, int level, const void* v_dev, void* Hv_dev, int prec);
+
+/* The paper's QP solvers for eq. (model_qp), min g.s + s.H s / 2 over
+ * lo <= s <= hi (Sec. 4.2.2), on `level` with H the level's lagged FP64
+ * Hessian as assembled by pf_hessvec_lag_set(..., PF_FP64) (else
+ * PF_ESTATE).  All vectors FP64 device arrays of the level's size.
+ * pf_qp_pgs: `sweeps` symmetric multicolour projected Gauss-Seidel sweeps
+ * on s_inout (colours = node parity classes 0 .. 2^d-1, fields of a node
+ * in order, then colours and fields reversed; s_i <- clamp(s_i -
+ * (g + H s)_i / H_ii, lo_i, hi_i) where H_ii > 0).  Deterministic: nodes of
+ * one colour do not couple.
+ * pf_qp_mprgp: MPRGP (modified proportioning with reduced gradient
+ * projections) from s = 0 on the diagonally scaled problem, the expansion
+ * step length 1 / (Gershgorin bound of the scaled H); stops when the
+ * projected gradient's norm <= tol or after maxit products; the result to
+ * s_out, the products used to *products_host (may be NULL). */
+pf_status pf_qp_pgs(pf_hierarchy* h, int level, const double* g_dev, const double* lo_dev,
+                    const double* hi_dev, double* s_inout_dev, int sweeps);
+pf_status pf_qp_mprgp(pf_hierarchy* h, int level, const double* g_dev, const double* lo_dev,
+                      const double* hi_dev, double* s_out_dev, double tol, int maxit,
+                      int* products_host);
 
 /* Transfers between level `coarse` and coarse+1 (Sec. 3), per plane:
  * prolong: Q1 interpolation I (fine = I coarse);

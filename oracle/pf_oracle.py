@@ -568,6 +568,9 @@ class TRParams:
     pg_ref: float = 0.0         # > 0: stopping test relative to this instead of the start
     level_rtol: float = 1e-3    # non-finest levels stop their TR loop once the
                                 # level's projected gradient fell by this factor
+    qp_solver: int = 0          # 0: projected truncated CG; 1: the paper's QP
+                                # solvers (PGS sweeps, MPRGP on the coarsest)
+    pgs_sweeps: int = 2         # symmetric PGS sweeps per subproblem
 
 
 def proj_box(s, lo, hi):
@@ -707,6 +710,190 @@ def solve_subproblem(g, Hv, lo, hi, delta, cg_max, tr: TRParams, stats=None, min
         if restarts > tr.max_restarts:
             break
     return proj_box(s, lo, hi)
+
+
+# --------------------------------------------------------------------------
+# the paper's QP solvers for eq. (model_qp) (Sec. 4.2.2): a few sweeps of
+# symmetric projected Gauss-Seidel on the non-coarsest levels, MPRGP on the
+# coarsest level
+# --------------------------------------------------------------------------
+def probe_sparse(grid: Grid, Hv) -> sp.csr_matrix:
+    """The (3^d-point block) matrix of the linear map Hv, recovered by
+    probing: nodes with equal coordinates mod 3 are at least 3 apart, so
+    their neighbourhoods do not overlap, and one product per (colour, field)
+    gives all their columns."""
+    d, N = grid.dim, grid.N
+    F = d + 1
+    ij = grid.node_coords()
+    colour = np.zeros(N, dtype=np.int64)
+    for k in range(d):
+        colour += (ij[k] % 3) * 3 ** k
+    rows, cols, vals = [], [], []
+    # neighbours of every node (within one index per axis)
+    for c in range(3 ** d):
+        nodes = np.where(colour == c)[0]
+        for f in range(F):
+            v = np.zeros(F * N)
+            v[f * N + nodes] = 1.0
+            y = Hv(v)
+            nz = np.nonzero(y)[0]
+            # the node that owns the nonzero y[r]: the colour-c node within
+            # one index of r's node on every axis
+            rn = nz % N
+            rij = ij[:, rn]
+            owner = np.zeros(len(nz), dtype=np.int64)
+            for k in range(d):
+                # the owner's coordinate on axis k is the one of rij-1, rij, rij+1 with the right residue
+                want = (c // 3 ** k) % 3
+                cand = rij[k] + ((want - rij[k]) % 3 + 1) % 3 - 1
+                owner += cand * (np.prod(grid.n[:k]) if k else 1)
+            rows.append(nz)
+            cols.append(f * N + owner)
+            vals.append(y[nz])
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(F * N, F * N))
+    return A
+
+
+def node_parity_colours(grid: Grid) -> np.ndarray:
+    """Colour of every node: sum_k (i_k mod 2) 2^k.  Nodes of one colour are
+    at least 2 apart on some axis, so no 3^d-point stencil couples them."""
+    ij = grid.node_coords()
+    col = np.zeros(grid.N, dtype=np.int64)
+    for k in range(grid.dim):
+        col += (ij[k] % 2) << k
+    return col
+
+
+def pgs_sweeps(A: sp.csr_matrix, grid: Grid, g, lo, hi, sweeps, s=None):
+    """Symmetric multicolour projected Gauss-Seidel for min g.s + 1/2 s.As,
+    lo <= s <= hi (Sec. 4.2.2; the colouring is the parallel form of
+    Gauss-Seidel the paper names for GPUs).  One sweep: colours
+    0 .. 2^d-1 with the fields of a node in order 0 .. d, then colours
+    2^d-1 .. 0 with fields d .. 0; each dof i takes
+    s_i <- clamp(s_i - (g + A s)_i / A_ii, lo_i, hi_i) (skipped where
+    A_ii <= 0), with the latest values of all others."""
+    d, N = grid.dim, grid.N
+    F = d + 1
+    s = np.zeros_like(g) if s is None else s.copy()
+    diag = A.diagonal()
+    col = node_parity_colours(grid)
+    order = [(c, f) for c in range(1 << d) for f in range(F)]
+    for _ in range(sweeps):
+        for c, f in order + order[::-1]:
+            idx = f * N + np.where(col == c)[0]
+            r = g[idx] + A[idx] @ s
+            dd = diag[idx]
+            pos = dd > 0.0
+            new = s[idx].copy()
+            new[pos] = np.minimum(np.maximum(s[idx][pos] - r[pos] / dd[pos], lo[idx][pos]), hi[idx][pos])
+            s[idx] = new
+    return s
+
+
+QP_CG = 0
+QP_PAPER = 1
+
+
+def mprgp(Hv, g, lo, hi, dscale, tol, maxit, gamma=1.0, lam_max=None):
+    """MPRGP (Dostal's modified proportioning with reduced gradient
+    projections) for min g.s + 1/2 s.Hs, lo <= s <= hi, on the diagonally
+    scaled problem y = D^(1/2) s (D = dscale, the positive diagonal; 1 where
+    it is not): A = D^(-1/2) H D^(-1/2), b = -D^(-1/2) g.  Steps:
+    - proportional iterate (||beta||^2 <= gamma^2 phi~.phi): a CG step on
+      the free set if it stays feasible, else an expansion step (the
+      feasible part of it, then a projected gradient step of length abar on
+      the free gradient) and a CG restart;
+    - otherwise a proportioning step along the chopped gradient beta.
+    Stops when ||phi + beta|| <= tol (tol None: the forcing tolerance
+    min(0.1, sqrt(|nu0|)) |nu0| of the first projected gradient nu0) or
+    after maxit products.  abar = 1 / lam_max (lam_max: an upper estimate of
+    ||A||).  Returns s."""
+    sq = np.sqrt(dscale)
+    A = lambda y: Hv(y / sq) / sq
+    b = -g / sq
+    l, u = lo * sq, hi * sq
+    y = np.minimum(np.maximum(np.zeros_like(g), l), u)
+    abar = 1.0 / lam_max
+
+    def split(y, gr):
+        # free: strictly inside; chopped: on a bound of a dof that can move
+        # (l < u), pointing out of the box; fixed dofs (l = u) count in neither
+        free = (l < y) & (y < u)
+        movable = l < u
+        beta = np.where(~free & movable & (y <= l), np.minimum(gr, 0.0), 0.0) + \
+            np.where(~free & movable & (y >= u), np.maximum(gr, 0.0), 0.0)
+        phi = np.where(free, gr, 0.0)
+        # reduced free gradient for the proportionality test
+        pt = np.where(phi > 0, np.minimum((y - l) / abar, phi), np.maximum((y - u) / abar, phi))
+        pt = np.where(free, pt, 0.0)
+        return free, phi, beta, pt
+
+    gr = A(y) - b
+    used = 1
+    free, phi, beta, pt = split(y, gr)
+    p = phi.copy()
+    if tol is None:
+        nu0 = float(np.linalg.norm(phi + beta))
+        tol = min(0.1, math.sqrt(nu0)) * nu0
+    while used < maxit and np.linalg.norm(phi + beta) > tol:
+        if float(beta @ beta) <= gamma * gamma * float(pt @ phi):
+            Ap = A(p)
+            used += 1
+            pAp = float(p @ Ap)
+            if pAp <= 0.0:
+                break
+            acg = float(gr @ p) / pAp
+            # largest feasible step along -p
+            with np.errstate(divide="ignore", invalid="ignore"):
+                af = np.min(np.where(p > 0, (y - l) / p, np.where(p < 0, (y - u) / p, np.inf)))
+            if acg <= af:
+                y = y - acg * p
+                gr = gr - acg * Ap
+                free, phi, beta, pt = split(y, gr)
+                gam = float(phi @ Ap) / pAp
+                p = phi - gam * p
+            else:
+                y = y - af * p
+                gr = gr - af * Ap
+                free, phi, _, _ = split(y, gr)
+                y = np.minimum(np.maximum(y - abar * phi, l), u)
+                gr = A(y) - b
+                used += 1
+                free, phi, beta, pt = split(y, gr)
+                p = phi.copy()
+        else:
+            d = beta
+            Ad = A(d)
+            used += 1
+            dAd = float(d @ Ad)
+            if dAd <= 0.0:
+                break
+            a = float(gr @ d) / dAd
+            y = y - a * d
+            gr = gr - a * Ad
+            free, phi, beta, pt = split(y, gr)
+            p = phi.copy()
+    return y / sq
+
+
+def paper_subproblem(model, g, lo, hi, tr: TRParams, stats=None):
+    """The TR subproblem eq. (model_qp) with the paper's QP solvers
+    (Sec. 4.2.2): MPRGP on the coarsest level (cg_coarse products, forcing
+    tolerance, expansion step from the Gershgorin bound of the diagonally
+    scaled Hessian), tr.pgs_sweeps symmetric PGS sweeps from s = 0 on the
+    other levels.  The level's lagged model Hessian is taken as a sparse
+    matrix by probing, once per lag."""
+    if not hasattr(model, "_sparse"):
+        model._sparse = probe_sparse(model.H.grids[model.level], model.Hlag)
+    A = model._sparse
+    if model.level == 0:
+        dd = A.diagonal()
+        dd = np.where(dd > 0.0, dd, 1.0)
+        sq = np.sqrt(dd)
+        lam = float(np.max(np.asarray(abs(sp.diags(1 / sq) @ A @ sp.diags(1 / sq)).sum(axis=1)).ravel()))
+        return mprgp(lambda v: A @ v, g, lo, hi, dd, None, tr.cg_coarse, lam_max=lam)
+    return pgs_sweeps(A, model.H.grids[model.level], g, lo, hi, tr.pgs_sweeps)
 
 
 # --------------------------------------------------------------------------
@@ -855,7 +1042,10 @@ def nonlinear_solve(model: LevelModel, x0, lb, ub, delta0, iters, cg_max, tr: TR
                 break
         lo = np.maximum(lb - x, -delta)
         hi = np.minimum(ub - x, delta)
-        s = solve_subproblem(g, model.Hlag, lo, hi, delta, cg_max, tr, stats, minv)
+        if tr.qp_solver == QP_PAPER:
+            s = paper_subproblem(model, g, lo, hi, tr, stats)
+        else:
+            s = solve_subproblem(g, model.Hlag, lo, hi, delta, cg_max, tr, stats, minv)
         pred = -(float(g @ s) + 0.5 * float(s @ model.Hlag(s)))
         stats["hessvecs"] += 1
         stats["tr_its"] += 1

@@ -19,6 +19,7 @@ PF_FP64, PF_FP32 = 0, 1
 PF_GALERKIN, PF_FIRST_ORDER = 0, 1
 PF_LINE2D, PF_DISC3D, PF_BOX3D = 0, 1, 2
 PF_START_PLAIN, PF_START_EXTRAPOLATE = 0, 1
+PF_QP_CG, PF_QP_PAPER = 0, 1
 
 STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_ENONFINITE",
                 5: "PF_ENOTCONV", 6: "PF_ETIMEOUT", 7: "PF_ESTATE", 8: "PF_EIO"}
@@ -35,7 +36,8 @@ EXPORTS = [
     "pf_unet_backward", "pf_unet_mse", "pf_unet_adam", "pf_learned_features", "pf_learned_target",
     "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient", "pf_rmtr_load_step_batch",
     "pf_energy_diff_mixed", "pf_gradient_step", "pf_gradient_df", "pf_energy_df",
-    "pf_state_save", "pf_state_load", "pf_galerkin_set", "pf_galerkin_apply",
+    "pf_state_save", "pf_state_load", "pf_galerkin_set", "pf_galerkin_apply", "pf_qp_pgs",
+    "pf_qp_mprgp",
 ]
 
 
@@ -56,7 +58,8 @@ class RmtrParams(C.Structure):
                 ("coarse_model", C.c_int), ("precision", C.c_int),
                 ("precondition", C.c_int), ("level_rtol", C.c_double),
                 ("max_restarts", C.c_int), ("keep_c_prev", C.c_int), ("pg_ref", C.c_double),
-                ("start", C.c_int), ("p_prev", C.c_double)]
+                ("start", C.c_int), ("p_prev", C.c_double), ("qp_solver", C.c_int),
+                ("pgs_sweeps", C.c_int)]
 
 
 class RmtrStats(C.Structure):
@@ -116,6 +119,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_state_save": (i, [vp, vp, C.c_char_p]),
         "pf_state_load": (i, [vp, vp, C.c_char_p]),
         "pf_galerkin_set": (i, [vp, vp]),
+        "pf_qp_pgs": (i, [vp, i, vp, vp, vp, vp, i]),
+        "pf_qp_mprgp": (i, [vp, i, vp, vp, vp, vp, d, i, C.POINTER(C.c_int)]),
         "pf_galerkin_apply": (i, [vp, i, vp, vp, i]),
         "pf_probe_fma": (i, [i, C.POINTER(d)]),
         "pf_energy_noalloc": (i, [i, C.POINTER(C.c_int), d, d, d, d, d, d, d, vp, i, vp, vp]),
@@ -452,6 +457,28 @@ def state_load(H: Hierarchy, x, path):
     import torch
     _check(lib().pf_state_load(H.handle, _dev(x, H.ndof(), torch.float64), os.fsencode(path)))
     return x
+
+
+def qp_pgs(H: Hierarchy, level: int, g, lo, hi, s, sweeps):
+    """Symmetric multicolour projected Gauss-Seidel sweeps on s (in place)
+    with the level's lagged FP64 stencil (pf_hessvec_lag_set first)."""
+    import torch
+    n = H.ndof(level)
+    _check(lib().pf_qp_pgs(H.handle, level, _dev(g, n, torch.float64), _dev(lo, n, torch.float64),
+                           _dev(hi, n, torch.float64), _dev(s, n, torch.float64), sweeps))
+    return s
+
+
+def qp_mprgp(H: Hierarchy, level: int, g, lo, hi, tol, maxit, out=None):
+    """MPRGP on the level's lagged FP64 stencil; returns (s, products)."""
+    import torch
+    n = H.ndof(level)
+    out = torch.empty_like(g) if out is None else out
+    used = C.c_int()
+    _check(lib().pf_qp_mprgp(H.handle, level, _dev(g, n, torch.float64), _dev(lo, n, torch.float64),
+                             _dev(hi, n, torch.float64), _dev(out, n, torch.float64), float(tol),
+                             int(maxit), C.byref(used)))
+    return out, used.value
 
 
 def galerkin_set(H: Hierarchy, x_lag_fine):

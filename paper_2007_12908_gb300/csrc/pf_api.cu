@@ -122,6 +122,8 @@ void pf_rmtr_params_default(pf_rmtr_params* p) {
   p->pg_ref = 0.0;
   p->start = PF_START_PLAIN;
   p->p_prev = 0.0;
+  p->qp_solver = PF_QP_CG;
+  p->pgs_sweeps = 2;
 }
 
 const char* pf_last_error(void) { return g_last_error.c_str(); }
@@ -482,6 +484,27 @@ pf_status pf_hessvec_lag_set(pf_hierarchy* h, int level, const void* x, int prec
   return PF_OK;
 }
 
+pf_status pf_qp_pgs(pf_hierarchy* h, int level, const double* g, const double* lo, const double* hi,
+                    double* s, int sweeps) {
+  if (!valid_level(h, level) || !g || !lo || !hi || !s || sweeps < 1) return bad("qp_pgs: bad argument");
+  if (!h->lv[level].stencil) {
+    set_error("qp_pgs: no FP64 lag set on this level (pf_hessvec_lag_set)");
+    return PF_ESTATE;
+  }
+  return qp_impl(h, level, g, lo, hi, s, sweeps, 0.0, 0, nullptr);
+}
+
+pf_status pf_qp_mprgp(pf_hierarchy* h, int level, const double* g, const double* lo, const double* hi,
+                      double* s, double tol, int maxit, int* products) {
+  if (!valid_level(h, level) || !g || !lo || !hi || !s || maxit < 1 || !(tol >= 0))
+    return bad("qp_mprgp: bad argument");
+  if (!h->lv[level].stencil) {
+    set_error("qp_mprgp: no FP64 lag set on this level (pf_hessvec_lag_set)");
+    return PF_ESTATE;
+  }
+  return qp_impl(h, level, g, lo, hi, s, 0, tol, maxit, products);
+}
+
 pf_status pf_galerkin_set(pf_hierarchy* h, const float* x_lag_fine) {
   if (!h || !x_lag_fine) return bad("galerkin_set: null argument");
   if (h->L < 2) return bad("galerkin_set: the hierarchy has no coarse level");
@@ -563,8 +586,12 @@ static pf_status check_params(const pf_rmtr_params& P) {
       (P.precision != PF_FP64 && P.precision != PF_FP32) ||
       (P.precondition != 0 && P.precondition != 1) || !(P.level_rtol >= 0 && P.level_rtol < 1) ||
       P.max_restarts < 0 || (P.keep_c_prev != 0 && P.keep_c_prev != 1) || !(P.pg_ref >= 0) ||
-      (P.start != PF_START_PLAIN && P.start != PF_START_EXTRAPOLATE) || !(P.p_prev >= 0))
+      (P.start != PF_START_PLAIN && P.start != PF_START_EXTRAPOLATE) || !(P.p_prev >= 0) ||
+      (P.qp_solver != PF_QP_CG && P.qp_solver != PF_QP_PAPER) || P.pgs_sweeps < 1)
     return bad("rmtr_load_step: invalid parameters");
+  if (P.qp_solver == PF_QP_PAPER && (P.precision != PF_FP64 || P.coarse_model != PF_FIRST_ORDER))
+    return bad("rmtr_load_step: the paper's QP solvers need precision PF_FP64 and coarse_model "
+               "PF_FIRST_ORDER (assembled FP64 Hessians on every level)");
   return PF_OK;
 }
 

@@ -73,6 +73,9 @@ namespace pf {
 pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_params& P,
                               pf_rmtr_stats* stats);
 pf_status projected_gradient_impl(pf_hierarchy* H, const double* x_dev, double* out);
+// sweeps > 0: PGS sweeps on s; else MPRGP into s (tol, maxit, *products)
+pf_status qp_impl(pf_hierarchy* H, int level, const double* g, const double* lo, const double* hi,
+                  double* s, int sweeps, double tol, int maxit, int* products);
 void refresh_pressure(pf_hierarchy* H);
 // Allocates level l's FP64 stencil on first use (held until destroy).
 cudaError_t ensure_stencil(pf_hierarchy* H, int l);

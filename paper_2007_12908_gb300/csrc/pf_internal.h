@@ -158,6 +158,12 @@ cudaError_t stencil_assemble(const Geom& g, const Mat<double>& m, const double* 
                              cudaStream_t st);
 cudaError_t stencil_apply(const Geom& g, const double* S, const double* v, double* y,
                           cudaStream_t st, const int* skip = nullptr);
+// One half of a symmetric multicolour projected Gauss-Seidel sweep with the
+// FP64 stencil S (colours in order, or reversed with fields reversed), and
+// the row sums of the diagonally scaled |S| (a Gershgorin bound).
+cudaError_t pgs_sweep(const Geom& g, const double* S, const double* gv, const double* lo,
+                      const double* hi, double* s, bool reverse, cudaStream_t st);
+cudaError_t scaled_rowsum(const Geom& g, const double* S, double* out, cudaStream_t st);
 // Diagonal of the Hessian at x (precision prec), written as FP64.
 cudaError_t elem_hessdiag(const Geom& g, const Mat<double>& m, const void* x, int prec,
                           double* y, cudaStream_t st);

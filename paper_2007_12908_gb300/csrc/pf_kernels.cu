@@ -1133,6 +1133,120 @@ __global__ void __launch_bounds__(128) k_stencil_apply_rows(Geom g, const double
   }
 }
 
+// Projected Gauss-Seidel on the nodes of one parity colour (i_k mod 2 =
+// bit k of `colour`): nodes of one colour are not coupled by the 3^d-point
+// stencil, so they update in parallel exactly as one after another.  Each
+// node updates its fields in order (reverse: in reverse order), each with
+// the latest values of the node's other fields:
+// s_f <- clamp(s_f - (g_f + (S s)_f) / S_ff, lo_f, hi_f) where S_ff > 0.
+template <int D>
+__global__ void __launch_bounds__(128) k_pgs_colour(Geom g, const double* __restrict__ S,
+                                                    const double* __restrict__ gv,
+                                                    const double* __restrict__ lo,
+                                                    const double* __restrict__ hi, double* s,
+                                                    int colour, int reverse) {
+  constexpr int F = D + 1, NO = D == 3 ? 27 : 9, CENTER = D == 3 ? 13 : 4;
+  const int cx = colour & 1, cy = (colour >> 1) & 1, cz = D == 3 ? (colour >> 2) & 1 : 0;
+  const int mx = (g.n[0] - cx + 1) / 2, my = (g.n[1] - cy + 1) / 2;
+  const int mz = D == 3 ? (g.n[2] - cz + 1) / 2 : 1;
+  const long long total = (long long)mx * my * mz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ix = 2 * int(t % mx) + cx;
+    const int iy = 2 * int((t / mx) % my) + cy;
+    const int iz = D == 3 ? 2 * int(t / ((long long)mx * my)) + cz : 0;
+    const long long i = ix + (long long)g.n[0] * (iy + (long long)g.n[1] * iz);
+    double own[F];
+#pragma unroll
+    for (int h = 0; h < F; ++h) own[h] = s[h * g.N + i];
+    // r = g + S s without the node's own (centre) block, then each field
+    // adds the centre block's row with the node's latest values
+    double r[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) r[f] = gv[f * g.N + i];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      if (o == CENTER) continue;
+      const int jx = ix + o % 3 - 1, jy = iy + (o / 3) % 3 - 1, jz = D == 3 ? iz + o / 9 - 1 : 0;
+      if (jx < 0 || jx >= g.n[0] || jy < 0 || jy >= g.n[1] || jz < 0 || jz >= g.n[2]) continue;
+      const long long j = jx + g.n[0] * (jy + (long long)g.n[1] * jz);
+#pragma unroll
+      for (int h = 0; h < F; ++h) {
+        const double sj = s[h * g.N + j];
+#pragma unroll
+        for (int f = 0; f < F; ++f) r[f] += S[((long long)(o * F + f) * F + h) * g.N + i] * sj;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+      const int f = reverse ? F - 1 - k : k;
+      double rf = r[f];
+#pragma unroll
+      for (int h = 0; h < F; ++h) rf += S[((long long)(CENTER * F + f) * F + h) * g.N + i] * own[h];
+      const double d = S[((long long)(CENTER * F + f) * F + f) * g.N + i];
+      if (d > 0.0) own[f] = fmin(fmax(own[f] - rf / d, lo[f * g.N + i]), hi[f * g.N + i]);
+    }
+#pragma unroll
+    for (int h = 0; h < F; ++h) s[h * g.N + i] = own[h];
+  }
+}
+
+cudaError_t pgs_sweep(const Geom& g, const double* S, const double* gv, const double* lo,
+                      const double* hi, double* s, bool reverse, cudaStream_t st) {
+  const int nc = 1 << g.dim;
+  for (int k = 0; k < nc; ++k) {
+    const int colour = reverse ? nc - 1 - k : k;
+    const long long nodes = (g.N + nc - 1) / nc + g.n[0] * g.n[1];
+    const int nb = int(std::min<long long>((nodes + 127) / 128, 16LL * 1216));
+    if (g.dim == 3) k_pgs_colour<3><<<nb, 128, 0, st>>>(g, S, gv, lo, hi, s, colour, reverse ? 1 : 0);
+    else k_pgs_colour<2><<<nb, 128, 0, st>>>(g, S, gv, lo, hi, s, colour, reverse ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
+// Row sums of |D^-1/2 S D^-1/2| (D the positive diagonal of S, 1 where it is
+// not): out[row] for every dof, whose maximum bounds the scaled operator's
+// largest eigenvalue (Gershgorin).
+template <int D>
+__global__ void __launch_bounds__(128) k_scaled_rowsum(Geom g, const double* __restrict__ S,
+                                                       double* __restrict__ out) {
+  constexpr int F = D + 1, NO = D == 3 ? 27 : 9, CENTER = D == 3 ? 13 : 4;
+  auto diag = [&](long long node, int f) {
+    const double d = S[((long long)(CENTER * F + f) * F + f) * g.N + node];
+    return d > 0.0 ? d : 1.0;
+  };
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = int(i % g.n[0]);
+    const long long rr = i / g.n[0];
+    const int iy = int(rr % g.n[1]);
+    const int iz = int(rr / g.n[1]);
+    double acc[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = 0.0;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const int jx = ix + o % 3 - 1, jy = iy + (o / 3) % 3 - 1, jz = D == 3 ? iz + o / 9 - 1 : 0;
+      if (jx < 0 || jx >= g.n[0] || jy < 0 || jy >= g.n[1] || jz < 0 || jz >= g.n[2]) continue;
+      const long long j = jx + g.n[0] * (jy + (long long)g.n[1] * jz);
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int h = 0; h < F; ++h)
+          acc[f] += fabs(S[((long long)(o * F + f) * F + h) * g.N + i]) / sqrt(diag(i, f) * diag(j, h));
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) out[f * g.N + i] = acc[f];
+  }
+}
+
+cudaError_t scaled_rowsum(const Geom& g, const double* S, double* out, cudaStream_t st) {
+  const int nb = int(std::min<long long>((g.N + 127) / 128, 16LL * 1216));
+  if (g.dim == 3) k_scaled_rowsum<3><<<nb, 128, 0, st>>>(g, S, out);
+  else k_scaled_rowsum<2><<<nb, 128, 0, st>>>(g, S, out);
+  return cudaGetLastError();
+}
+
 cudaError_t stencil_assemble(const Geom& g, const Mat<double>& m, const double* coef, double* S,
                              cudaStream_t st) {
   const long long total = (g.dim == 3 ? 27LL : 9LL) * g.N;

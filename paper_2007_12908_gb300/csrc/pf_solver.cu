@@ -914,6 +914,169 @@ struct Solver {
     return ex;
   }
 
+  // ---------------------------------------------------------------- the paper's QP solvers
+  // (Sec. 4.2.2) on the level's FP64 stencil: symmetric multicolour
+  // projected Gauss-Seidel and MPRGP.  g, lo, hi and s are level vectors.
+  void pgs_solve(int l, const double* g, const double* lo, const double* hi, double* s, int sweeps) {
+    const double* Sx = H->lv[l].stencil;
+    for (int k = 0; k < sweeps; ++k) {
+      ck(pgs_sweep(H->geo[l], Sx, g, lo, hi, s, false, st), "pgs");
+      ck(pgs_sweep(H->geo[l], Sx, g, lo, hi, s, true, st), "pgs");
+      S.launches += 2 << H->dim;
+    }
+  }
+
+  // MPRGP from s = 0 on the diagonally scaled problem y = D^(1/2) s; the
+  // expansion step 1 / (Gershgorin bound of D^(-1/2) H D^(-1/2)).  tol < 0:
+  // the forcing tolerance min(0.1, sqrt(|nu0|)) |nu0| of the initial
+  // projected gradient nu0.  Returns the products used.  Uses B.s (y),
+  // B.Hs (gradient), B.p, B.q (A p), B.r, B.t1 (scale), B.t2, B.w, B.Hw
+  // (scaled bounds).
+  int mprgp_solve(int l, const double* g, const double* lo, const double* hi, double* out,
+                  double tol, int maxit) {
+    LevelBuf& B = H->lv[l];
+    const long long n = B.n;
+    const Geom geo = H->geo[l];
+    const int Fd = F;
+    const double* Sx = B.stencil;
+    double *y = B.s, *gr = B.Hs, *p = B.p, *Ap = B.q, *d = B.r, *sq = B.t1, *tmp = B.t2;
+    double *lw = B.w, *up = B.Hw;
+    const long long N = geo.N;
+    const int center = H->dim == 3 ? 13 : 4;
+    map(n, [=] __device__(long long i) {
+      const int f = int(i / N);
+      const long long node = i - f * N;
+      const double dd = Sx[((long long)(center * Fd + f) * Fd + f) * N + node];
+      const double q = dd > 0.0 ? sqrt(dd) : 1.0;
+      sq[i] = q;
+      lw[i] = lo[i] * q;
+      up[i] = hi[i] * q;
+      y[i] = 0.0;
+      gr[i] = g[i] / q;  // A 0 - b, b = -D^(-1/2) g
+    });
+    ck(scaled_rowsum(geo, Sx, tmp, st), "rowsum");
+    S.launches += 1;
+    double lam;
+    reduce<1, OpMax>(n, [=] __device__(long long i, double(&v)[1]) { v[0] = tmp[i]; }, &lam);
+    const double abar = 1.0 / lam;
+    auto A = [&](const double* v, double* out_) {
+      map(n, [=] __device__(long long i) { tmp[i] = v[i] / sq[i]; });
+      ck(stencil_apply(geo, Sx, tmp, out_, st), "hessvec");
+      map(n, [=] __device__(long long i) { out_[i] /= sq[i]; });
+      S.launches += 1;
+      S.hessvecs += 1;
+      S.fe_hessvec += frac(l);
+    };
+    // free / chopped / reduced free gradient of element i
+    auto phi_of = [=] __device__(long long i) {
+      const double yi = y[i];
+      return (lw[i] < yi && yi < up[i]) ? gr[i] : 0.0;
+    };
+    auto beta_of = [=] __device__(long long i) {
+      const double yi = y[i], li = lw[i], ui = up[i], gi = gr[i];
+      if (li < yi && yi < ui) return 0.0;
+      if (!(li < ui)) return 0.0;
+      return yi <= li ? fmin(gi, 0.0) : fmax(gi, 0.0);
+    };
+    auto set_p_phi = [&]() { map(n, [=] __device__(long long i) { p[i] = phi_of(i); }); };
+    set_p_phi();
+    int used = 1;
+    double nrm0 = -1.0;
+    while (true) {
+      double r3[3];
+      reduce<3, OpSum>(n, [=] __device__(long long i, double(&v)[3]) {
+        const double ph = phi_of(i), be = beta_of(i);
+        const double yi = y[i];
+        double pt = 0.0;
+        if (lw[i] < yi && yi < up[i])
+          pt = ph > 0.0 ? fmin((yi - lw[i]) / abar, ph) : fmax((yi - up[i]) / abar, ph);
+        v[0] = (ph + be) * (ph + be);
+        v[1] = be * be;
+        v[2] = pt * ph;
+      }, r3);
+      const double nrm = std::sqrt(r3[0]);
+      if (nrm0 < 0.0) {
+        nrm0 = nrm;
+        if (tol < 0.0) tol = std::min(0.1, std::sqrt(nrm0)) * nrm0;
+      }
+      if (!(nrm > tol) || used >= maxit) break;
+      if (r3[1] <= r3[2]) {  // proportional (Gamma = 1)
+        A(p, Ap);
+        ++used;
+        double r2[2];
+        reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
+          v[0] = p[i] * Ap[i];
+          v[1] = gr[i] * p[i];
+        }, r2);
+        if (!(r2[0] > 0.0)) break;
+        const double acg = r2[1] / r2[0];
+        double af;
+        reduce<1, OpMin>(n, [=] __device__(long long i, double(&v)[1]) {
+          const double pi = p[i];
+          v[0] = pi > 0.0 ? (y[i] - lw[i]) / pi : (pi < 0.0 ? (y[i] - up[i]) / pi : INFINITY);
+        }, &af);
+        if (acg <= af) {
+          map(n, [=] __device__(long long i) {
+            y[i] -= acg * p[i];
+            gr[i] -= acg * Ap[i];
+          });
+          double ga;
+          reduce<1, OpSum>(n, [=] __device__(long long i, double(&v)[1]) { v[0] = phi_of(i) * Ap[i]; }, &ga);
+          const double gam = ga / r2[0];
+          map(n, [=] __device__(long long i) { p[i] = phi_of(i) - gam * p[i]; });
+        } else {
+          map(n, [=] __device__(long long i) {
+            y[i] -= af * p[i];
+            gr[i] -= af * Ap[i];
+          });
+          map(n, [=] __device__(long long i) { d[i] = phi_of(i); });
+          map(n, [=] __device__(long long i) { y[i] = fmin(fmax(y[i] - abar * d[i], lw[i]), up[i]); });
+          A(y, gr);
+          ++used;
+          const double* gg = g;
+          map(n, [=] __device__(long long i) { gr[i] += gg[i] / sq[i]; });
+          set_p_phi();
+        }
+      } else {  // proportioning along the chopped gradient
+        map(n, [=] __device__(long long i) { d[i] = beta_of(i); });
+        A(d, Ap);
+        ++used;
+        double r2[2];
+        reduce<2, OpSum>(n, [=] __device__(long long i, double(&v)[2]) {
+          v[0] = d[i] * Ap[i];
+          v[1] = gr[i] * d[i];
+        }, r2);
+        if (!(r2[0] > 0.0)) break;
+        const double a = r2[1] / r2[0];
+        map(n, [=] __device__(long long i) {
+          y[i] -= a * d[i];
+          gr[i] -= a * Ap[i];
+        });
+        set_p_phi();
+      }
+    }
+    map(n, [=] __device__(long long i) { out[i] = y[i] / sq[i]; });
+    return used;
+  }
+
+  // The TR subproblem with the paper's QP solvers: MPRGP on the coarsest
+  // level (cg_max products), pgs_sweeps symmetric PGS sweeps elsewhere.
+  void paper_subproblem(int l, int cg_max) {
+    LevelBuf& B = H->lv[l];
+    if (l == 0) {
+      // MPRGP leaves its result in B.s, the step
+      const int used = mprgp_solve(l, B.g, B.lo, B.hi, B.s, -1.0, cg_max);
+      S.cg += used;
+      S.cg_level[0] += used;
+      return;
+    }
+    zero(B.s, B.n);
+    pgs_solve(l, B.g, B.lo, B.hi, B.s, P.pgs_sweeps);
+    S.cg_level[std::min(l, 7)] += P.pgs_sweeps;
+    S.hessvecs += 2 * P.pgs_sweeps;
+    S.fe_hessvec += 2.0 * P.pgs_sweeps * frac(l);
+  }
+
   // Projected-search truncated CG for min g.s + 1/2 s.Hs over lo <= s <= hi
   // (eq. model_qp); the step is left in B.s (FP64).  On sub32 levels the
   // solve runs on FP32 copies of g and of the box, rounded towards zero so
@@ -922,6 +1085,10 @@ struct Solver {
   void subproblem(int l, double delta, int cg_max) {
     LevelBuf& B = H->lv[l];
     const long long n = B.n;
+    if (P.qp_solver == PF_QP_PAPER) {
+      paper_subproblem(l, cg_max);
+      return;
+    }
     if (!sub32(l)) {
       subproblem_t<double>(l, delta, cg_max,
                            {B.g, B.lo, B.hi, B.minv, B.s, B.Hs, B.r, B.p, B.q, B.w, B.Hw, B.t3,
@@ -1496,6 +1663,28 @@ pf_status projected_gradient_impl(pf_hierarchy* H, const double* x_dev, double* 
     return PF_ECUDA;
   }
   return std::isfinite(*out) ? PF_OK : PF_ENONFINITE;
+}
+
+pf_status qp_impl(pf_hierarchy* H, int level, const double* g, const double* lo, const double* hi,
+                  double* s, int sweeps, double tol, int maxit, int* products) {
+  pf_rmtr_stats S{};
+  pf_rmtr_params P;
+  pf_rmtr_params_default(&P);
+  try {
+    Solver solver(H, P, S);
+    if (sweeps > 0) {
+      solver.pgs_solve(level, g, lo, hi, s, sweeps);
+      ck(cudaStreamSynchronize(H->st), "sync");
+    } else {
+      const int used = solver.mprgp_solve(level, g, lo, hi, s, tol, maxit);
+      ck(cudaStreamSynchronize(H->st), "sync");
+      if (products) *products = used;
+    }
+  } catch (const CudaFail& f) {
+    set_error(std::string("CUDA error in ") + f.where + ": " + cudaGetErrorString(f.e));
+    return PF_ECUDA;
+  }
+  return PF_OK;
 }
 
 pf_status rmtr_load_step_impl(pf_hierarchy* H, double* x_dev, const pf_rmtr_params& P,

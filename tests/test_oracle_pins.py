@@ -8,6 +8,8 @@ import math
 import os
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg  # noqa: F401
 import pytest
 
 import pfinputs as PI
@@ -649,3 +651,112 @@ def test_pins_catch_a_planted_gate_sign_error(monkeypatch):
     monkeypatch.setattr(O, "trust_region_gate", wrong)
     with pytest.raises(AssertionError):
         test_trust_region_gate_ratio_from_the_quartic()
+
+
+# ---------------------------------------------------------------- the paper's QP solvers
+def _qp_case(dim=2, n=(6, 5), seed=51):
+    """A box QP from the functional's Hessian at a mild state (SPD there):
+    bounds as a TR subproblem at a fracture state would give them."""
+    g = O.Grid(dim, n, 0.25)
+    prm = O.Params(E=1.0, nu=0.3, Gc=1.0, ls=0.5, p=0.0)
+    x = PI.random_state(seed, dim, g.N, u_scale=1e-3, c_hi=0.3)
+    A = O.probe_sparse(g, lambda v: O.hessvec(g, prm, x, v))
+    r = PI.rng(seed + 1)
+    gv = r.standard_normal(x.size)
+    lo = -r.uniform(0.01, 0.2, x.size)
+    hi = r.uniform(0.01, 0.2, x.size)
+    # clamped displacement dofs on the boundary, as in every TR subproblem
+    fixed = np.zeros(x.size, dtype=bool)
+    bnd = g.boundary_nodes()
+    for f in range(dim):
+        fixed[f * g.N:(f + 1) * g.N] = bnd
+    lo[fixed] = 0.0
+    hi[fixed] = 0.0
+    return g, A, gv, lo, hi
+
+
+def _kkt_residual(A, g, lo, hi, s):
+    """|| s - P(s - (g + A s)) ||: zero exactly at the box QP's KKT point."""
+    gr = g + A @ s
+    return float(np.linalg.norm(s - np.minimum(np.maximum(s - gr, lo), hi)))
+
+
+def test_probe_sparse_is_the_dense_hessian():
+    g = O.Grid(3, (3, 4, 3), 0.3)
+    prm = _prm()
+    x = PI.random_state(52, 3, g.N, u_scale=0.3)
+    A = O.probe_sparse(g, lambda v: O.hessvec(g, prm, x, v)).toarray()
+    D = O.dense_hessian(g, prm, x)
+    assert np.max(np.abs(A - D)) <= 1e-14 * np.max(np.abs(D))
+
+
+def test_pgs_diagonal_qp_is_exact_in_one_sweep():
+    """For a diagonal H every dof is independent: one sweep gives the
+    closed-form minimiser clamp(-g_i / h_i, lo_i, hi_i)."""
+    g = O.Grid(2, (4, 3), 0.5)
+    r = PI.rng(53)
+    h = r.uniform(0.5, 2.0, 3 * g.N)
+    A = sp.diags(h).tocsr()
+    gv = r.standard_normal(3 * g.N)
+    lo, hi = -0.3 * np.ones(3 * g.N), 0.2 * np.ones(3 * g.N)
+    s = O.pgs_sweeps(A, g, gv, lo, hi, 1)
+    assert np.max(np.abs(s - np.clip(-gv / h, lo, hi))) <= 1e-15
+
+
+def test_pgs_decreases_the_model_and_reaches_kkt():
+    g, A, gv, lo, hi = _qp_case()
+    m = lambda s: float(gv @ s) + 0.5 * float(s @ (A @ s))
+    s, prev = np.zeros_like(gv), 0.0
+    for _ in range(200):
+        s = O.pgs_sweeps(A, g, gv, lo, hi, 1, s)
+        assert m(s) <= prev + 1e-15
+        prev = m(s)
+    assert np.all(s >= lo) and np.all(s <= hi)
+    assert _kkt_residual(A, gv, lo, hi, s) <= 1e-10 * np.linalg.norm(gv)
+
+
+def test_mprgp_reaches_the_kkt_point_of_pgs():
+    g, A, gv, lo, hi = _qp_case(3, (4, 4, 3), 54)
+    Hv = lambda v: A @ v
+    dd = A.diagonal()
+    lam = float(sp.linalg.eigsh(sp.diags(1 / np.sqrt(dd)) @ A @ sp.diags(1 / np.sqrt(dd)), k=1,
+                                return_eigenvectors=False)[0])
+    s = O.mprgp(Hv, gv, lo, hi, dd, 1e-12 * np.linalg.norm(gv), 5000, lam_max=1.01 * lam)
+    assert np.all(s >= lo - 1e-15) and np.all(s <= hi + 1e-15)
+    assert _kkt_residual(A, gv, lo, hi, s) <= 1e-10 * np.linalg.norm(gv)
+    sp_ = O.pgs_sweeps(A, g, gv, lo, hi, 3000)
+    assert np.max(np.abs(s - sp_)) <= 1e-8 * np.max(np.abs(s))
+
+
+def test_mprgp_1d_closed_form():
+    """A 1x1 box QP: the minimiser clamp(-g/h, lo, hi) in one proportioning
+    or CG step."""
+    for gv, h, lo, hi in ((2.0, 4.0, -1.0, 1.0), (-3.0, 0.5, -1.0, 2.0), (5.0, 1.0, -1.0, 1.0)):
+        s = O.mprgp(lambda v: h * v, np.array([gv]), np.array([lo]), np.array([hi]), np.array([h]),
+                    1e-14, 50, lam_max=1.0)
+        assert abs(s[0] - min(max(-gv / h, lo), hi)) <= 1e-14
+
+
+def test_pins_catch_an_unprojected_gauss_seidel(monkeypatch):
+    """Gauss-Seidel without the projection leaves the box: the KKT pin fails."""
+    real = O.pgs_sweeps
+
+    def unprojected(A, grid, g, lo, hi, sweeps, s=None):
+        return real(A, grid, g, np.full_like(lo, -np.inf), np.full_like(hi, np.inf), sweeps, s)
+
+    monkeypatch.setattr(O, "pgs_sweeps", unprojected)
+    with pytest.raises(AssertionError):
+        test_pgs_decreases_the_model_and_reaches_kkt()
+
+
+def test_pins_catch_a_gradient_sign_error_in_mprgp(monkeypatch):
+    """MPRGP handed the model's gradient with the wrong sign solves another
+    QP: the KKT pin fails."""
+    real = O.mprgp
+
+    def wrong(Hv, g, lo, hi, dscale, tol, maxit, gamma=1.0, lam_max=None):
+        return real(Hv, -g, lo, hi, dscale, tol, maxit, gamma=gamma, lam_max=lam_max)
+
+    monkeypatch.setattr(O, "mprgp", wrong)
+    with pytest.raises(AssertionError):
+        test_mprgp_reaches_the_kkt_point_of_pgs()
