@@ -760,3 +760,26 @@ def test_pins_catch_a_gradient_sign_error_in_mprgp(monkeypatch):
     monkeypatch.setattr(O, "mprgp", wrong)
     with pytest.raises(AssertionError):
         test_mprgp_reaches_the_kkt_point_of_pgs()
+
+
+def test_propagation_starts_at_the_griffith_pressure():
+    """The oracle's ramp (tests/golden/propagation.json, written by
+    tests/golden/make_propagation.py) grows the centred crack between
+    p = 2.0 and 2.5.  Griffith's critical pressure of a line crack of
+    half-length a in plane strain, p_c = sqrt(E' G / (pi a)), E' = E/(1 -
+    nu^2), with AT2's discrete effective toughness G = G_c (1 + h/(2 l_s))
+    = 1.25 G_c at l_s = 2h, is 2.09 for a = 0.1: inside that bracket.
+    Below it the crack's extent barely moves; above it, it at least
+    quadruples and the energy falls."""
+    gold = json.load(open(os.path.join(GOLD, "propagation.json")))
+    E, nu, Gc, a = gold["E"], gold["nu"], gold["Gc"], 0.1
+    pc = math.sqrt(E / (1 - nu * nu) * 1.25 * Gc / (math.pi * a))
+    assert 2.0 < pc < 2.5
+    steps = gold["steps"]
+    n0 = steps[0]["crack_nodes"]
+    below = [s for s in steps if s["p"] < pc]
+    above = [s for s in steps if s["p"] > pc]
+    assert all(s["crack_nodes"] < 1.5 * n0 for s in below)
+    assert all(s["crack_nodes"] > 4 * n0 for s in above)
+    es = [s["energy"] for s in steps]
+    assert all(b < a_ for a_, b in zip(es, es[1:]))
