@@ -112,6 +112,8 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the uneven 2D batch (64 instances, 129^2 .. 1025^2) instead of the 3D workload")
     ap.add_argument("--batch-threads", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched run: keep the default tile rule instead of the autotuner's choice")
     ap.add_argument("--paper-scale", action="store_true",
                     help="the paper's 3D scenario at its size (393^3, 242.8M dofs, 100 plates)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -861,6 +863,14 @@ def run_batched(args):
         Hs.append(H)
         xs.append(x)
     dofs = sum(H.ndof() for H in Hs)
+    # the tile autotuner on every instance (per level: the fastest FP32
+    # Hessian tile variant, measured), unless --no-autotune
+    tuned = {}
+    if not args.no_autotune:
+        for H, n in zip(Hs, sizes):
+            var, us = pf.autotune(H)
+            tuned.setdefault(str(n), []).append(var)
+        torch.cuda.synchronize()
 
     def step(t, threads):
         for H in Hs:
@@ -892,6 +902,7 @@ def run_batched(args):
                    "sizes": sizes, "fractures": counts, "precision": args.precision,
                    "start": args.start, "threads": args.batch_threads or len(Hs)},
         "instances_per_s": len(Hs) / sec,
+        "tile_variants": {k: v[0] for k, v in tuned.items()},
         "converged": [sum(o["converged"] for o in out) for out in outs],
         "cycles_mean": [statistics.mean(o["cycles"] for o in out) for out in outs],
         "clocks": clk,

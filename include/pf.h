@@ -407,6 +407,25 @@ pf_status pf_energy_noalloc(int dim, const int n[3], double h, double E, double 
                             double ls, double k_res, double p, const void* x_dev, int prec,
                             double* E_dev, void* stream);
 
+/* Tile autotuner (no counterpart in the paper): times the FP32 Hessian
+ * product of every level of h on each of its tile variants (3D: 1
+ * element-owned 8^3 element tiles, 2 owner-computes 8^3 node tiles, 3
+ * owner-computes 4^3; 2D: 0 32x8, 1 16x8, 2 64x4, 3 32x4 node tiles) with
+ * CUDA events on h's stream (one warm-up and five timed launches each on the
+ * level's own buffers), and keeps the fastest for the level's FP32
+ * products from then on, in the solver and in pf_hessvec.  The variants
+ * compute the same product with different summation orders (results agree
+ * to FP32 rounding; each is deterministic).  variant_out (n_levels ints)
+ * and us_out (4 n_levels doubles, microseconds per product, -1 where a
+ * variant does not apply) may be NULL.  Rebuilds the hierarchy's CUDA
+ * graphs on next use.  Call between load steps; synchronises the stream. */
+pf_status pf_autotune(pf_hierarchy* h, int* variant_out, double* us_out);
+/* The tile variant of one level (0 = the default rule), e.g. to reuse a
+ * choice of pf_autotune in later runs so that they repeat bit for bit.
+ * set also rebuilds the hierarchy's CUDA graphs on next use. */
+pf_status pf_tile_variant_set(pf_hierarchy* h, int level, int variant);
+pf_status pf_tile_variant_get(const pf_hierarchy* h, int level, int* variant);
+
 /* Measurement helper with no counterpart in the paper: runs a kernel of
  * independent fused multiply-adds in precision prec on the legacy stream
  * and writes the achieved rate (flop/s, an FMA counted as 2) to *flops_host.

@@ -37,7 +37,7 @@ EXPORTS = [
     "pf_learned_apply", "pf_learned_propose", "pf_projected_gradient", "pf_rmtr_load_step_batch",
     "pf_energy_diff_mixed", "pf_gradient_step", "pf_gradient_df", "pf_energy_df",
     "pf_state_save", "pf_state_load", "pf_galerkin_set", "pf_galerkin_apply", "pf_qp_pgs",
-    "pf_qp_mprgp",
+    "pf_qp_mprgp", "pf_autotune", "pf_tile_variant_set", "pf_tile_variant_get",
 ]
 
 
@@ -120,6 +120,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_state_load": (i, [vp, vp, C.c_char_p]),
         "pf_galerkin_set": (i, [vp, vp]),
         "pf_qp_pgs": (i, [vp, i, vp, vp, vp, vp, i]),
+        "pf_autotune": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "pf_tile_variant_set": (i, [vp, i, i]),
+        "pf_tile_variant_get": (i, [vp, i, C.POINTER(C.c_int)]),
         "pf_qp_mprgp": (i, [vp, i, vp, vp, vp, vp, d, i, C.POINTER(C.c_int)]),
         "pf_galerkin_apply": (i, [vp, i, vp, vp, i]),
         "pf_probe_fma": (i, [i, C.POINTER(d)]),
@@ -457,6 +460,26 @@ def state_load(H: Hierarchy, x, path):
     import torch
     _check(lib().pf_state_load(H.handle, _dev(x, H.ndof(), torch.float64), os.fsencode(path)))
     return x
+
+
+def autotune(H: Hierarchy):
+    """Times every tile variant of each level's FP32 Hessian product and
+    keeps the fastest; returns (variants per level, microseconds per
+    (level, variant), -1 where a variant does not apply)."""
+    var = (C.c_int * H.n_levels)()
+    us = (C.c_double * (4 * H.n_levels))()
+    _check(lib().pf_autotune(H.handle, var, us))
+    return list(var), [list(us[4 * l:4 * l + 4]) for l in range(H.n_levels)]
+
+
+def tile_variant_set(H: Hierarchy, level: int, variant: int):
+    _check(lib().pf_tile_variant_set(H.handle, level, variant))
+
+
+def tile_variant_get(H: Hierarchy, level: int) -> int:
+    out = C.c_int()
+    _check(lib().pf_tile_variant_get(H.handle, level, C.byref(out)))
+    return out.value
 
 
 def qp_pgs(H: Hierarchy, level: int, g, lo, hi, s, sweeps):

@@ -484,6 +484,76 @@ pf_status pf_hessvec_lag_set(pf_hierarchy* h, int level, const void* x, int prec
   return PF_OK;
 }
 
+pf_status pf_tile_variant_set(pf_hierarchy* h, int level, int variant) {
+  if (!valid_level(h, level) || variant < 0 || variant > 3)
+    return bad("tile_variant_set: bad level or variant (0 .. 3)");
+  h->geo[level].hv_variant = variant;
+  for (auto& G : h->cg_graphs) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = pf_hierarchy::CgGraph{};
+  }
+  return PF_OK;
+}
+
+pf_status pf_tile_variant_get(const pf_hierarchy* h, int level, int* variant) {
+  if (!valid_level(h, level) || !variant) return bad("tile_variant_get: bad argument");
+  *variant = h->geo[level].hv_variant;
+  return PF_OK;
+}
+
+pf_status pf_autotune(pf_hierarchy* h, int* variant_out, double* us_out) {
+  if (!h) return bad("autotune: null handle");
+  cudaEvent_t e0, e1;
+  PF_TRY_CUDA(cudaEventCreate(&e0), "autotune");
+  PF_TRY_CUDA(cudaEventCreate(&e1), "autotune");
+  pf_status rc = PF_OK;
+  for (int l = 0; l < h->L && rc == PF_OK; ++l) {
+    LevelBuf& B = h->lv[l];
+    Geom& g = h->geo[l];
+    float* v = reinterpret_cast<float*>(B.p);
+    float* y = reinterpret_cast<float*>(B.q);
+    cudaError_t e = cudaMemsetAsync(v, 0, sizeof(float) * B.n, h->st);
+    const int first = h->dim == 3 ? 1 : 0;
+    int best = 0;
+    double best_us = 1e300;
+    for (int var = 0; var < 4 && e == cudaSuccess; ++var) {
+      if (us_out) us_out[4 * l + var] = -1.0;
+      if (var < first) continue;
+      g.hv_variant = var;
+      e = elem_hessvec(g, h->mat[l], B.xlag32, v, y, 1, h->st, nullptr, h->etile_part, h->p_dev);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->st);
+      for (int r = 0; r < 5 && e == cudaSuccess; ++r)
+        e = elem_hessvec(g, h->mat[l], B.xlag32, v, y, 1, h->st, nullptr, h->etile_part, h->p_dev);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      const double us = 1e3 * double(ms) / 5.0;
+      if (us_out) us_out[4 * l + var] = us;
+      if (us < best_us) {
+        best_us = us;
+        best = var;
+      }
+    }
+    g.hv_variant = best;
+    if (variant_out) variant_out[l] = best;
+    if (e != cudaSuccess) {
+      set_error(std::string("autotune: ") + cudaGetErrorString(e));
+      rc = PF_ECUDA;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // CG graphs captured the old tiles: rebuild on next use
+  for (auto& G : h->cg_graphs) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = pf_hierarchy::CgGraph{};
+  }
+  return rc;
+}
+
 pf_status pf_qp_pgs(pf_hierarchy* h, int level, const double* g, const double* lo, const double* hi,
                     double* s, int sweeps) {
   if (!valid_level(h, level) || !g || !lo || !hi || !s || sweeps < 1) return bad("qp_pgs: bad argument");

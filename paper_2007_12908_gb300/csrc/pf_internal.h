@@ -14,6 +14,11 @@ struct Geom {
   int ne[3];     // elements per axis
   long long NE;  // elements
   double h;
+  // tile variant of the FP32 Hessian products on this grid (0: the default
+  // rule; set per level by the autotuner, pf_autotune): 3D 1 element-owned
+  // 8^3 tiles, 2 owner-computes 8^3, 3 owner-computes 4^3; 2D 1 16x8,
+  // 2 64x4, 3 32x4 node tiles (0: 32x8)
+  int hv_variant;
 };
 
 // Fixed-size deterministic reduction scratch: one partial per block (up to

@@ -31,6 +31,7 @@ Geom make_geom(int dim, const int n[3], double h) {
     g.NE *= g.ne[k];
   }
   g.h = h;
+  g.hv_variant = 0;
   return g;
 }
 
@@ -194,6 +195,16 @@ template <>
 struct Tile<2> {
   static constexpr int X = 32, Y = 8, Z = 1, THREADS = 128;
 };
+// the other 2D node tiles the autotuner chooses from
+struct Tile2_16x8 {
+  static constexpr int X = 16, Y = 8, Z = 1, THREADS = 128;
+};
+struct Tile2_64x4 {
+  static constexpr int X = 64, Y = 4, Z = 1, THREADS = 128;
+};
+struct Tile2_32x4 {
+  static constexpr int X = 32, Y = 4, Z = 1, THREADS = 128;
+};
 
 // OP_GDIFF: y += grad E(x) - grad E(x - v), the gradient step from x - v to
 // x in the arithmetic of TC (elem_gradient_diff at x with step -v).
@@ -227,15 +238,15 @@ __global__ void __launch_bounds__(256) k_hess_coef(Geom g, Mat<T> m, const T* __
 // device-side CG stops this way without a host round trip).
 // FP32 instances are limited to 128 registers so that two CTAs (16 warps)
 // share an SM and hide the gather and barrier latency.
-template <int D, class TC, class TIO, int OP, class TM = TC>
-__global__ void __launch_bounds__(Tile<D>::THREADS, sizeof(TC) == 4 ? 2 : 1)
+template <int D, class TC, class TIO, int OP, class TM = TC, class TS = Tile<D>>
+__global__ void __launch_bounds__(TS::THREADS, sizeof(TC) == 4 ? 2 : 1)
     k_elem_scatter(Geom g, Mat<TC> m, const TM* __restrict__ x, const TIO* __restrict__ v,
                    TIO* __restrict__ y, const int* __restrict__ skip) {
   if (skip && *skip) return;
   constexpr int F = D + 1, NC = 1 << D;
-  constexpr int TX = Tile<D>::X, TY = Tile<D>::Y, TZ = Tile<D>::Z;
+  constexpr int TX = TS::X, TY = TS::Y, TZ = TS::Z;
   constexpr int EX = TX + 1, EY = TY + 1, EZ = D == 3 ? TZ + 1 : 1;
-  constexpr int NEL = EX * EY * EZ, NOWN = TX * TY * TZ, NT = Tile<D>::THREADS;
+  constexpr int NEL = EX * EY * EZ, NOWN = TX * TY * TZ, NT = TS::THREADS;
   __shared__ TC acc[F][NOWN];
   const int ox = blockIdx.x * TX, oy = blockIdx.y * TY, oz = D == 3 ? blockIdx.z * TZ : 0;
   for (int i = threadIdx.x; i < F * NOWN; i += NT) (&acc[0][0])[i] = TC(0);
@@ -413,19 +424,30 @@ __global__ void __launch_bounds__(HessTile<T>::THREADS, T == 8 ? 2 : 4)
   }
 }
 
-template <int D>
+template <int D, class TS = Tile<D>>
 static dim3 scatter_grid(const Geom& g) {
-  return dim3((g.n[0] + Tile<D>::X - 1) / Tile<D>::X, (g.n[1] + Tile<D>::Y - 1) / Tile<D>::Y,
-              D == 3 ? (g.n[2] + Tile<D>::Z - 1) / Tile<D>::Z : 1);
+  return dim3((g.n[0] + TS::X - 1) / TS::X, (g.n[1] + TS::Y - 1) / TS::Y,
+              D == 3 ? (g.n[2] + TS::Z - 1) / TS::Z : 1);
 }
 
-template <int D, class TC, class TIO, int OP, class TM = TC>
+template <int D, class TC, class TIO, int OP, class TM = TC, class TS = Tile<D>>
 static cudaError_t launch_scatter(const Geom& g, const Mat<double>& m, const void* x,
                                   const void* v, void* y, const int* skip, cudaStream_t st) {
-  k_elem_scatter<D, TC, TIO, OP, TM><<<scatter_grid<D>(g), Tile<D>::THREADS, 0, st>>>(
+  k_elem_scatter<D, TC, TIO, OP, TM, TS><<<scatter_grid<D, TS>(g), TS::THREADS, 0, st>>>(
       g, cast_mat<TC>(m), static_cast<const TM*>(x), static_cast<const TIO*>(v),
       static_cast<TIO*>(y), skip);
   return cudaGetLastError();
+}
+
+// The 2D FP32 Hessian product on the node tile of the grid's variant.
+static cudaError_t launch_hess2_f32(const Geom& g, const Mat<double>& m, const void* x,
+                                   const void* v, void* y, const int* skip, cudaStream_t st) {
+  switch (g.hv_variant) {
+    case 1: return launch_scatter<2, float, float, OP_HESS, float, Tile2_16x8>(g, m, x, v, y, skip, st);
+    case 2: return launch_scatter<2, float, float, OP_HESS, float, Tile2_64x4>(g, m, x, v, y, skip, st);
+    case 3: return launch_scatter<2, float, float, OP_HESS, float, Tile2_32x4>(g, m, x, v, y, skip, st);
+    default: return launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st);
+  }
 }
 
 cudaError_t elem_gradient_step(const Geom& g, const Mat<double>& m, const double* x,
@@ -653,13 +675,18 @@ static bool etile_eligible(const Geom& g) {
   return g.dim == 3 && b8 >= 2 * 152;
 }
 
-int hessvec32_launches(const Geom& g, const void* part) {
-  return part && etile_eligible(g) ? 2 : 1;
+// Whether the 3D FP32 product runs on element-owned tiles: by the grid's
+// variant (1 yes, 2 and 3 no), else by the default rule (at least two 8^3
+// tiles per SM).
+static bool etile_used(const Geom& g, const void* part) {
+  if (g.dim != 3 || !part) return false;
+  if (g.hv_variant) return g.hv_variant == 1;
+  return etile_eligible(g);
 }
 
-bool hessvec32_dot_fused(const Geom& g, const void* part) {
-  return part && etile_eligible(g) && g.dim == 3;
-}
+int hessvec32_launches(const Geom& g, const void* part) { return etile_used(g, part) ? 2 : 1; }
+
+bool hessvec32_dot_fused(const Geom& g, const void* part) { return etile_used(g, part); }
 
 cudaError_t elem_hessvec32_dot(const Geom& g, const Mat<double>& m, const float* x, float* p,
                                float* q, CgCtrl* c, double* partials, unsigned* counter,
@@ -682,7 +709,7 @@ static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const 
   auto tiles = [&g](int t) {
     return dim3((g.n[0] + t - 1) / t, (g.n[1] + t - 1) / t, (g.n[2] + t - 1) / t);
   };
-  if (part && etile_eligible(g)) {
+  if (etile_used(g, part)) {
     const dim3 be((g.ne[0] + 7) / 8, (g.ne[1] + 7) / 8, (g.ne[2] + 7) / 8);
     float4* pp = static_cast<float4*>(part);
     k_hess_etile3<TV><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, v, pp, skip, p_dev,
@@ -692,7 +719,8 @@ static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const 
     return cudaGetLastError();
   }
   const dim3 b8 = tiles(8);
-  if ((long long)b8.x * b8.y * b8.z >= 2 * 152)
+  const bool t8 = g.hv_variant ? g.hv_variant != 3 : (long long)b8.x * b8.y * b8.z >= 2 * 152;
+  if (t8)
     k_hess_tile3<TV, 8><<<b8, HessTile<8>::THREADS, 0, st>>>(g, cast_mat<float>(m), x, v, y, skip,
                                                               p_dev);
   else
@@ -709,7 +737,7 @@ cudaError_t elem_hessvec(const Geom& g, const Mat<double>& m, const void* x, con
                                            static_cast<const float*>(v), static_cast<float*>(y),
                                            skip, st, part, p_dev)
                 : launch_scatter<3, double, double, OP_HESS>(g, m, x, v, y, skip, st);
-  return prec ? launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st)
+  return prec ? launch_hess2_f32(g, m, x, v, y, skip, st)
               : launch_scatter<2, double, double, OP_HESS>(g, m, x, v, y, skip, st);
 }
 
