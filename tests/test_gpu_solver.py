@@ -252,3 +252,33 @@ def test_stopping_reference(pf):
             assert st["converged"]
             if st["pg_ref"] != st["pg0"]:  # extrapolated steps
                 assert abs(st["pg_ref"] - direct) <= 1e-10 * direct
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_3d_65_load_step_fields_match_oracle(pf, precision):
+    """One load step of the disc network on a 65^3 three-level hierarchy:
+    its finest level takes the element-owned FP32 products (mixed) and the
+    full-grid FP64 stencil product (k_stencil_apply, FP64).  The converged
+    fields at 1,500 sampled determined nodes match the oracle's
+    (tests/golden/field_samples_65.json, written by the committed oracle
+    script) to 1e-8 of each field's max-norm, and the energy to 1e-10 (FP64)
+    or 1e-8 (mixed)."""
+    import torch
+    gold = json.load(open(os.path.join(GOLD, "field_samples_65.json")))
+    H, Ho = pair(3, (17, 17, 17), 3, 1 / 16, nu=0.25, p=gold["p"])
+    g = Ho.fine
+    assert list(g.n) == gold["grid"]
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    pf.fractures_set(H, pf.PF_DISC3D, PI.disc_network_3d(gold["seed"], gold["fractures"]), g.h, x)
+    prec = pf.PF_FP64 if precision == "fp64" else pf.PF_FP32
+    st = pf.rmtr_load_step(H, x, pf.default_params(precision=prec, rtol=1e-12))
+    assert st["converged"] == 1
+    tol_e = ENERGY_TOL if precision == "fp64" else 1e-8
+    assert abs(st["energy"] - gold["energy"]) <= tol_e * abs(gold["energy"])
+    xg = host(x)
+    nodes = np.asarray(gold["nodes"])
+    for f in range(4):
+        got = xg[f * g.N + nodes]
+        want = np.asarray(gold["fields"][f])
+        assert np.max(np.abs(got - want)) <= FIELD_TOL * gold["field_max"][f], (f, np.max(np.abs(got - want)))
+    H.close()
