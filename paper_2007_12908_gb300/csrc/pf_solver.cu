@@ -533,10 +533,22 @@ struct Solver {
       // free outside the subproblem)
       const bool m32 = mixed32(l);
       double* d = sub32(l) ? B.Hw : B.minv;
-      ck(elem_hessdiag(H->geo[l], H->mat[l], m32 ? (const void*)B.xlag32 : (const void*)B.xlag,
-                       m32 ? 1 : 0, d, st),
-         "hessdiag");
-      S.launches += 1;
+      if (gstored(l)) {
+        // the stored Galerkin operator's own diagonal (its centre blocks)
+        const float* gsv = B.gs;
+        const long long N = H->geo[l].N;
+        const int Fd = F, c = H->dim == 3 ? 13 : 4;
+        map(B.n, [=] __device__(long long i) {
+          const int f = int(i / N);
+          const long long k = i - f * N;
+          d[i] = double(gsv[((long long)(c * Fd + f) * Fd + f) * N + k]);
+        });
+      } else {
+        ck(elem_hessdiag(H->geo[l], H->mat[l], m32 ? (const void*)B.xlag32 : (const void*)B.xlag,
+                         m32 ? 1 : 0, d, st),
+           "hessdiag");
+        S.launches += 1;
+      }
       if (sub32(l)) {
         float* mi = reinterpret_cast<float*>(B.minv);
         map(B.n, [=] __device__(long long i) {
