@@ -114,6 +114,13 @@ def parse():
     ap.add_argument("--batch-threads", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched run: keep the default tile rule instead of the autotuner's choice")
+    ap.add_argument("--learned", action="store_true",
+                    help="the learned-iterate workload (2D 1025^2, 1000 fractures, trained U-Net)")
+    ap.add_argument("--traj", type=int, default=200, help="--learned: training trajectories")
+    ap.add_argument("--traj-steps", type=int, default=20, help="--learned: pressure steps per trajectory")
+    ap.add_argument("--heldout", type=int, default=20, help="--learned: held-out trajectories")
+    ap.add_argument("--fractures", type=int, default=1000, help="--learned: line fractures per network")
+    ap.add_argument("--train-steps", type=int, default=2000, help="--learned: Adam steps (batch 4)")
     ap.add_argument("--paper-scale", action="store_true",
                     help="the paper's 3D scenario at its size (393^3, 242.8M dofs, 100 plates)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -208,6 +215,13 @@ def cpu_cores():
 
 
 def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             low = line.lower()
@@ -840,6 +854,89 @@ def run_paper_scale(args):
     return 0
 
 
+def run_learned(args):
+    """The learned-initial-iterate workload: 2D 1025^2 grid (seven levels from
+    17^2), 1,000 line fractures per trajectory, the ramp p_t = 5e-4 t,
+    t = 1..20.  Trains the U-Net on args.traj solver trajectories (each its own
+    seeded network) with the library's forward/backward/Adam kernels, then
+    runs args.heldout held-out trajectories from the plain, the extrapolated
+    and the learned start, reporting V-cycles and seconds per load step."""
+    import torch
+    from paper_2007_12908_gb300 import build
+    build.build()
+    import paper_2007_12908_gb300 as pf
+    from paper_2007_12908_gb300 import learned as Lm
+    steps = args.traj_steps
+    pressures = [5e-4 * t for t in range(1, steps + 1)]
+    H = pf.mesh_hierarchy_create(2, (17, 17), 7, 1 / 16, E=1.0, nu=0.3, Gc=1.0)
+    (nx, ny), h, N = H.levels[-1]
+    # the solver settings of this workload: the crack networks converge
+    # slowly with first-order coarse models (50-80+ V-cycles per step), so the
+    # stored Galerkin operators with 50 CG iterations per coarse smoothing
+    # step and 200 on the finest level
+    solver = dict(precision=pf.PF_FP32, coarse_model=pf.PF_GALERKIN, cg_smooth=50, cg_fine=200)
+    prm = pf.default_params(start=pf.PF_START_EXTRAPOLATE, **solver)
+
+    def network(seed):
+        x0 = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+        pf.fractures_set(H, pf.PF_LINE2D, PI.line_network_2d(seed, args.fractures), h, x0)
+        return x0
+
+    learner = Lm.LearnedIterate(H, seed=1)
+    data = []
+    t0 = time.perf_counter()
+    for k in range(args.traj):
+        states = Lm.trajectory(H, network(PI.SEED_2D_LEARNED + k), pressures, prm)
+        data += Lm.samples(learner, states, pressures)
+        del states
+        print(f"trajectory {k + 1}/{args.traj}: {len(data)} samples, {time.perf_counter() - t0:.0f} s",
+              file=sys.stderr, flush=True)
+    t_data = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    losses = Lm.train(learner, data, steps=args.train_steps, lr=1e-3, batch=4)
+    t_train = time.perf_counter() - t1
+    del data
+    torch.cuda.empty_cache()
+    res = {m: [] for m in ("plain", "extrapolated", "learned")}
+    plain_prm = pf.default_params(**solver)
+    for k in range(args.heldout):
+        x0 = network(PI.SEED_2D_LEARNED + 100000 + k)
+        for mode in res:
+            recs, _ = Lm.run_ramp(H, x0, pressures, plain_prm, mode=mode, learner=learner)
+            res[mode].append(recs)
+        print(f"held-out {k + 1}/{args.heldout}", file=sys.stderr, flush=True)
+    summary = {}
+    for mode, runs in res.items():
+        later = [r for recs in runs for r in recs[1:]]
+        summary[mode] = {"v_cycles_per_step": statistics.mean(r["cycles"] for r in later),
+                         "s_per_load_step": statistics.mean(r["seconds"] for r in later),
+                         "converged": all(r["converged"] for recs in runs for r in recs)}
+    acc = [r.get("accepted", False) for recs in res["learned"] for r in recs[1:]]
+    acc_e = [r.get("accepted_extrapolated", False) for recs in res["learned"] for r in recs[1:]]
+    line = {
+        "metric": "learned initial iterate: V-cycles and s/load-step (t >= 2) on held-out trajectories",
+        "value": summary["learned"]["s_per_load_step"], "unit": UNIT, "higher_is_better": False,
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": "2d_1025^2_q1_7level_1000lines_ramp20", "grid": [nx, ny], "levels": 7,
+                   "dofs": H.ndof(), "fractures": args.fractures, "pressure_steps": pressures,
+                   "training_trajectories": args.traj, "heldout_trajectories": args.heldout,
+                   "samples": args.traj * (steps - 1), "adam_steps": args.train_steps, "batch": 4,
+                   "precision": "mixed", "coarse_model": "galerkin", "cg_smooth": 50, "cg_fine": 200,
+                   "network": "U-Net 16-32-64-128, BF16, tensor-core convolutions"},
+        "starts": summary,
+        "gain_v_cycles": {"over_plain": summary["plain"]["v_cycles_per_step"] - summary["learned"]["v_cycles_per_step"],
+                          "over_extrapolated": summary["extrapolated"]["v_cycles_per_step"]
+                          - summary["learned"]["v_cycles_per_step"]},
+        "gate_accepted": {"network": statistics.mean(1.0 if a else 0.0 for a in acc),
+                          "extrapolation": statistics.mean(1.0 if a else 0.0 for a in acc_e)},
+        "loss": {"first": float(np.mean(losses[:10])), "last": float(np.mean(losses[-10:]))},
+        "seconds": {"trajectories": t_data, "training": t_train},
+    }
+    print(json.dumps(line))
+    H.close()
+    return 0
+
+
 def run_batched(args):
     """Load steps of 64 uneven 2D instances (16 each of 129^2, 257^2, 513^2,
     1025^2 nodes; 10-1000 line fractures, +-30 deg families) run
@@ -921,6 +1018,8 @@ def main():
         return run_batched(args)
     if args.paper_scale:
         return run_paper_scale(args)
+    if args.learned:
+        return run_learned(args)
     return run_ours(args)
 
 
