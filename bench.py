@@ -121,6 +121,9 @@ def parse():
     ap.add_argument("--heldout", type=int, default=20, help="--learned: held-out trajectories")
     ap.add_argument("--fractures", type=int, default=1000, help="--learned: line fractures per network")
     ap.add_argument("--train-steps", type=int, default=2000, help="--learned: Adam steps (batch 4)")
+    ap.add_argument("--unet-kernels", action="store_true",
+                    help="time the U-Net's tensor-core convolutions on a --unet-size grid")
+    ap.add_argument("--unet-size", type=int, default=1032)
     ap.add_argument("--paper-scale", action="store_true",
                     help="the paper's 3D scenario at its size (393^3, 242.8M dofs, 100 plates)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -937,6 +940,60 @@ def run_learned(args):
     return 0
 
 
+def run_unet_kernels(args):
+    """The learned iterate's U-Net on an S x S grid (the 1025^2 workload pads
+    to 1032): forward and backward times of the tensor-core convolution
+    kernels and their rate against the measured BF16 peak."""
+    import torch
+    from paper_2007_12908_gb300 import build
+    build.build()
+    from paper_2007_12908_gb300 import _binding as B
+    from paper_2007_12908_gb300 import learned as Lm
+    S = args.unet_size
+    net = B.Unet(S, S)
+    net.set_params(Lm.he_init(3))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    x = torch.randn(5, S, S, device="cuda", generator=g)
+    t = torch.randn(3, S, S, device="cuda", generator=g)
+    flops = 0
+    shapes = Lm.layer_shapes()
+    lev = [0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0, 0]
+    for (co, ci, k), l in zip(shapes, lev):
+        flops += 2 * (S >> l) * (S >> l) * co * ci * k * k
+    for _ in range(3):
+        y = net.forward(x)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        y = net.forward(x)
+    b.record()
+    torch.cuda.synchronize()
+    t_f = a.elapsed_time(b) / args.steps * 1e-3
+    _, dy = net.mse(y, t)
+    net.backward(dy)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.steps):
+        net.backward(dy)
+    b.record()
+    torch.cuda.synchronize()
+    t_b = a.elapsed_time(b) / args.steps * 1e-3
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops_sustained"]
+        src = "measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    except (OSError, KeyError, ValueError):
+        peak, src = 1700.0, "fallback"
+    print(json.dumps({"unet": {"grid": S, "flop_forward": flops, "forward_ms": t_f * 1e3,
+                               "forward_tflops": flops / t_f / 1e12, "backward_ms": t_b * 1e3,
+                               "backward_tflops": 2 * flops / t_b / 1e12,
+                               "forward_frac": flops / t_f / 1e12 / peak, "peak_tflops": peak,
+                               "peak_source": src}}))
+    return 0
+
+
 def run_batched(args):
     """Load steps of 64 uneven 2D instances (16 each of 129^2, 257^2, 513^2,
     1025^2 nodes; 10-1000 line fractures, +-30 deg families) run
@@ -1020,6 +1077,8 @@ def main():
         return run_paper_scale(args)
     if args.learned:
         return run_learned(args)
+    if args.unet_kernels:
+        return run_unet_kernels(args)
     return run_ours(args)
 
 
