@@ -222,7 +222,9 @@ __global__ void __launch_bounds__(256) k_conv_mma(MmaIn src, int H, int W, int M
 }
 
 // Weight gradient partials on the tensor cores.  grid: (ceil(CI/NB),
-// ceil(CO/MB), P); chunk p covers pixel rows [p rows_per, (p+1) rows_per).
+// ceil(CO/MB), P); the 16 x 16 pixel tiles of the layer (tx per row, T in
+// all, row-major) are cut into P contiguous chunks, chunk p taking tiles
+// [p T / P, (p+1) T / P) in order.
 // The CTA stages, per 16 x 16 pixel tile, dpre for its MB output channels
 // (A rows; K = the 16 pixels of a tile row) and the fused input for its NB
 // input channels (three copies shifted by kx, so that every pixel pair a
@@ -243,7 +245,7 @@ template <int K, int MB, int NB>
 __global__ void __launch_bounds__(256) k_conv_wgrad_mma(const float* __restrict__ dout,
                                                         const __nv_bfloat16* __restrict__ out,
                                                         int relu, ConvIn in, int H, int W, int CO,
-                                                        int rows_per, float* __restrict__ part,
+                                                        int P, float* __restrict__ part,
                                                         float* __restrict__ part_b) {
   using S = WgradSmem<K, MB, NB>;
   constexpr int R = S::R, YT = S::YT, SD = S::SD, SX = S::SX, KK = K * K;
@@ -256,7 +258,9 @@ __global__ void __launch_bounds__(256) k_conv_wgrad_mma(const float* __restrict_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t4 = lane & 3;
   const int n0 = blockIdx.x * NB, m0 = blockIdx.y * MB, p = blockIdx.z;
-  const int y_lo = p * rows_per, y_hi = min(H, y_lo + rows_per);
+  const int tx = (W + 15) / 16;
+  const long long T = (long long)tx * ((H + 15) / 16);
+  const long long t_lo = p * T / P, t_hi = (p + 1) * T / P;
   float acc[PER][4];
 #pragma unroll
   for (int i = 0; i < PER; ++i)
@@ -266,13 +270,14 @@ __global__ void __launch_bounds__(256) k_conv_wgrad_mma(const float* __restrict_
 #pragma unroll
   for (int j = 0; j < BPW; ++j) accb[j] = 0.f;
   auto dpre = [&](int c, int yy, int xx) -> float {
-    if (m0 + c >= CO || yy >= y_hi || xx >= W) return 0.f;
+    if (m0 + c >= CO || yy >= H || xx >= W) return 0.f;
     const long long o = ((long long)(m0 + c) * H + yy) * W + xx;
     const float d = dout[o];
     return (relu && !(__bfloat162float(out[o]) > 0.f)) ? 0.f : d;
   };
-  for (int yb = y_lo; yb < y_hi; yb += 16)
-    for (int xb = 0; xb < W; xb += 16) {
+  for (long long ti = t_lo; ti < t_hi; ++ti) {
+    const int yb = int(ti / tx) * 16, xb = int(ti % tx) * 16;
+    {
       for (int i = threadIdx.x; i < MB * 16 * 8; i += 256) {
         const int wd = i & 7, r = (i >> 3) & 15, c = i >> 7;
         const float v0 = dpre(c, yb + r, xb + 2 * wd), v1 = dpre(c, yb + r, xb + 2 * wd + 1);
@@ -326,6 +331,7 @@ __global__ void __launch_bounds__(256) k_conv_wgrad_mma(const float* __restrict_
       }
       __syncthreads();
     }
+  }
   // c0 (m = g, n = 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
@@ -363,12 +369,21 @@ void launch_conv_mma(const MmaIn& src, int H, int W, int M, int Kc, int CIw,
     k_conv_mma<K, 64, DGRAD><<<grid, 256, 0, st>>>(src, H, W, M, Kc, CIw, w, bias, relu, ob, of);
 }
 
-constexpr int WG_MB = 32, WG_NB = 16, WG_ROWS = 32;
+constexpr int WG_MB = 32, WG_NB = 16;
+
+// Pixel-tile chunks of a weight-gradient launch: enough for two CTAs per SM
+// over the (input block, output block) grid, at most one chunk per tile.
+int wgrad_chunks(int H, int W, int CI, int CO, int sms) {
+  const long long T = (long long)((W + 15) / 16) * ((H + 15) / 16);
+  const long long base = (long long)((CI + WG_NB - 1) / WG_NB) * ((CO + WG_MB - 1) / WG_MB);
+  const long long want = (2LL * sms + base - 1) / base;
+  return int(std::max<long long>(1, std::min(T, want)));
+}
 
 template <int K>
 cudaError_t launch_wgrad_mma(const float* dout, const __nv_bfloat16* out, int relu, const ConvIn& in,
-                             int H, int W, int CO, float* part, float* part_b, cudaStream_t st) {
-  const int CI = in.ca + in.cb, P = (H + WG_ROWS - 1) / WG_ROWS;
+                             int H, int W, int CO, int P, float* part, float* part_b, cudaStream_t st) {
+  const int CI = in.ca + in.cb;
   const dim3 grid((CI + WG_NB - 1) / WG_NB, (CO + WG_MB - 1) / WG_MB, P);
   const size_t bytes = WgradSmem<K, WG_MB, WG_NB>::bytes;
   static_assert(WgradSmem<3, WG_MB, WG_NB>::bytes <= 100 * 1024, "wgrad shared memory above 100 KB");
@@ -381,7 +396,7 @@ cudaError_t launch_wgrad_mma(const float* dout, const __nv_bfloat16* out, int re
     if (e != cudaSuccess) return e;
     dev_done = dev;
   }
-  k_conv_wgrad_mma<K, WG_MB, WG_NB><<<grid, 256, bytes, st>>>(dout, out, relu, in, H, W, CO, WG_ROWS,
+  k_conv_wgrad_mma<K, WG_MB, WG_NB><<<grid, 256, bytes, st>>>(dout, out, relu, in, H, W, CO, P,
                                                              part, part_b);
   return cudaGetLastError();
 }
@@ -497,6 +512,7 @@ struct ConvLayer {
 
 struct pf_unet {
   int H = 0, W = 0, nin = 0, nout = 0, L = 4;
+  int sms = 1;  // SMs of the device (the weight-gradient chunking)
   int ch[4] = {16, 32, 64, 128};
   cudaStream_t st = nullptr;
   std::vector<ConvLayer> layers;  // enc0a, enc0b, ..., enc3b, dec2a, dec2b, dec1a, ..., head
@@ -594,6 +610,12 @@ pf_status pf_unet_create(int height, int width, int n_in, int n_out, const int c
     }
   pf_unet* u = new pf_unet();
   u->H = height; u->W = width; u->nin = n_in; u->nout = n_out;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&u->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      u->sms = 1;
+  }
   for (int k = 0; k < 4; ++k) u->ch[k] = channels[k];
   u->st = static_cast<cudaStream_t>(stream);
   long long off = 0;
@@ -642,8 +664,7 @@ pf_status pf_unet_create(int height, int width, int n_in, int n_out, const int c
       }
     }
     max_din = std::max(max_din, (long long)c.ci * hw);
-    const int H_l = height >> lev;
-    const int P = (H_l + 31) / 32;
+    const int P = wgrad_chunks(height >> lev, width >> lev, c.ci, c.co, u->sms);
     max_part = std::max(max_part, (long long)P * ((long long)c.co * c.ci * c.k * c.k + c.co));
   }
   if ((rc = ualloc(u, (void**)&u->dscratch, sizeof(float) * max_din)) ||
@@ -765,13 +786,13 @@ pf_status pf_unet_backward(pf_unet* u, const float* dy) {
     const __nv_bfloat16* out = (l == nl - 1) ? nullptr : u->act[l];
     const int relu = c.relu ? 1 : 0;
     // weight and bias gradients
-    const int P = (H + WG_ROWS - 1) / WG_ROWS;
+    const int P = wgrad_chunks(H, W, c.ci, c.co, u->sms);
     const long long nw = (long long)c.co * c.ci * c.k * c.k;
     float* part_b = u->wpart + (long long)P * nw;
     if (c.k == 3)
-      launch_wgrad_mma<3>(dout, out, relu, in, H, W, c.co, u->wpart, part_b, u->st);
+      launch_wgrad_mma<3>(dout, out, relu, in, H, W, c.co, P, u->wpart, part_b, u->st);
     else
-      launch_wgrad_mma<1>(dout, out, relu, in, H, W, c.co, u->wpart, part_b, u->st);
+      launch_wgrad_mma<1>(dout, out, relu, in, H, W, c.co, P, u->wpart, part_b, u->st);
     k_sum_parts<<<grid1(nw), 256, 0, u->st>>>(u->wpart, P, nw, u->g + c.off_w);
     k_sum_parts<<<grid1(c.co), 256, 0, u->st>>>(part_b, P, c.co, u->g + c.off_b);
     if (l == 0) continue;  // no gradient needed for the input features
