@@ -112,6 +112,9 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the uneven 2D batch (64 instances, 129^2 .. 1025^2) instead of the 3D workload")
     ap.add_argument("--batch-threads", type=int, default=0)
+    ap.add_argument("--batched-ops", action="store_true",
+                    help="time only the batched operators (one persistent launch over the instances)")
+    ap.add_argument("--batch-count", type=int, default=64, help="--batched-ops: instances of the draw")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched run: keep the default tile rule instead of the autotuner's choice")
     ap.add_argument("--learned", action="store_true",
@@ -994,6 +997,105 @@ def run_unet_kernels(args):
     return 0
 
 
+def time_batched_ops(pf, torch, Hs, states, K):
+    """The batched FP32 Hessian product over every instance in one persistent
+    launch (pf_batch_hessvec): microseconds per launch with CUDA events on
+    the batch's stream, HBM rate at the algorithmic 12 B/dof (x, v read, Hv
+    written; the vectors exceed L2), against the same products launched
+    one instance at a time."""
+    st = torch.cuda.Stream()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(17)
+    xs, vs, ys = [], [], []
+    for H, x in zip(Hs, states):
+        N = H.nodes()
+        x32 = x.float()
+        x32[:2 * N] += 1e-3 * torch.randn(2 * N, device="cuda", generator=g)
+        xs.append(x32)
+        vs.append(torch.randn(3 * N, device="cuda", generator=g))
+        ys.append(torch.empty(3 * N, device="cuda"))
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        B = pf.Batch(Hs, stream=st)
+        bps, tune_us = B.autotune(xs, vs, ys)
+        vhv = torch.empty(len(Hs), dtype=torch.float64, device="cuda")
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+
+        def timed(dot):
+            for _ in range(3):
+                B.hessvec(xs, vs, ys, vhv=vhv if dot else None)
+            a.record(st)
+            for _ in range(K):
+                B.hessvec(xs, vs, ys, vhv=vhv if dot else None)
+            b.record(st)
+            b.synchronize()
+            return a.elapsed_time(b) * 1e3 / K
+
+        us = timed(False)
+        us_dot = timed(True)
+    one = 0.0
+    for H, x32, v, y in zip(Hs, xs, vs, ys):
+        s2 = H.stream
+        with torch.cuda.stream(s2):
+            pf.hessvec(H, H.n_levels - 1, x32, v, out=y)
+            a.record(s2)
+            for _ in range(K):
+                pf.hessvec(H, H.n_levels - 1, x32, v, out=y)
+            b.record(s2)
+        b.synchronize()
+        one += a.elapsed_time(b) * 1e3 / K
+    B.close()
+    dofs = sum(H.ndof() for H in Hs)
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        src = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        hbm, src = 6800.0, "fallback"
+    gbs = 12.0 * dofs / (us * 1e-6) / 1e9
+    return {"kernel": "k_batch_hess2", "instances": len(Hs), "dofs": dofs, "us_per_launch": us,
+            "us_per_launch_with_vHv": us_dot, "gdofs": dofs / us / 1e3, "achieved_gbs": gbs,
+            "algorithmic_bytes": 12 * dofs, "peak_gbs": hbm, "hbm_frac": gbs / hbm, "peak_source": src,
+            "blocks_per_sm": bps, "autotune_us": tune_us, "one_launch_per_instance_us": one,
+            "speedup_vs_one_launch_per_instance": one / us, "launches_timed": K}
+
+
+def batched_instances(pf, torch, count, streams):
+    sizes, counts = PI.batched_grid_draw(PI.SEED_2D_BATCHED, 64)
+    sizes, counts = sizes[:count], counts[:count]
+    Hs, xs = [], []
+    for i, (n, nf) in enumerate(zip(sizes, counts)):
+        levels = int(round(np.log2((n - 1) / 16))) + 1
+        st = torch.cuda.Stream() if streams else None
+        H = pf.mesh_hierarchy_create(2, (17, 17), levels, 1 / 16, E=1.0, nu=0.3, Gc=1.0, stream=st)
+        x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        pf.fractures_set(H, pf.PF_LINE2D, PI.line_network_2d(PI.SEED_2D_BATCHED + 1 + i, nf),
+                         H.levels[-1][1], x)
+        Hs.append(H)
+        xs.append(x)
+    return sizes, counts, Hs, xs
+
+
+def run_batched_ops(args):
+    """Only the batched operators on the first --batch-count instances of the
+    uneven 2D draw (all 64 by default)."""
+    import torch
+    from paper_2007_12908_gb300 import build
+    build.build()
+    import paper_2007_12908_gb300 as pf
+    sizes, counts, Hs, xs = batched_instances(pf, torch, args.batch_count, True)
+    for H in Hs:
+        pf.pressure_set(H, 1e-3)
+    clocks = Clocks(0)
+    clocks.start()
+    r = time_batched_ops(pf, torch, Hs, xs, args.steps)
+    r["clocks"] = clocks.stop()
+    r["sizes"] = sizes
+    print(json.dumps({"batched_hessvec": r}))
+    return 0
+
+
 def run_batched(args):
     """Load steps of 64 uneven 2D instances (16 each of 129^2, 257^2, 513^2,
     1025^2 nodes; 10-1000 line fractures, +-30 deg families) run
@@ -1002,20 +1104,9 @@ def run_batched(args):
     from paper_2007_12908_gb300 import build
     build.build()
     import paper_2007_12908_gb300 as pf
-    sizes, counts = PI.batched_grid_draw(PI.SEED_2D_BATCHED, 64)
     prm = pf.default_params(precision=pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64,
                             start=pf.PF_START_EXTRAPOLATE if args.start == "extrapolate" else pf.PF_START_PLAIN)
-    Hs, xs = [], []
-    for i, (n, nf) in enumerate(zip(sizes, counts)):
-        levels = int(round(np.log2((n - 1) / 16))) + 1
-        st = torch.cuda.Stream()
-        H = pf.mesh_hierarchy_create(2, (17, 17), levels, 1 / 16, E=1.0, nu=0.3, Gc=1.0, stream=st)
-        x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
-        pf.fractures_set(H, pf.PF_LINE2D, PI.line_network_2d(PI.SEED_2D_BATCHED + 1 + i, nf),
-                         H.levels[-1][1], x)
-        Hs.append(H)
-        xs.append(x)
+    sizes, counts, Hs, xs = batched_instances(pf, torch, 64, True)
     dofs = sum(H.ndof() for H in Hs)
     # the tile autotuner on every instance (per level: the fastest FP32
     # Hessian tile variant, measured), unless --no-autotune
@@ -1046,6 +1137,7 @@ def run_batched(args):
         outs.append(out)
     clk = clocks.stop()
     sec = statistics.mean(times)
+    ops = time_batched_ops(pf, torch, Hs, xs, 20)
     line = {
         "metric": "batched RMTR load steps: GDoF/s over 64 uneven 2D instances",
         "value": dofs / sec / 1e9, "unit": "GDoF/s (load steps)", "n_gpus": 1,
@@ -1060,6 +1152,7 @@ def run_batched(args):
         "converged": [sum(o["converged"] for o in out) for out in outs],
         "cycles_mean": [statistics.mean(o["cycles"] for o in out) for out in outs],
         "clocks": clk,
+        "batched_hessvec": ops,
     }
     print(json.dumps(line))
     return 0
@@ -1071,6 +1164,8 @@ def main():
         return oracle_worker(json.loads(args.oracle_worker))
     if args.impl == "reference":
         return run_reference(args)
+    if args.batched_ops:
+        return run_batched_ops(args)
     if args.batched:
         return run_batched(args)
     if args.paper_scale:

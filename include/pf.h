@@ -426,6 +426,47 @@ pf_status pf_autotune(pf_hierarchy* h, int* variant_out, double* us_out);
 pf_status pf_tile_variant_set(pf_hierarchy* h, int level, int variant);
 pf_status pf_tile_variant_get(const pf_hierarchy* h, int level, int* variant);
 
+/* ------------------------------------------------------------------------
+ * Batched 2D operators (no counterpart in the paper, which solves one
+ * network per run): the finest levels of n 2D hierarchies of any sizes
+ * evaluated by ONE persistent launch over an (instance, strip, row) work
+ * list -- strips of 63 node columns, every warp an equal share of all
+ * instances' rows -- with per-instance (segmented) reductions.  The
+ * operators are those of pf_hessvec and pf_energy (Sec. 2 functional,
+ * Sec. 4.2.1 Hessian), on each instance's own grid, material and current
+ * pressure (read from its hierarchy at every call).
+ *
+ * pf_batch_create keeps the hierarchies (they must outlive the batch) and
+ * runs on `stream` (cudaStream_t, NULL = legacy stream).  2D only
+ * (PF_EINVAL otherwise).  Device scratch: one double per node row of each
+ * strip and per element row (about 8 B per 60 nodes). */
+typedef struct pf_batch pf_batch;
+pf_status pf_batch_create(int n, pf_hierarchy* const* hs, void* stream, pf_batch** out);
+pf_status pf_batch_destroy(pf_batch* b);
+/* Total dofs, blocks per SM of the product launch, SM count. */
+pf_status pf_batch_info(const pf_batch* b, long long* dofs, int* blocks_per_sm, int* sms);
+/* Hv_dev[i] = H(x_dev[i]) v_dev[i] for every instance, FP32 vectors of
+ * 3 N_i values (planes u_x, u_y, c), computed in FP32 with paired-FP32
+ * instructions.  Hv_dev[i] must not overlap x_dev[i] or v_dev[i].  With
+ * vHv_dev (device, n doubles; may be NULL) also v_i . H v_i per instance
+ * (FP32 node-row sums, FP64 across rows, fixed order).  Asynchronous on
+ * the batch's stream; results are the same bit for bit for every launch
+ * configuration.  The pointer tables are copied to the device when they
+ * change (the call then synchronises the stream once). */
+pf_status pf_batch_hessvec(pf_batch* b, const float* const* x_dev, const float* const* v_dev,
+                           float* const* Hv_dev, double* vHv_dev);
+/* E_host[i] = energy of FP64 x_dev[i] (3 N_i values), FP64 arithmetic,
+ * element rows summed in a fixed order.  Synchronous; PF_ENONFINITE if
+ * any energy is not finite. */
+pf_status pf_batch_energy(pf_batch* b, const double* const* x_dev, double* E_host);
+/* Autotuner of the product launch: times blocks per SM 1 .. 4 (those the
+ * kernel's occupancy allows; us_out[k-1] = -1 otherwise) on the given
+ * vectors with CUDA events (one warm-up, five timed) and keeps the
+ * fastest.  bps_out, us_out (4 doubles) may be NULL. */
+pf_status pf_batch_autotune(pf_batch* b, const float* const* x_dev, const float* const* v_dev,
+                            float* const* Hv_dev, int* bps_out, double* us_out);
+pf_status pf_batch_variant_set(pf_batch* b, int blocks_per_sm);
+
 /* Measurement helper with no counterpart in the paper: runs a kernel of
  * independent fused multiply-adds in precision prec on the legacy stream
  * and writes the achieved rate (flop/s, an FMA counted as 2) to *flops_host.

@@ -38,6 +38,8 @@ EXPORTS = [
     "pf_energy_diff_mixed", "pf_gradient_step", "pf_gradient_df", "pf_energy_df",
     "pf_state_save", "pf_state_load", "pf_galerkin_set", "pf_galerkin_apply", "pf_qp_pgs",
     "pf_qp_mprgp", "pf_autotune", "pf_tile_variant_set", "pf_tile_variant_get",
+    "pf_batch_create", "pf_batch_destroy", "pf_batch_info", "pf_batch_hessvec", "pf_batch_energy",
+    "pf_batch_autotune", "pf_batch_variant_set",
 ]
 
 
@@ -146,6 +148,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_projected_gradient": (i, [vp, vp, C.POINTER(d)]),
         "pf_rmtr_load_step_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(RmtrParams), i,
                                         C.POINTER(RmtrStats), C.POINTER(C.c_int)]),
+        "pf_batch_create": (i, [i, C.POINTER(vp), vp, C.POINTER(vp)]),
+        "pf_batch_destroy": (i, [vp]),
+        "pf_batch_info": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "pf_batch_hessvec": (i, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]),
+        "pf_batch_energy": (i, [vp, C.POINTER(vp), C.POINTER(d)]),
+        "pf_batch_autotune": (i, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int),
+                                  C.POINTER(d)]),
+        "pf_batch_variant_set": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -480,6 +490,78 @@ def tile_variant_get(H: Hierarchy, level: int) -> int:
     out = C.c_int()
     _check(lib().pf_tile_variant_get(H.handle, level, C.byref(out)))
     return out.value
+
+
+class Batch:
+    """Batched 2D operators over the finest levels of several hierarchies:
+    one persistent launch per call over every instance (pf_batch_*).  The
+    hierarchies must stay open while the batch is used."""
+
+    def __init__(self, Hs, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.Hs = list(Hs)
+        hv = (C.c_void_p * len(self.Hs))(*[H.handle for H in self.Hs])
+        out = C.c_void_p()
+        _check(lib().pf_batch_create(len(self.Hs), hv, C.c_void_p(stream.cuda_stream), C.byref(out)))
+        self.handle = out
+
+    def info(self):
+        dofs, bps, sms = C.c_longlong(), C.c_int(), C.c_int()
+        _check(lib().pf_batch_info(self.handle, C.byref(dofs), C.byref(bps), C.byref(sms)))
+        return {"dofs": dofs.value, "blocks_per_sm": bps.value, "sms": sms.value}
+
+    def _tables(self, xs, vs, ys):
+        import torch
+        n = len(self.Hs)
+        if not (len(xs) == len(vs) == len(ys) == n):
+            raise ValueError("one x, v and Hv per instance")
+        xt = (C.c_void_p * n)(*[_dev(x, H.ndof(), torch.float32).value for H, x in zip(self.Hs, xs)])
+        vt = (C.c_void_p * n)(*[_dev(v, H.ndof(), torch.float32).value for H, v in zip(self.Hs, vs)])
+        yt = (C.c_void_p * n)(*[_dev(y, H.ndof(), torch.float32).value for H, y in zip(self.Hs, ys)])
+        return xt, vt, yt
+
+    def hessvec(self, xs, vs, ys=None, vhv=None):
+        """ys[i] = H(xs[i]) vs[i] (float32 CUDA tensors); with vhv (a float64
+        CUDA tensor of one value per instance) also vs[i] . ys[i]."""
+        import torch
+        ys = [torch.empty_like(v) for v in vs] if ys is None else ys
+        xt, vt, yt = self._tables(xs, vs, ys)
+        dp = _dev(vhv, len(self.Hs), torch.float64) if vhv is not None else None
+        _check(lib().pf_batch_hessvec(self.handle, xt, vt, yt, dp))
+        return ys
+
+    def energy(self, xs):
+        """Energies of float64 states xs[i], one float per instance."""
+        import torch
+        n = len(self.Hs)
+        xt = (C.c_void_p * n)(*[_dev(x, H.ndof(), torch.float64).value for H, x in zip(self.Hs, xs)])
+        out = (C.c_double * n)()
+        _check(lib().pf_batch_energy(self.handle, xt, out))
+        return list(out)
+
+    def autotune(self, xs, vs, ys):
+        xt, vt, yt = self._tables(xs, vs, ys)
+        bps = C.c_int()
+        us = (C.c_double * 4)()
+        _check(lib().pf_batch_autotune(self.handle, xt, vt, yt, C.byref(bps), us))
+        return bps.value, list(us)
+
+    def variant_set(self, blocks_per_sm):
+        _check(lib().pf_batch_variant_set(self.handle, blocks_per_sm))
+
+    def close(self):
+        if self.handle:
+            lib().pf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def qp_pgs(H: Hierarchy, level: int, g, lo, hi, s, sweeps):

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpf.so")
 SOURCES = ["pf_kernels.cu", "pf_solver.cu", "pf_api.cu", "pf_noalloc.cu", "pf_unet.cu", "pf_learned.cu",
-           "pf_state.cu", "pf_galerkin.cu"]
+           "pf_state.cu", "pf_galerkin.cu", "pf_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--extended-lambda", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]
