@@ -115,6 +115,10 @@ def parse():
     ap.add_argument("--batched-ops", action="store_true",
                     help="time only the batched operators (one persistent launch over the instances)")
     ap.add_argument("--batch-count", type=int, default=64, help="--batched-ops: instances of the draw")
+    ap.add_argument("--batch-bps", type=int, default=0,
+                    help="--batched-ops: blocks per SM of the product launch (0: autotune)")
+    ap.add_argument("--batch-stride", type=int, default=1,
+                    help="--batched-ops: every k-th instance of the draw (the draw is sorted by size)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched run: keep the default tile rule instead of the autotuner's choice")
     ap.add_argument("--learned", action="store_true",
@@ -997,7 +1001,7 @@ def run_unet_kernels(args):
     return 0
 
 
-def time_batched_ops(pf, torch, Hs, states, K):
+def time_batched_ops(pf, torch, Hs, states, K, bps=0):
     """The batched FP32 Hessian product over every instance in one persistent
     launch (pf_batch_hessvec): microseconds per launch with CUDA events on
     the batch's stream, HBM rate at the algorithmic 12 B/dof (x, v read, Hv
@@ -1017,7 +1021,11 @@ def time_batched_ops(pf, torch, Hs, states, K):
     torch.cuda.synchronize()
     with torch.cuda.stream(st):
         B = pf.Batch(Hs, stream=st)
-        bps, tune_us = B.autotune(xs, vs, ys)
+        if bps:  # a fixed launch configuration (e.g. under a profiler, whose replays skew the timings)
+            B.variant_set(bps)
+            tune_us = None
+        else:
+            bps, tune_us = B.autotune(xs, vs, ys)
         vhv = torch.empty(len(Hs), dtype=torch.float64, device="cuda")
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -1060,11 +1068,12 @@ def time_batched_ops(pf, torch, Hs, states, K):
             "speedup_vs_one_launch_per_instance": one / us, "launches_timed": K}
 
 
-def batched_instances(pf, torch, count, streams):
+def batched_instances(pf, torch, count, streams, stride=1):
     sizes, counts = PI.batched_grid_draw(PI.SEED_2D_BATCHED, 64)
-    sizes, counts = sizes[:count], counts[:count]
+    pick = list(range(0, 64, stride))[:count]
     Hs, xs = [], []
-    for i, (n, nf) in enumerate(zip(sizes, counts)):
+    for i in pick:
+        n, nf = sizes[i], counts[i]
         levels = int(round(np.log2((n - 1) / 16))) + 1
         st = torch.cuda.Stream() if streams else None
         H = pf.mesh_hierarchy_create(2, (17, 17), levels, 1 / 16, E=1.0, nu=0.3, Gc=1.0, stream=st)
@@ -1074,7 +1083,7 @@ def batched_instances(pf, torch, count, streams):
                          H.levels[-1][1], x)
         Hs.append(H)
         xs.append(x)
-    return sizes, counts, Hs, xs
+    return [sizes[i] for i in pick], [counts[i] for i in pick], Hs, xs
 
 
 def run_batched_ops(args):
@@ -1084,12 +1093,12 @@ def run_batched_ops(args):
     from paper_2007_12908_gb300 import build
     build.build()
     import paper_2007_12908_gb300 as pf
-    sizes, counts, Hs, xs = batched_instances(pf, torch, args.batch_count, True)
+    sizes, counts, Hs, xs = batched_instances(pf, torch, args.batch_count, True, args.batch_stride)
     for H in Hs:
         pf.pressure_set(H, 1e-3)
     clocks = Clocks(0)
     clocks.start()
-    r = time_batched_ops(pf, torch, Hs, xs, args.steps)
+    r = time_batched_ops(pf, torch, Hs, xs, args.steps, args.batch_bps)
     r["clocks"] = clocks.stop()
     r["sizes"] = sizes
     print(json.dumps({"batched_hessvec": r}))

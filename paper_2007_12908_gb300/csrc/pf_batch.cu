@@ -7,10 +7,10 @@
 // per-instance launch and the grid ends together.
 //
 // A warp marches up its strip one element row at a time.  Lane j evaluates
-// the two elements of columns c0 - 1 + 2j and c0 + 2j as the two halves of
+// the elements of columns c0 + j and c0 + 32 + j as the two halves of
 // float2 values (paired FP32 instructions), reading only node row y + 1 per
-// step: the row below is still in registers, the right-hand corner comes
-// from the next lane by a shuffle.  Corner contributions are added per
+// step (the row below is still in registers); a node's right-hand element
+// is in the next lane, reached by a shuffle.  Corner contributions are added per
 // node in a fixed order -- left element before right, the element row
 // below before the one above -- so the product is the same bit for bit for
 // every grid size, strip cut and warp range (and across autotuned
@@ -177,115 +177,124 @@ __device__ __forceinline__ void hess2_pair(const float2 xe[3][4], const float2 v
   test_pair<true>(s0, scx, scy, out[2]);
 }
 
-// One row of node values of a vector (3 planes) at the lane's columns
-// nA, nB and nC = nB + 1 (nC from the next lane; lane 31 loads its own).
-struct Row3 {
-  float a[3], b[3], c[3];
+// One row of node values of a vector (3 planes) as element-pair corners:
+// lane j's elements are columns e1 = c0 + j and e2 = c0 + 32 + j, so
+// L = (node e1, node e2) holds their left corners and R = (node e1 + 1,
+// node e2 + 1) their right ones; no node value sits in two pairs of a lane.
+// Interior rows of interior strips (every column and the row inside the
+// grid, a warp-uniform test) load with no bounds checks; elsewhere values
+// outside the grid read as 0 (they only enter elements outside the grid,
+// whose outputs are dropped).  Indices are 32-bit: pf_batch_create refuses
+// instances with 3 N >= 2^31.
+struct Row2 {
+  float2 L[3], R[3];
 };
-struct Cols {
-  int nA, nB, nC;
-  bool inA, inB, inC;
-};
-__device__ __forceinline__ void load_ab(const float* __restrict__ src, const Geom& g, const Cols& k,
-                                        int y, float a[3], float b[3]) {
-  const bool ry = y >= 0 && y < g.n[1];
+template <bool EDGE>
+__device__ __forceinline__ void load_row(const float* __restrict__ src, int N, int n0, int n1,
+                                         int e1, int y, Row2& r) {
+  if constexpr (!EDGE) {
+    const float* p = src + (y * n0 + e1);
 #pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    const long long base = f * g.N + (long long)y * g.n[0];
-    a[f] = (ry && k.inA) ? __ldg(src + base + k.nA) : 0.f;
-    b[f] = (ry && k.inB) ? __ldg(src + base + k.nB) : 0.f;
+    for (int f = 0; f < 3; ++f) {
+      r.L[f] = make_float2(__ldg(p + f * N), __ldg(p + f * N + 32));
+      r.R[f] = make_float2(__ldg(p + f * N + 1), __ldg(p + f * N + 33));
+    }
+  } else {
+    const bool ry = y >= 0 && y < n1;
+    const bool i0 = ry && e1 >= 0 && e1 < n0, i1 = ry && e1 + 1 < n0;
+    const bool i32 = ry && e1 + 32 < n0, i33 = ry && e1 + 33 < n0;
+    const int b = ry ? y * n0 + e1 : 0;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const float* p = src + f * N + b;
+      r.L[f] = make_float2(i0 ? __ldg(p) : 0.f, i32 ? __ldg(p + 32) : 0.f);
+      r.R[f] = make_float2(i1 ? __ldg(p + 1) : 0.f, i33 ? __ldg(p + 33) : 0.f);
+    }
   }
 }
-__device__ __forceinline__ void finish_row(const float* __restrict__ src, const Geom& g,
-                                           const Cols& k, int y, int lane, const float a[3],
-                                           const float b[3], Row3& r) {
-  const bool own_c = lane == 31 && y >= 0 && y < g.n[1] && k.inC;
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    r.a[f] = a[f];
-    r.b[f] = b[f];
-    float c = __shfl_down_sync(kFull, a[f], 1);
-    if (lane == 31) c = own_c ? __ldg(src + f * g.N + (long long)y * g.n[0] + k.nC) : 0.f;
-    r.c[f] = c;
-  }
+__device__ __forceinline__ void load_row(bool interior, const float* __restrict__ src, int N,
+                                         int n0, int n1, int e1, int y, Row2& r) {
+  if (interior && y >= 0 && y < n1) load_row<false>(src, N, n0, n1, e1, y, r);
+  else load_row<true>(src, N, n0, n1, e1, y, r);
 }
 
 // Rows [r0, r0 + rows) of strip `strip` of one instance: the Hessian at x
 // applied to v, written to y; with DOT, the node rows' v . Hv to
-// rowdot[0 .. rows).
+// rowdot[0 .. rows).  The strip evaluates element columns c0 .. c0 + 63
+// (c0 = 63 strip - 1) and owns node columns c0 + 1 .. c0 + 63: lane j the
+// nodes c0 + 1 + j (right corner of e1 plus left corner of the next
+// element) and, for j < 31, c0 + 33 + j.
 template <bool DOT>
 __device__ __forceinline__ void hess2_strip(const BInst& I, const BVec& V, int strip, int r0,
                                             int rows, int lane, double* __restrict__ rowdot) {
-  const Geom& g = I.g;
-  const int n0 = g.n[0], n1 = g.n[1];
-  Cols k;
-  k.nA = strip * kStripCols - 1 + 2 * lane;
-  k.nB = k.nA + 1;
-  k.nC = k.nA + 2;
-  k.inA = k.nA >= 0 && k.nA < n0;
-  k.inB = k.nB < n0;
-  k.inC = k.nC < n0;
-  const bool elA = k.nA >= 0 && k.nA < n0 - 1, elB = k.nB < n0 - 1;
-  const bool ownA = lane > 0 && k.inA, ownB = k.inB;
-  Row3 bx, bv, tx, tv;
-  {
-    float a[3], b[3];
-    load_ab(V.x, g, k, r0 - 1, a, b);
-    finish_row(V.x, g, k, r0 - 1, lane, a, b, bx);
-    load_ab(V.v, g, k, r0 - 1, a, b);
-    finish_row(V.v, g, k, r0 - 1, lane, a, b, bv);
-  }
-  float pxa[3], pxb[3], pva[3], pvb[3];  // the next row, loaded one step ahead
-  load_ab(V.x, g, k, r0, pxa, pxb);
-  load_ab(V.v, g, k, r0, pva, pvb);
-  float carA[3] = {0.f, 0.f, 0.f}, carB[3] = {0.f, 0.f, 0.f};
+  const int n0 = I.g.n[0], n1 = I.g.n[1], N = int(I.g.N);
+  const int c0 = strip * kStripCols - 1;
+  const int e1 = c0 + lane;
+  const bool interior = strip > 0 && c0 + 64 < n0;  // columns c0 .. c0 + 64 inside (warp-uniform)
+  const bool ok1 = e1 >= 0 && e1 < n0 - 1, ok2 = e1 + 32 < n0 - 1;
+  const bool all_el = __all_sync(kFull, ok1 && ok2);
+  const bool own1 = e1 + 1 < n0, own2 = lane < 31 && e1 + 33 < n0;
+  const int src_lane = (lane + 1) & 31;  // the lane holding the element right of e1 (lane 31: e2 of lane 0)
+  Row2 bx, bv, tx, tv, px, pv;
+  load_row(interior, V.x, N, n0, n1, e1, r0 - 1, bx);
+  load_row(interior, V.v, N, n0, n1, e1, r0 - 1, bv);
+  load_row(interior, V.x, N, n0, n1, e1, r0, px);  // the next row, loaded one step ahead
+  load_row(interior, V.v, N, n0, n1, e1, r0, pv);
+  float car1[3] = {0.f, 0.f, 0.f}, car2[3] = {0.f, 0.f, 0.f};
   for (int s = 0; s <= rows; ++s) {
     const int ey = r0 - 1 + s;  // element row; its top node row is ey + 1
-    finish_row(V.x, g, k, ey + 1, lane, pxa, pxb, tx);
-    finish_row(V.v, g, k, ey + 1, lane, pva, pvb, tv);
+    tx = px;
+    tv = pv;
     if (s < rows) {
-      load_ab(V.x, g, k, ey + 2, pxa, pxb);
-      load_ab(V.v, g, k, ey + 2, pva, pvb);
+      load_row(interior, V.x, N, n0, n1, e1, ey + 2, px);
+      load_row(interior, V.v, N, n0, n1, e1, ey + 2, pv);
     }
     float2 xe[3][4], ve[3][4];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      xe[f][0] = f2(bx.a[f], bx.b[f]);
-      xe[f][1] = f2(bx.b[f], bx.c[f]);
-      xe[f][2] = f2(tx.a[f], tx.b[f]);
-      xe[f][3] = f2(tx.b[f], tx.c[f]);
-      ve[f][0] = f2(bv.a[f], bv.b[f]);
-      ve[f][1] = f2(bv.b[f], bv.c[f]);
-      ve[f][2] = f2(tv.a[f], tv.b[f]);
-      ve[f][3] = f2(tv.b[f], tv.c[f]);
+      xe[f][0] = bx.L[f];
+      xe[f][1] = bx.R[f];
+      xe[f][2] = tx.L[f];
+      xe[f][3] = tx.R[f];
+      ve[f][0] = bv.L[f];
+      ve[f][1] = bv.R[f];
+      ve[f][2] = tv.L[f];
+      ve[f][3] = tv.R[f];
     }
     float2 out[3][4];
     hess2_pair(xe, ve, I, out);
     const bool rowok = ey >= 0 && ey < n1 - 1;
-    const bool okA = rowok && elA, okB = rowok && elB;
+    if (!(rowok && all_el)) {  // warp-uniform: drop elements outside the grid
+      const bool a = rowok && ok1, b = rowok && ok2;
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!a) out[f][k].x = 0.f;
+          if (!b) out[f][k].y = 0.f;
+        }
+    }
     float dot = 0.f;
+    float* yrow = V.y + (ey * n0 + e1 + 1);  // dereferenced only for ey in [r0, r0 + rows)
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        if (!okA) out[f][a].x = 0.f;
-        if (!okB) out[f][a].y = 0.f;
-      }
-      // node row ey from the bottom corners, row ey + 1 from the top ones;
-      // per node the left element's corner comes first
-      const float lb = __shfl_up_sync(kFull, out[f][1].y, 1);
-      const float lt = __shfl_up_sync(kFull, out[f][3].y, 1);
-      const float botA = lb + out[f][0].x, botB = out[f][1].x + out[f][0].y;
-      const float topA = lt + out[f][2].x, topB = out[f][3].x + out[f][2].y;
+      // per node the left element's corner comes first: right corner of
+      // e1 (e2) plus the left corner of the element to its right
+      const float sb = lane == 0 ? out[f][0].y : out[f][0].x;
+      const float st = lane == 0 ? out[f][2].y : out[f][2].x;
+      const float rb1 = __shfl_sync(kFull, sb, src_lane), rt1 = __shfl_sync(kFull, st, src_lane);
+      const float rb2 = __shfl_down_sync(kFull, out[f][0].y, 1);
+      const float rt2 = __shfl_down_sync(kFull, out[f][2].y, 1);
+      const float bot1 = out[f][1].x + rb1, bot2 = out[f][1].y + rb2;
+      const float top1 = out[f][3].x + rt1, top2 = out[f][3].y + rt2;
       if (s > 0) {
-        const float hA = carA[f] + botA, hB = carB[f] + botB;
-        const long long base = f * g.N + (long long)ey * n0;
-        if (ownA) V.y[base + k.nA] = hA;
-        if (ownB) V.y[base + k.nB] = hB;
-        if constexpr (DOT) dot += (ownA ? hA * bv.a[f] : 0.f) + (ownB ? hB * bv.b[f] : 0.f);
+        const float h1 = car1[f] + bot1, h2 = car2[f] + bot2;
+        if (own1) yrow[f * N] = h1;
+        if (own2) yrow[f * N + 32] = h2;
+        if constexpr (DOT) dot += (own1 ? h1 * bv.R[f].x : 0.f) + (own2 ? h2 * bv.R[f].y : 0.f);
       }
-      carA[f] = topA;
-      carB[f] = topB;
+      car1[f] = top1;
+      car2[f] = top2;
     }
     if constexpr (DOT) {
       if (s > 0) {
@@ -548,6 +557,8 @@ pf_status pf_batch_create(int n, pf_hierarchy* const* hs, void* stream, pf_batch
   for (int i = 0; i < n; ++i) {
     if (!hs[i]) return bad_b("batch_create: null hierarchy");
     if (hs[i]->dim != 2) return bad_b("batch_create: the batched operators are 2D");
+    if (3 * hs[i]->geo[hs[i]->L - 1].N >= (1LL << 31))
+      return bad_b("batch_create: an instance has 3 N >= 2^31 dofs (32-bit indices)");
   }
   pf_batch* b = new pf_batch();
   b->n = n;
