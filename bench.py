@@ -135,6 +135,8 @@ def parse():
                     help="the paper's 3D scenario at its size (393^3, 242.8M dofs, 100 plates)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched-ops", action="store_true",
+                    help="skip the batched 2D product measurement of the default line")
     return ap.parse_args()
 
 
@@ -750,6 +752,22 @@ def run_ours(args):
                                                             allc["energy"]))},
                "hessvec_129_gpu_fp32_over_oracle": (pass_all["passes"]["hessvec"]["seconds"] / t32)}
 
+    # ---- the batched workload's data-parallel kernel: the FP32 Hessian
+    # product of the 64 uneven 2D instances in one persistent launch
+    bops = None
+    if rank == 0 and world == 1 and not args.no_batched_ops:
+        _, _, Hb, xb = batched_instances(pf, torch, 64, True)
+        for Hh in Hb:
+            pf.pressure_set(Hh, 1e-3)
+        bclk = Clocks(0)
+        bclk.start()
+        bops = time_batched_ops(pf, torch, Hb, xb, 20)
+        bops["clocks"] = bclk.stop()
+        for Hh in Hb:
+            Hh.close()
+        del Hb, xb
+        torch.cuda.empty_cache()
+
     launches = int(sum(s["launches"] for s in stats))
     value = job_s
     if rank == 0:
@@ -775,6 +793,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
+            "batched_hessvec": bops,
             "solver": {k: [s[k] for s in stats] for k in ("cycles", "converged", "cg", "tr_its",
                                                           "tr_rejected", "coarse_rejected", "status",
                                                           "hv_cauchy", "hv_search", "cg_restarts",

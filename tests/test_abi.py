@@ -112,3 +112,18 @@ def test_batch_validation_on_host(lib):
     xv = (C.c_void_p * 1)(None)
     assert lib.pf_rmtr_load_step_batch(1, hv, xv, None, 0, None, None) == B.PF_EINVAL
     assert lib.pf_rmtr_load_step_batch(0, None, None, None, 0, None, None) == B.PF_OK
+
+
+def test_batched_operators_validation_on_host(lib):
+    out = C.c_void_p()
+    assert lib.pf_batch_create(0, None, None, C.byref(out)) == B.PF_EINVAL
+    hv = (C.c_void_p * 2)(None, None)
+    assert lib.pf_batch_create(2, hv, None, C.byref(out)) == B.PF_EINVAL
+    assert b"null hierarchy" in lib.pf_last_error()
+    assert lib.pf_batch_create(1, hv, None, None) == B.PF_EINVAL
+    assert lib.pf_batch_hessvec(None, None, None, None, None) == B.PF_EINVAL
+    assert lib.pf_batch_energy(None, None, None) == B.PF_EINVAL
+    assert lib.pf_batch_info(None, None, None, None) == B.PF_EINVAL
+    assert lib.pf_batch_autotune(None, None, None, None, None, None) == B.PF_EINVAL
+    assert lib.pf_batch_variant_set(None, 1) == B.PF_EINVAL
+    assert lib.pf_batch_destroy(None) == B.PF_OK
