@@ -128,6 +128,8 @@ def parse():
     ap.add_argument("--heldout", type=int, default=20, help="--learned: held-out trajectories")
     ap.add_argument("--fractures", type=int, default=1000, help="--learned: line fractures per network")
     ap.add_argument("--train-steps", type=int, default=2000, help="--learned: Adam steps (batch 4)")
+    ap.add_argument("--traj-batch", type=int, default=8,
+                    help="--learned: trajectories generated concurrently")
     ap.add_argument("--unet-kernels", action="store_true",
                     help="time the U-Net's tensor-core convolutions on a --unet-size grid")
     ap.add_argument("--unet-size", type=int, default=1032)
@@ -906,20 +908,38 @@ def run_learned(args):
     solver = dict(precision=pf.PF_FP32, coarse_model=pf.PF_GALERKIN, cg_smooth=50, cg_fine=200)
     prm = pf.default_params(start=pf.PF_START_EXTRAPOLATE, **solver)
 
-    def network(seed):
+    def network(seed, Hh=None):
+        """The seeded network's fractures in x0 and in Hh's c_prev (the
+        irreversibility bound belongs to the hierarchy that solves it)."""
+        Hh = H if Hh is None else Hh
         x0 = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
-        pf.fractures_set(H, pf.PF_LINE2D, PI.line_network_2d(seed, args.fractures), h, x0)
+        torch.cuda.synchronize()
+        pf.fractures_set(Hh, pf.PF_LINE2D, PI.line_network_2d(seed, args.fractures), h, x0)
+        torch.cuda.synchronize()
         return x0
 
     learner = Lm.LearnedIterate(H, seed=1)
     data = []
     t0 = time.perf_counter()
-    for k in range(args.traj):
-        states = Lm.trajectory(H, network(PI.SEED_2D_LEARNED + k), pressures, prm)
-        data += Lm.samples(learner, states, pressures)
-        del states
-        print(f"trajectory {k + 1}/{args.traj}: {len(data)} samples, {time.perf_counter() - t0:.0f} s",
+    # trajectories in groups of --traj-batch, each group's load steps run
+    # concurrently on hierarchies of their own (one stream each)
+    K = max(1, args.traj_batch)
+    Hg = [H] + [pf.mesh_hierarchy_create(2, (17, 17), 7, 1 / 16, E=1.0, nu=0.3, Gc=1.0,
+                                         stream=torch.cuda.Stream()) for _ in range(K - 1)]
+    for k0 in range(0, args.traj, K):
+        ks = list(range(k0, min(args.traj, k0 + K)))
+        x0s = [network(PI.SEED_2D_LEARNED + k, Hg[j]) for j, k in enumerate(ks)]
+        if K == 1:
+            group = [Lm.trajectory(H, x0s[0], pressures, prm)]
+        else:
+            group = Lm.trajectories(Hg[:len(ks)], x0s, pressures, prm)
+        for states in group:
+            data += Lm.samples(learner, states, pressures)
+        del group, x0s
+        print(f"trajectories {ks[-1] + 1}/{args.traj}: {len(data)} samples, {time.perf_counter() - t0:.0f} s",
               file=sys.stderr, flush=True)
+    for Hh in Hg[1:]:
+        Hh.close()
     t_data = time.perf_counter() - t0
     t1 = time.perf_counter()
     losses = Lm.train(learner, data, steps=args.train_steps, lr=1e-3, batch=4)
@@ -949,6 +969,7 @@ def run_learned(args):
         "config": {"workload": "2d_1025^2_q1_7level_1000lines_ramp20", "grid": [nx, ny], "levels": 7,
                    "dofs": H.ndof(), "fractures": args.fractures, "pressure_steps": pressures,
                    "training_trajectories": args.traj, "heldout_trajectories": args.heldout,
+                   "trajectories_generated_concurrently": max(1, args.traj_batch),
                    "samples": args.traj * (steps - 1), "adam_steps": args.train_steps, "batch": 4,
                    "precision": "mixed", "coarse_model": "galerkin", "cg_smooth": 50, "cg_fine": 200,
                    "network": "U-Net 16-32-64-128, BF16, tensor-core convolutions"},

@@ -100,6 +100,24 @@ def trajectory(H, x0, pressures, params):
     return states
 
 
+def trajectories(Hs, x0s, pressures, params, n_threads=0):
+    """trajectory() of several networks at once: at every pressure one
+    batched load step over the hierarchies Hs (same grid, one stream each),
+    run concurrently by the library's host workers."""
+    import torch
+    xs = [x0.clone() for x0 in x0s]
+    states = [[x.clone()] for x in xs]
+    for p in pressures:
+        for H in Hs:
+            B.pressure_set(H, p)
+        torch.cuda.synchronize()
+        B.rmtr_load_step_batch(Hs, xs, params, n_threads=n_threads)
+        torch.cuda.synchronize()
+        for k, x in enumerate(xs):
+            states[k].append(x.clone())
+    return states
+
+
 def samples(learner, states, pressures):
     """(features, target) pairs of every transition t-1 -> t with p_{t-1} > 0."""
     out = []

@@ -221,6 +221,27 @@ def test_batched_energy_matches_oracle():
         t[0].close()
 
 
+def test_batched_energy_non_finite():
+    """A NaN in one instance's state makes pf_batch_energy return
+    PF_ENONFINITE; the other instances' energies are still written."""
+    torch = require_cuda()
+    import paper_2007_12908_gb300 as pf
+    from oracle import pf_oracle as O
+    from tests.gpu_common import dev
+    inst, B = _ragged_batch(torch, pf)
+    xs = [dev(t[2]) for t in inst]
+    xs[2][5] = float("nan")
+    with pytest.raises(pf.PfError) as e:
+        B.energy(xs)
+    assert e.value.status == pf.PF_ENONFINITE
+    xs[2][5] = 0.0
+    E = B.energy(xs)
+    assert all(np.isfinite(E))
+    B.close()
+    for t in inst:
+        t[0].close()
+
+
 def test_batched_rejects_3d():
     torch = require_cuda()
     import paper_2007_12908_gb300 as pf
