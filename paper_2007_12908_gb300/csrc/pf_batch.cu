@@ -35,7 +35,7 @@ namespace {
 constexpr int kStripCols = 63;   // node columns a warp owns (64 element columns)
 constexpr int kSegChunk = 2048;  // partials per block of the segmented sum
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kHessThreads = 128;  // 4 warps per block, 3 blocks per SM at 152 registers
+constexpr int kHessThreads = 128;  // 4 warps per block; 3 blocks per SM fit its 168 registers
 
 struct BInst {
   Geom g;            // finest grid of the instance
@@ -55,7 +55,6 @@ struct BVec {
   float* y;
 };
 
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 using p2::add2;
 using p2::bc;
 using p2::fma2;
