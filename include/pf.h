@@ -359,6 +359,27 @@ pf_status pf_rmtr_load_step_batch(int n, pf_hierarchy* const* hs, double* const*
 /* Copies the finest-level c_prev (FP64, N values) to c_prev_dev. */
 pf_status pf_get_c_prev(pf_hierarchy* h, double* c_prev_dev);
 
+/* Fields the solver keeps for a level, copied to out_dev (FP64, device):
+ *   PF_FIELD_C_PREV  the irreversibility bound c_prev (finest level only;
+ *                    N values), eq. (space_pf);
+ *   PF_FIELD_LOWER,  the level's feasible set as the last load step left it
+ *   PF_FIELD_UPPER   ((d+1) N values): on the finest level eq. (space_pf)
+ *                    (c_prev <= c <= 1, u = 0 on the boundary, u free
+ *                    elsewhere as -inf / +inf); on a coarser level the
+ *                    coarse feasible set F^l of the last V-cycle around
+ *                    its start x0 = P x (Alg. 1); PF_ESTATE before the
+ *                    first load step and after pf_fractures_set or
+ *                    pf_state_load;
+ *   PF_FIELD_FIXED   1 for the dofs the clamped boundary fixes (every u
+ *                    component on the boundary), 0 elsewhere ((d+1) N).
+ * PF_EINVAL for another `which` or c_prev asked of a coarse level.
+ * Asynchronous on the hierarchy's stream. */
+#define PF_FIELD_C_PREV 0
+#define PF_FIELD_LOWER 1
+#define PF_FIELD_UPPER 2
+#define PF_FIELD_FIXED 3
+pf_status pf_get_fields(pf_hierarchy* h, int level, int which, double* out_dev);
+
 /* Checkpoint and resume (Sec. 4.1 workflow: the state is exported after
  * every pseudo-time step).  pf_state_save writes the finest FP64 state x_dev
  * ((dim+1) N values), the hierarchy's c_prev, the current pressure and the

@@ -12,7 +12,7 @@ from ._binding import (  # noqa: F401
     hessvec, hessvec_lag_set, hessvec_lagged, mesh_hierarchy_create, pressure_set, project, prolong, restrict, rmtr_load_step,
     rmtr_load_step_host, projected_gradient, rmtr_load_step_batch, energy_diff_mixed,
     gradient_step, gradient_df, energy_df, state_save, state_load, galerkin_set, galerkin_apply, qp_pgs, qp_mprgp, autotune, tile_variant_set, tile_variant_get,
-    Batch,
+    Batch, get_fields, PF_FIELD_C_PREV, PF_FIELD_LOWER, PF_FIELD_UPPER, PF_FIELD_FIXED,
     PF_QP_CG, PF_QP_PAPER,
     PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENONFINITE, PF_ENOTCONV, PF_ETIMEOUT, PF_ESTATE, PF_EIO,
 )

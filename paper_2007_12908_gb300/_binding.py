@@ -39,7 +39,7 @@ EXPORTS = [
     "pf_state_save", "pf_state_load", "pf_galerkin_set", "pf_galerkin_apply", "pf_qp_pgs",
     "pf_qp_mprgp", "pf_autotune", "pf_tile_variant_set", "pf_tile_variant_get",
     "pf_batch_create", "pf_batch_destroy", "pf_batch_info", "pf_batch_hessvec", "pf_batch_energy",
-    "pf_batch_autotune", "pf_batch_variant_set",
+    "pf_batch_autotune", "pf_batch_variant_set", "pf_get_fields",
 ]
 
 
@@ -156,6 +156,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pf_batch_autotune": (i, [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int),
                                   C.POINTER(d)]),
         "pf_batch_variant_set": (i, [vp, i]),
+        "pf_get_fields": (i, [vp, i, i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -454,6 +455,19 @@ def get_c_prev(H: Hierarchy):
     import torch
     out = torch.empty(H.nodes(), dtype=torch.float64, device="cuda")
     _check(lib().pf_get_c_prev(H.handle, _dev(out, H.nodes())))
+    return out
+
+
+PF_FIELD_C_PREV, PF_FIELD_LOWER, PF_FIELD_UPPER, PF_FIELD_FIXED = 0, 1, 2, 3
+
+
+def get_fields(H: Hierarchy, level: int, which: int):
+    """A field the solver keeps for a level (pf_get_fields): c_prev (finest
+    level), the feasible set's lower / upper bounds, or the fixed-dof mask."""
+    import torch
+    n = H.nodes(level) if which == PF_FIELD_C_PREV else H.ndof(level)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    _check(lib().pf_get_fields(H.handle, level, which, _dev(out, n)))
     return out
 
 

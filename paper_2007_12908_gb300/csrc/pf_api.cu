@@ -354,6 +354,7 @@ pf_status pf_fractures_set(pf_hierarchy* h, int kind, int n, const double* rows,
     return PF_ECUDA;
   }
   h->have_fractures = true;
+  h->bounds_set = false;
   h->p_last = 0.0;
   return PF_OK;
 }
@@ -755,6 +756,35 @@ pf_status pf_get_c_prev(pf_hierarchy* h, double* out) {
                               cudaMemcpyDeviceToDevice, h->st),
               "get_c_prev");
   return PF_OK;
+}
+
+pf_status pf_get_fields(pf_hierarchy* h, int level, int which, double* out) {
+  if (!valid_level(h, level) || !out) return bad("get_fields: bad argument");
+  const Geom& g = h->geo[level];
+  const long long n = (long long)(h->dim + 1) * g.N;
+  switch (which) {
+    case PF_FIELD_C_PREV:
+      if (level != h->L - 1) return bad("get_fields: c_prev lives on the finest level");
+      PF_TRY_CUDA(cudaMemcpyAsync(out, h->c_prev, sizeof(double) * g.N, cudaMemcpyDeviceToDevice,
+                                  h->st),
+                  "get_fields");
+      return PF_OK;
+    case PF_FIELD_LOWER:
+    case PF_FIELD_UPPER:
+      if (!h->bounds_set) {
+        set_error("get_fields: no load step has set the feasible sets");
+        return PF_ESTATE;
+      }
+      PF_TRY_CUDA(cudaMemcpyAsync(out, which == PF_FIELD_LOWER ? h->lv[level].lb : h->lv[level].ub,
+                                  sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st),
+                  "get_fields");
+      return PF_OK;
+    case PF_FIELD_FIXED:
+      PF_TRY_CUDA(fixed_mask(g, out, h->st), "get_fields");
+      return PF_OK;
+    default:
+      return bad("get_fields: unknown field");
+  }
 }
 
 pf_status pf_probe_fma(int prec, double* flops) {

@@ -65,6 +65,7 @@ struct pf_hierarchy {
   std::vector<CgGraph> cg_graphs;
   bool cg_graph_ok = true;  // false once the driver refused to build one
   bool have_fractures = false;
+  bool bounds_set = false;  // lv[].lb / ub hold a load step's feasible sets
   std::vector<pf::LevelBuf> lv;
   std::vector<void*> allocations;
 };
@@ -84,4 +85,7 @@ cudaError_t ensure_stencil(pf_hierarchy* H, int l);
 // the finest level's FP32 lag x (R G I chain, see pf_galerkin.cu).
 cudaError_t ensure_galerkin(pf_hierarchy* H, int l);
 cudaError_t galerkin_build(pf_hierarchy* H, const float* x_fine, cudaStream_t st);
+// out[i] = 1 for the dofs the clamped boundary fixes (u on the boundary), 0
+// elsewhere; (dim + 1) g.N values.
+cudaError_t fixed_mask(const Geom& g, double* out, cudaStream_t st);
 }  // namespace pf

@@ -386,6 +386,22 @@ __device__ __forceinline__ bool on_boundary(const Geom& g, long long i) {
   return b;
 }
 
+__global__ void k_fixed_mask(Geom g, double* __restrict__ out) {
+  const long long n = (long long)(g.dim + 1) * g.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int f = int(i / g.N);
+    out[i] = (f < g.dim && on_boundary(g, i - f * g.N)) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t fixed_mask(const Geom& g, double* out, cudaStream_t st) {
+  const long long n = (long long)(g.dim + 1) * g.N;
+  const int blocks = int(std::min<long long>((n + 255) / 256, 4LL * 1216));
+  k_fixed_mask<<<blocks, 256, 0, st>>>(g, out);
+  return cudaGetLastError();
+}
+
 __device__ __forceinline__ double clampv(double x, double lo, double hi) {
   return fmin(fmax(x, lo), hi);
 }
@@ -1602,6 +1618,7 @@ struct Solver {
         ub[i] = u;
         x[i] = fmin(fmax(x[i], l), u);
       });
+      H->bounds_set = true;
     }
     double pg0;
     if (g_at_t3 && step_update(L - 1)) {

@@ -160,6 +160,7 @@ pf_status pf_state_load(pf_hierarchy* H, double* x_dev, const char* path) {
   H->p = hd.p;
   for (auto& m : H->mat) m.p = hd.p;
   H->p_last = hd.p_last;
+  H->bounds_set = false;
   H->have_fractures = true;
   return PF_OK;
 }

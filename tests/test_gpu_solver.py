@@ -282,3 +282,48 @@ def test_3d_65_load_step_fields_match_oracle(pf, precision):
         want = np.asarray(gold["fields"][f])
         assert np.max(np.abs(got - want)) <= FIELD_TOL * gold["field_max"][f], (f, np.max(np.abs(got - want)))
     H.close()
+
+
+def test_get_fields(pf):
+    """pf_get_fields: c_prev against the oracle's rasterisation, the fixed-dof
+    mask against the boundary, the finest feasible set of eq. (space_pf)
+    after a load step, and the coarse feasible set's shape (lower <= upper,
+    boundary displacement corrections fixed)."""
+    import torch
+    H, Ho = pair(2, (9, 9), 2, 1 / 8, p=1e-3)
+    g = Ho.fine
+    N = g.N
+    x = torch.zeros(H.ndof(), dtype=torch.float64, device="cuda")
+    rows = PI.centred_crack_2d(0.2)
+    pf.fractures_set(H, pf.PF_LINE2D, rows, g.h, x)
+    c_or = O.rasterize(g, O.LINE2D, rows, g.h)
+    assert np.array_equal(host(pf.get_fields(H, 1, pf.PF_FIELD_C_PREV)), c_or)
+    with pytest.raises(pf.PfError) as e:
+        pf.get_fields(H, 1, pf.PF_FIELD_LOWER)
+    assert e.value.status == pf.PF_ESTATE
+    with pytest.raises(pf.PfError):
+        pf.get_fields(H, 0, pf.PF_FIELD_C_PREV)
+    ix, iy = np.meshgrid(np.arange(g.n[0]), np.arange(g.n[1]), indexing="xy")
+    bnd = ((ix == 0) | (iy == 0) | (ix == g.n[0] - 1) | (iy == g.n[1] - 1)).ravel()
+    fixed = host(pf.get_fields(H, 1, pf.PF_FIELD_FIXED))
+    assert np.array_equal(fixed, np.concatenate([bnd, bnd, np.zeros(N, bool)]).astype(float))
+    st = pf.rmtr_load_step(H, x, pf.default_params())
+    assert st["converged"]
+    cp = host(pf.get_fields(H, 1, pf.PF_FIELD_C_PREV))
+    lo, up = host(pf.get_fields(H, 1, pf.PF_FIELD_LOWER)), host(pf.get_fields(H, 1, pf.PF_FIELD_UPPER))
+    assert np.array_equal(lo[2 * N:], cp) and np.all(up[2 * N:] == 1.0)
+    for f in range(2):
+        lf, uf = lo[f * N:(f + 1) * N], up[f * N:(f + 1) * N]
+        assert np.all(lf[bnd] == 0.0) and np.all(uf[bnd] == 0.0)
+        assert np.all(np.isneginf(lf[~bnd])) and np.all(np.isposinf(uf[~bnd]))
+    gc = Ho.grids[0]
+    lc, uc = host(pf.get_fields(H, 0, pf.PF_FIELD_LOWER)), host(pf.get_fields(H, 0, pf.PF_FIELD_UPPER))
+    assert np.all(lc <= uc)
+    jx, jy = np.meshgrid(np.arange(gc.n[0]), np.arange(gc.n[1]), indexing="xy")
+    bc_ = ((jx == 0) | (jy == 0) | (jx == gc.n[0] - 1) | (jy == gc.n[1] - 1)).ravel()
+    for f in range(2):
+        assert np.array_equal(lc[f * gc.N:(f + 1) * gc.N][bc_], uc[f * gc.N:(f + 1) * gc.N][bc_])
+    pf.fractures_set(H, pf.PF_LINE2D, rows, g.h, x)
+    with pytest.raises(pf.PfError):
+        pf.get_fields(H, 1, pf.PF_FIELD_UPPER)
+    H.close()
