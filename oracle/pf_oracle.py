@@ -16,8 +16,11 @@ Everything here is plain float64 numpy written from the paper:
   Algorithm 2, Convergence_control of Algorithm 3, the ratios of
   eq. (rho_tr) and eq. (rho_ml), and Hessian lagging (Sec. 4.2.1);
 * the trust-region subproblem eq. (model_qp), solved by a projected
-  truncated CG (the paper uses MPRGP / HJPGS; the reading is recorded in the
-  design notes).
+  truncated CG (the default reading), or by the paper's own QP solvers
+  (Sec. 4.2.2): multicolour symmetric projected Gauss-Seidel smoothing and
+  MPRGP on the coarsest level;
+* the trust-region gate of a proposed iterate (eq. (rho_tr) with
+  Algorithm 3's acceptance), used by the learned initial iterate.
 
 Readings where the paper is silent or inconsistent (all listed in the design
 notes): the sign of the pressure term (+p g(c) div u, derived from eq.
@@ -30,13 +33,28 @@ Layout: a state vector x holds (d+1) planes [u_x, u_y, (u_z), c], each of
 N = prod(n) nodal values in lexicographic order with x fastest.
 Level index 0 is the coarsest level (the paper's l = 1).
 
-Parity status: energy, gradient and hessvec are pinned by the patch test,
-exact 5-point finite differences, symmetry and an independently assembled
-dense Hessian; the Jacobi diagonal by that dense Hessian's diagonal;
-Convergence_control by a hand-written table of Algorithm 3's cases;
-transfers by linear reproduction and adjointness; the solver by the 1D
-closed-form phase-field profile, Sneddon's opening and the invariants.  The level model's choice of f~^l beyond "the same functional on
-the coarse grid" is "parity unpinned" apart from its coherence identities.
+Parity status:
+* energy, gradient and hessvec: the patch test, exact 5-point finite
+  differences, symmetry and an independently assembled dense Hessian; the
+  exact quartic energy difference against the polynomial it must be;
+* the Jacobi diagonal: that dense Hessian's diagonal;
+* Convergence_control: a hand-written table of Algorithm 3's cases;
+* transfers: linear reproduction, adjointness and the coarse feasible set's
+  defining property;
+* rasterisation: lattice-point counts of discs and plates, the centred
+  crack's three rows, the paper's printed dof counts for the grids;
+* the subproblem: 1D and separable closed forms, the bent Cauchy path, the
+  radius cap; PGS and MPRGP: the exact one-sweep diagonal case, the KKT
+  point, the 1D closed form;
+* the gate: the ratio from the exact quartic within the cancellation bound;
+* the solver: the 1D closed-form phase-field profile, Sneddon's opening and
+  the invariants, and the onset of propagation at the Griffith pressure;
+* planted mistakes (a sign, a dropped pressure term, a model sign, the
+  projection, the diagonal, swapped radius factors or thresholds, the gate's
+  sign, an unprojected Gauss-Seidel step, MPRGP's gradient sign) each fail a
+  named test.
+The level model's choice of f~^l beyond "the same functional on the coarse
+grid" is "parity unpinned" apart from its coherence identities.
 """
 from __future__ import annotations
 
