@@ -204,6 +204,36 @@ def test_batched_hessvec_variants_bitwise_and_pressure():
         t[0].close()
 
 
+def test_batched_hessvec_strip_edges():
+    """Grid widths around the 63-column strips and the 32-lane halves
+    (62 .. 65, 94 .. 96, 126 .. 128 nodes, two to four rows) in one launch,
+    each against the oracle."""
+    torch = require_cuda()
+    import paper_2007_12908_gb300 as pf
+    from oracle import pf_oracle as O
+    from tests.gpu_common import dev, pair, relinf
+    widths = [62, 63, 64, 65, 94, 95, 96, 126, 127, 128]
+    inst = []
+    for k, w in enumerate(widths):
+        H, Ho = pair(2, (w, 2 + k % 3), 1, 1 / (w - 1), p=3e-3)
+        g = Ho.fine
+        x = PI.random_state(800 + k, 2, g.N, u_scale=1e-3, c_hi=1.0)
+        v = PI.random_direction(900 + k, x.size)
+        inst.append((H, Ho, x, v))
+    B = pf.Batch([t[0] for t in inst])
+    vhv = torch.empty(len(inst), dtype=torch.float64, device="cuda")
+    ys = B.hessvec([dev(t[2], torch.float32) for t in inst], [dev(t[3], torch.float32) for t in inst],
+                   vhv=vhv)
+    d = host(vhv)
+    for k, ((H, Ho, x, v), y) in enumerate(zip(inst, ys)):
+        ho = O.hessvec(Ho.fine, Ho.prm, x, v)
+        assert relinf(host(y), ho) <= 2e-5, (widths[k], relinf(host(y), ho))
+        assert abs(d[k] - float(v @ ho)) <= 2e-5 * float(np.sum(np.abs(v) * np.abs(ho))), widths[k]
+    B.close()
+    for t in inst:
+        t[0].close()
+
+
 def test_batched_energy_matches_oracle():
     torch = require_cuda()
     import paper_2007_12908_gb300 as pf
