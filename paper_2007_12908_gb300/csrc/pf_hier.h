@@ -63,7 +63,7 @@ struct pf_hierarchy {
     int nodes = 0;                // kernel launches per iteration of the body
   };
   std::vector<CgGraph> cg_graphs;
-  bool cg_graph_ok = true;  // false once the driver refused to build one
+  bool cg_graph_ok = true;  // false once the CUDA driver refused to build one
   bool have_fractures = false;
   bool bounds_set = false;  // lv[].lb / ub hold a load step's feasible sets
   std::vector<pf::LevelBuf> lv;

@@ -862,7 +862,7 @@ struct Solver {
   // The CG loop of level l as an executable graph: a while node whose body
   // is cg_iter and k_cg_cond.  Built on first use and rebuilt when the
   // pressure (a kernel argument of the FP32 Hessian) or the preconditioning
-  // flag changes; a level's subproblem vectors sit at fixed addresses.  Null where the driver cannot build it (the caller then
+  // flag changes; a level's subproblem vectors sit at fixed addresses.  Null where the CUDA driver cannot build it (the caller then
   // drives the loop from the host).
   template <class V>
   cudaGraphExec_t cg_graph(int l, V* p, V* q, const V* ga, const V* gb, const V* mi, V* w, V* r,
