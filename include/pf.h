@@ -431,14 +431,15 @@ pf_status pf_energy_noalloc(int dim, const int n[3], double h, double E, double 
 /* Tile autotuner (no counterpart in the paper): times the FP32 Hessian
  * product of every level of h on each of its tile variants (3D: 1
  * element-owned 8^3 element tiles, 2 owner-computes 8^3 node tiles, 3
- * owner-computes 4^3; 2D: 0 32x8, 1 16x8, 2 64x4, 3 32x4 node tiles) with
+ * owner-computes 4^3; 2D: 0 32x8, 1 16x8, 2 64x4, 3 32x4 node tiles, 4
+ * strips of 63 node columns marched one element row at a time) with
  * CUDA events on h's stream (one warm-up and five timed launches each on the
  * level's own buffers), and keeps the fastest for the level's FP32
  * products from then on, in the solver and in pf_hessvec.  The variants
  * compute the same product with different summation orders (results agree
  * to FP32 rounding; each is deterministic).  variant_out (n_levels ints)
- * and us_out (4 n_levels doubles, microseconds per product, -1 where a
- * variant does not apply) may be NULL.  Rebuilds the hierarchy's CUDA
+ * and us_out (5 n_levels doubles, microseconds per product of variants
+ * 0 .. 4, -1 where a variant does not apply) may be NULL.  Rebuilds the hierarchy's CUDA
  * graphs on next use.  Call between load steps; synchronises the stream. */
 pf_status pf_autotune(pf_hierarchy* h, int* variant_out, double* us_out);
 /* The tile variant of one level (0 = the default rule), e.g. to reuse a

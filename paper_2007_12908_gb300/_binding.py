@@ -491,9 +491,9 @@ def autotune(H: Hierarchy):
     keeps the fastest; returns (variants per level, microseconds per
     (level, variant), -1 where a variant does not apply)."""
     var = (C.c_int * H.n_levels)()
-    us = (C.c_double * (4 * H.n_levels))()
+    us = (C.c_double * (5 * H.n_levels))()
     _check(lib().pf_autotune(H.handle, var, us))
-    return list(var), [list(us[4 * l:4 * l + 4]) for l in range(H.n_levels)]
+    return list(var), [list(us[5 * l:5 * l + 5]) for l in range(H.n_levels)]
 
 
 def tile_variant_set(H: Hierarchy, level: int, variant: int):

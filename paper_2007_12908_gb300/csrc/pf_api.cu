@@ -486,8 +486,8 @@ pf_status pf_hessvec_lag_set(pf_hierarchy* h, int level, const void* x, int prec
 }
 
 pf_status pf_tile_variant_set(pf_hierarchy* h, int level, int variant) {
-  if (!valid_level(h, level) || variant < 0 || variant > 3)
-    return bad("tile_variant_set: bad level or variant (0 .. 3)");
+  if (!valid_level(h, level) || variant < 0 || variant > (h->dim == 2 ? 4 : 3))
+    return bad("tile_variant_set: bad level or variant (0 .. 3, 2D 0 .. 4)");
   h->geo[level].hv_variant = variant;
   for (auto& G : h->cg_graphs) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -503,6 +503,8 @@ pf_status pf_tile_variant_get(const pf_hierarchy* h, int level, int* variant) {
   return PF_OK;
 }
 
+constexpr int kTileVariants = 5;  // slots per level in pf_autotune's us_out
+
 pf_status pf_autotune(pf_hierarchy* h, int* variant_out, double* us_out) {
   if (!h) return bad("autotune: null handle");
   cudaEvent_t e0, e1;
@@ -515,11 +517,12 @@ pf_status pf_autotune(pf_hierarchy* h, int* variant_out, double* us_out) {
     float* v = reinterpret_cast<float*>(B.p);
     float* y = reinterpret_cast<float*>(B.q);
     cudaError_t e = cudaMemsetAsync(v, 0, sizeof(float) * B.n, h->st);
-    const int first = h->dim == 3 ? 1 : 0;
+    const int first = h->dim == 3 ? 1 : 0, last = h->dim == 3 ? 3 : 4;
     int best = 0;
     double best_us = 1e300;
-    for (int var = 0; var < 4 && e == cudaSuccess; ++var) {
-      if (us_out) us_out[4 * l + var] = -1.0;
+    for (int var = 0; var < kTileVariants && e == cudaSuccess; ++var) {
+      if (us_out) us_out[kTileVariants * l + var] = -1.0;
+      if (var > last) continue;
       if (var < first) continue;
       g.hv_variant = var;
       e = elem_hessvec(g, h->mat[l], B.xlag32, v, y, 1, h->st, nullptr, h->etile_part, h->p_dev);
@@ -531,7 +534,7 @@ pf_status pf_autotune(pf_hierarchy* h, int* variant_out, double* us_out) {
       float ms = 0.f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       const double us = 1e3 * double(ms) / 5.0;
-      if (us_out) us_out[4 * l + var] = us;
+      if (us_out) us_out[kTileVariants * l + var] = us;
       if (us < best_us) {
         best_us = us;
         best = var;

@@ -426,6 +426,28 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// One instance's FP32 Hessian product on the same strips (the 2D product's
+// "marching strips" tile variant): the instance travels as a kernel
+// argument; skip non-null and set makes the launch a no-op (a CG run that
+// has stopped).
+__global__ void __launch_bounds__(128, 3)
+    k_hess2_march(const BInst I, const BVec V, long long T, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  long long s = w * T / W;
+  const long long s_end = (w + 1) * T / W;
+  const int n1 = I.g.n[1];
+  while (s < s_end) {
+    const int strip = int(s / n1), r0 = int(s % n1);
+    const long long left = s_end - s;
+    const int rows = left < (long long)(n1 - r0) ? int(left) : n1 - r0;
+    hess2_strip<false>(I, V, strip, r0, rows, lane, nullptr);
+    s += rows;
+  }
+}
+
 }  // namespace
 }  // namespace pf
 
@@ -547,6 +569,32 @@ pf_status launch_hess(pf_batch* b, int bps, bool dot) {
 }
 
 }  // namespace
+
+namespace pf {
+cudaError_t hess2_march(const Geom& g, const Mat<double>& m, const float* x, const float* v,
+                        float* y, const int* skip, cudaStream_t st) {
+  if (g.dim != 2 || 3 * g.N >= (1LL << 31)) return cudaErrorInvalidValue;
+  BInst I;
+  std::memset(&I, 0, sizeof(I));
+  I.g = g;
+  I.md = m;
+  I.strips = (g.n[0] + kStripCols - 1) / kStripCols;
+  set_consts(I, m);
+  const long long T = (long long)I.strips * g.n[1];
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 1;
+    return n;
+  }();
+  // every warp at least 8 rows (one halo row each), at most 3 blocks per SM
+  const long long warps = std::min<long long>(3LL * 4 * sms, (T + 7) / 8);
+  const int blocks = int(std::max<long long>(1, (warps + 3) / 4));
+  k_hess2_march<<<blocks, kHessThreads, 0, st>>>(I, BVec{x, v, y}, T, skip);
+  return cudaGetLastError();
+}
+}  // namespace pf
 
 extern "C" {
 

@@ -17,7 +17,7 @@ struct Geom {
   // tile variant of the FP32 Hessian products on this grid (0: the default
   // rule; set per level by the autotuner, pf_autotune): 3D 1 element-owned
   // 8^3 tiles, 2 owner-computes 8^3, 3 owner-computes 4^3; 2D 1 16x8,
-  // 2 64x4, 3 32x4 node tiles (0: 32x8)
+  // 2 64x4, 3 32x4 node tiles (0: 32x8), 4 marching strips
   int hv_variant;
 };
 
@@ -191,6 +191,13 @@ cudaError_t galerkin_rap(const Geom& gc, const Geom& gf, const float* Kf, float*
 cudaError_t galerkin_assemble(const Geom& g, const float* K, float* S, cudaStream_t st);
 cudaError_t galerkin_apply(const Geom& g, const float* S, const void* v, void* y, int prec,
                            cudaStream_t st, const int* skip = nullptr);
+
+// The 2D FP32 Hessian product on 63-column strips marched one element row
+// at a time (pf_batch.cu), one instance: y = H(x) v, FP32 planes.  The
+// node sums are in a fixed order, so the result does not depend on the
+// launch shape.  skip as for the other element kernels.
+cudaError_t hess2_march(const Geom& g, const Mat<double>& m, const float* x, const float* v,
+                        float* y, const int* skip, cudaStream_t st);
 
 // Fracture band rasterisation into the c plane (FP64) of x and c_prev.
 // rows: device array of precomputed shape rows of kRasterRow doubles (see

@@ -446,6 +446,9 @@ static cudaError_t launch_hess2_f32(const Geom& g, const Mat<double>& m, const v
     case 1: return launch_scatter<2, float, float, OP_HESS, float, Tile2_16x8>(g, m, x, v, y, skip, st);
     case 2: return launch_scatter<2, float, float, OP_HESS, float, Tile2_64x4>(g, m, x, v, y, skip, st);
     case 3: return launch_scatter<2, float, float, OP_HESS, float, Tile2_32x4>(g, m, x, v, y, skip, st);
+    case 4:
+      return hess2_march(g, m, static_cast<const float*>(x), static_cast<const float*>(v),
+                         static_cast<float*>(y), skip, st);
     default: return launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st);
   }
 }

@@ -57,7 +57,7 @@ def test_every_tile_variant_matches_oracle(dim, nc, L, hc):
     v = PI.random_direction(92, x.size)
     ho = O.hessvec(g, Ho.prm, x, v)
     xd, vd = dev(x, torch.float32), dev(v, torch.float32)
-    for var in ((1, 2, 3) if dim == 3 else (0, 1, 2, 3)):
+    for var in ((1, 2, 3) if dim == 3 else (0, 1, 2, 3, 4)):
         pf.tile_variant_set(H, L - 1, var)
         assert pf.tile_variant_get(H, L - 1) == var
         a = pf.hessvec(H, L - 1, xd, vd)
