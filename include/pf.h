@@ -442,7 +442,10 @@ pf_status pf_energy_noalloc(int dim, const int n[3], double h, double E, double 
  * 0 .. 4, -1 where a variant does not apply) may be NULL.  Rebuilds the hierarchy's CUDA
  * graphs on next use.  Call between load steps; synchronises the stream. */
 pf_status pf_autotune(pf_hierarchy* h, int* variant_out, double* us_out);
-/* The tile variant of one level (0 = the default rule), e.g. to reuse a
+/* The tile variant of one level (0 = the default rule: 3D element-owned
+ * tiles on grids of at least 304 8^3 tiles, else owner-computes 8^3 or 4^3
+ * node tiles; 2D marching strips on grids of at least 200,000 nodes, else
+ * 32x8 node tiles), e.g. to reuse a
  * choice of pf_autotune in later runs so that they repeat bit for bit.
  * set also rebuilds the hierarchy's CUDA graphs on next use. */
 pf_status pf_tile_variant_set(pf_hierarchy* h, int level, int variant);

@@ -17,7 +17,8 @@ struct Geom {
   // tile variant of the FP32 Hessian products on this grid (0: the default
   // rule; set per level by the autotuner, pf_autotune): 3D 1 element-owned
   // 8^3 tiles, 2 owner-computes 8^3, 3 owner-computes 4^3; 2D 1 16x8,
-  // 2 64x4, 3 32x4 node tiles (0: 32x8), 4 marching strips
+  // 2 64x4, 3 32x4 node tiles, 4 marching strips (0: strips on grids of
+  // at least 200,000 nodes, else 32x8)
   int hv_variant;
 };
 

@@ -449,7 +449,14 @@ static cudaError_t launch_hess2_f32(const Geom& g, const Mat<double>& m, const v
     case 4:
       return hess2_march(g, m, static_cast<const float*>(x), static_cast<const float*>(v),
                          static_cast<float*>(y), skip, st);
-    default: return launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st);
+    default:
+      // the default rule: marching strips on grids of at least 200,000
+      // nodes (1.4x the node tiles at 1025^2), 32 x 8 node tiles below
+      // (the strips' row-by-row march is latency-bound on small grids)
+      if (g.N >= 200000)
+        return hess2_march(g, m, static_cast<const float*>(x), static_cast<const float*>(v),
+                           static_cast<float*>(y), skip, st);
+      return launch_scatter<2, float, float, OP_HESS>(g, m, x, v, y, skip, st);
   }
 }
 
