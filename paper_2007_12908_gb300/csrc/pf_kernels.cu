@@ -562,9 +562,10 @@ __global__ void __launch_bounds__(256, 2)
 
 // Sum at node n of the blocks of the up to 8 element tiles that contain
 // it, in ascending tile order (z, y, x).  Along each axis a node lies in
-// one tile, or in two where it sits on a tile boundary; all candidate loads
-// are issued before the first add (absent tiles add an exact zero), so a
-// node costs one memory latency, not one per tile.
+// one tile, or in two where it sits on a tile boundary.  Only the tiles that
+// hold the node are loaded and added; the loads of each z layer of
+// candidates are issued together, so a node costs one memory latency (two
+// on a z boundary), not one per tile.
 __device__ __forceinline__ float4 etile_node_sum(const Geom& g, const float4* __restrict__ part,
                                                  long long n, int tx, int ty, int tz) {
   constexpr int T = 8, NN = T + 1, NH = NN * NN * NN;
@@ -586,23 +587,38 @@ __device__ __forceinline__ float4 etile_node_sum(const Geom& g, const float4* __
   const int z0 = k >= T ? (k - 1) / T : 0;
   const bool hx = min(i / T, tx - 1) > x0, hy = min(j / T, ty - 1) > y0;
   const bool hz = min(k / T, tz - 1) > z0;
-  float4 c[8];
+  // the node's entry in tile (x0, y0, z0); the next tile along an axis
+  // holds it at a constant offset (one tile on, T nodes back)
+  const long long base = (x0 + (long long)tx * (y0 + (long long)ty * z0)) * NH +
+                         ((i - T * x0) + NN * ((j - T * y0) + NN * (k - T * z0)));
+  const long long dX = NH - T, dY = (long long)tx * NH - T * NN;
+  const long long dZ = (long long)tx * ty * NH - T * NN * NN;
+  // candidates q = dx + 2 dy + 4 dz, added in q order; the loads of a z
+  // layer (q = 0..3, then 4..7 where the node is on a z boundary) are all
+  // issued before its first add
+  float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
-    const bool ok = (!dx || hx) && (!dy || hy) && (!dz || hz);
-    const int bx = x0 + dx, by = y0 + dy, bz = z0 + dz;
-    const long long tile = bx + (long long)tx * (by + (long long)ty * bz);
-    const int loc = (i - T * bx) + NN * ((j - T * by) + NN * (k - T * bz));
-    c[q] = ok ? part[tile * NH + loc] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  float4 sum = c[0];
+  for (int dz = 0; dz < 2; ++dz) {
+    if (dz && !hz) break;
+    const long long b = base + dz * dZ;
+    float4 c[4];
 #pragma unroll
-  for (int q = 1; q < 8; ++q) {
-    sum.x += c[q].x;
-    sum.y += c[q].y;
-    sum.z += c[q].z;
-    sum.w += c[q].w;
+    for (int q = 0; q < 4; ++q) {
+      const int dx = q & 1, dy = q >> 1;
+      if ((!dx || hx) && (!dy || hy)) c[q] = part[b + dx * dX + dy * dY];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int dx = q & 1, dy = q >> 1;
+      if (dz == 0 && q == 0) {
+        sum = c[0];
+      } else if ((!dx || hx) && (!dy || hy)) {
+        sum.x += c[q].x;
+        sum.y += c[q].y;
+        sum.z += c[q].z;
+        sum.w += c[q].w;
+      }
+    }
   }
   return sum;
 }
