@@ -566,9 +566,22 @@ __global__ void __launch_bounds__(256, 2)
 // hold the node are loaded and added; the loads of each z layer of
 // candidates are issued together, so a node costs one memory latency (two
 // on a z boundary), not one per tile.
-__device__ __forceinline__ float4 etile_node_sum(const float4* __restrict__ part, int i, int j,
-                                                 int k, int tx, int ty, int tz) {
+__device__ __forceinline__ float4 etile_node_sum(const Geom& g, const float4* __restrict__ part,
+                                                 long long n, int tx, int ty, int tz) {
   constexpr int T = 8, NN = T + 1, NH = NN * NN * NN;
+  int i, j, k;
+  if (g.N <= 0xffffffffLL) {  // 32-bit index arithmetic where it suffices
+    unsigned u = unsigned(n);
+    i = int(u % unsigned(g.n[0]));
+    u /= unsigned(g.n[0]);
+    j = int(u % unsigned(g.n[1]));
+    k = int(u / unsigned(g.n[1]));
+  } else {
+    i = int(n % g.n[0]);
+    const long long r = n / g.n[0];
+    j = int(r % g.n[1]);
+    k = int(r / g.n[1]);
+  }
   // tiles t with 8t <= coordinate <= 8t + 8: t0, and t0 + 1 if present
   const int x0 = i >= T ? (i - 1) / T : 0, y0 = j >= T ? (j - 1) / T : 0;
   const int z0 = k >= T ? (k - 1) / T : 0;
@@ -610,40 +623,6 @@ __device__ __forceinline__ float4 etile_node_sum(const float4* __restrict__ part
   return sum;
 }
 
-// A thread's walk over the nodes n0, n0 + S, n0 + 2S, ... of a grid-stride
-// loop with the grid coordinates (i, j, k) carried along: the stride's own
-// coordinates are added with carries, so no node needs a division.
-struct NodeWalk {
-  long long n;
-  int i, j, k, si, sj, sk, n0, n1;
-  __device__ NodeWalk(const Geom& g, long long start, long long stride) : n(start) {
-    n0 = g.n[0];
-    n1 = g.n[1];
-    i = int(start % n0);
-    j = int((start / n0) % n1);
-    k = int(start / ((long long)n0 * n1));
-    si = int(stride % n0);
-    sj = int((stride / n0) % n1);
-    sk = int(stride / ((long long)n0 * n1));
-  }
-  __device__ __forceinline__ void next(long long stride) {
-    n += stride;
-    i += si;
-    int cy = 0;
-    if (i >= n0) {
-      i -= n0;
-      cy = 1;
-    }
-    j += sj + cy;
-    cy = 0;
-    if (j >= n1) {
-      j -= n1;
-      cy = 1;
-    }
-    k += sk + cy;
-  }
-};
-
 // Pass 2: each node sums the blocks of the tiles that contain it and
 // writes y.
 template <class TV>
@@ -653,10 +632,10 @@ __global__ void __launch_bounds__(256) k_etile_gather3(Geom g, const float4* __r
   if (skip && *skip) return;
   constexpr int T = 8;
   const int tx = (g.ne[0] + T - 1) / T, ty = (g.ne[1] + T - 1) / T, tz = (g.ne[2] + T - 1) / T;
-  const long long N = g.N, S = (long long)gridDim.x * blockDim.x;
-  for (NodeWalk w(g, blockIdx.x * (long long)blockDim.x + threadIdx.x, S); w.n < N; w.next(S)) {
-    const long long n = w.n;
-    const float4 sum = etile_node_sum(part, w.i, w.j, w.k, tx, ty, tz);
+  const long long N = g.N;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const float4 sum = etile_node_sum(g, part, n, tx, ty, tz);
     y[n] = TV(sum.x);
     y[N + n] = TV(sum.y);
     y[2 * N + n] = TV(sum.z);
@@ -682,9 +661,8 @@ __global__ void __launch_bounds__(256, 4) k_etile_gather3_dot(Geom g,
   const long long N = g.N;
   const float be = dir.r ? float(c->beta) : 0.f;
   float pq = 0.f;
-  const long long S = (long long)gridDim.x * blockDim.x;
-  for (NodeWalk w(g, blockIdx.x * (long long)blockDim.x + threadIdx.x, S); w.n < N; w.next(S)) {
-    const long long n = w.n;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
     float p0 = p[n], p1 = p[N + n], p2 = p[2 * N + n], p3 = p[3 * N + n];
     if (dir.r) {
       const float* r = dir.r;
@@ -700,7 +678,7 @@ __global__ void __launch_bounds__(256, 4) k_etile_gather3_dot(Geom g,
       p[2 * N + n] = p2;
       p[3 * N + n] = p3;
     }
-    const float4 sum = etile_node_sum(part, w.i, w.j, w.k, tx, ty, tz);
+    const float4 sum = etile_node_sum(g, part, n, tx, ty, tz);
     y[n] = sum.x;
     y[N + n] = sum.y;
     y[2 * N + n] = sum.z;
