@@ -487,15 +487,16 @@ cudaError_t elem_gradient(const Geom& g, const Mat<double>& m, const void* x, vo
 // to part (one block of 729 float4 per tile).
 // With dir.r set (FP32 CG), v is the previous direction and the staged
 // operand is M^-1 r + beta v, beta = *beta.
+constexpr int kEtileThreads = 128;  // 4 CTAs per SM at 128 registers
 template <class TV>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kEtileThreads, 512 / kEtileThreads)
     k_hess_etile3(Geom g, Mat<float> m, const float* __restrict__ x, const TV* __restrict__ v,
                   float4* __restrict__ part, const int* __restrict__ skip,
                   const float* __restrict__ p_dev, CgDirIn dir, const double* beta) {
   if (skip && *skip) return;
   if (p_dev) m.p = *p_dev;
   const float be = dir.r ? float(*beta) : 0.f;
-  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN, NT = 256;
+  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN, NT = kEtileThreads;
   __shared__ float4 xs[NH], vs[NH], acc[NH];
   const int ox = blockIdx.x * T, oy = blockIdx.y * T, oz = blockIdx.z * T;
   const int nx0 = g.n[0], ny0 = g.n[1], nz0 = g.n[2];
@@ -720,7 +721,7 @@ cudaError_t elem_hessvec32_dot(const Geom& g, const Mat<double>& m, const float*
   if (!hessvec32_dot_fused(g, part)) return cudaErrorNotSupported;
   const dim3 be((g.ne[0] + 7) / 8, (g.ne[1] + 7) / 8, (g.ne[2] + 7) / 8);
   float4* pp = static_cast<float4*>(part);
-  k_hess_etile3<float><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, p, pp, &c->done, p_dev, dir,
+  k_hess_etile3<float><<<be, kEtileThreads, 0, st>>>(g, cast_mat<float>(m), x, p, pp, &c->done, p_dev, dir,
                                            &c->beta);
   // kMaxBlocks = two waves of 4 blocks per SM
   const int nb = int(std::min<long long>((g.N + 255) / 256, kMaxBlocks));
@@ -738,7 +739,7 @@ static cudaError_t launch_hess_tile3(const Geom& g, const Mat<double>& m, const 
   if (etile_used(g, part)) {
     const dim3 be((g.ne[0] + 7) / 8, (g.ne[1] + 7) / 8, (g.ne[2] + 7) / 8);
     float4* pp = static_cast<float4*>(part);
-    k_hess_etile3<TV><<<be, 256, 0, st>>>(g, cast_mat<float>(m), x, v, pp, skip, p_dev,
+    k_hess_etile3<TV><<<be, kEtileThreads, 0, st>>>(g, cast_mat<float>(m), x, v, pp, skip, p_dev,
                                           CgDirIn{nullptr, nullptr}, nullptr);
     const int nb = int(std::min<long long>((g.N + 255) / 256, 8LL * 1216));
     k_etile_gather3<TV><<<nb, 256, 0, st>>>(g, pp, y, skip);
