@@ -72,7 +72,7 @@ METRIC = "RMTR s/load-step & hessvec GDoF/s: mixed+learned vs FP64 plain, same G
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # roofline kernels on this workload, from one ncu capture of
 # `bench.py --kernels-only`; to be re-captured whenever those kernels change.
-TRAFFIC_HESSVEC_FP32 = (68.725e6 + 18.661e6) + (47.787e6 + 0.276e6)  # element pass + gather
+TRAFFIC_HESSVEC_FP32 = (69.044e6 + 17.576e6) + (47.787e6 + 1.250e6)  # element pass + gather
 TRAFFIC_HESSVEC_FP64 = 7595.291e6 + 86.475e6
 UNIT = "s/load-step"
 # FP32 flops of one element of the 3D FP32 Hessian product (the paired-FMA
