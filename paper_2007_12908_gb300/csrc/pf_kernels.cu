@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(TS::THREADS, sizeof(TC) == 4 ? 2 : 1)
 // threads, one round) for grids too small to give every SM two 8^3 tiles.
 template <int T>
 struct HessTile {
-  static constexpr int THREADS = T == 8 ? 256 : 128;
+  static constexpr int THREADS = 128;  // four CTAs per SM at 128 registers (8^3 tiles)
 };
 
 // OP: OP_HESS (y = H(x) v, paired FP32 algebra) or OP_GDIFF (y += grad E(x)
@@ -341,7 +341,7 @@ struct HessTile {
 // p_dev: when non-null, the pressure is read from it (a CUDA graph that
 // captured the launch then follows pf_pressure_set).
 template <class TV, int T = 8, int OP = OP_HESS, class TX = float>
-__global__ void __launch_bounds__(HessTile<T>::THREADS, T == 8 ? 2 : 4)
+__global__ void __launch_bounds__(HessTile<T>::THREADS, 4)
     k_hess_tile3(Geom g, Mat<float> m, const TX* __restrict__ x, const TV* __restrict__ v,
                  TV* __restrict__ y, const int* __restrict__ skip,
                  const float* __restrict__ p_dev = nullptr) {
@@ -1403,13 +1403,13 @@ cudaError_t elem_energy_diff(const Geom& g, const Mat<double>& m, const void* x,
 // and s in shared memory as float4, and adds the FP64 g . s of the nodes the
 // tile owns ([o, o+8) per axis, the last tile of an axis also its end node).
 // out = (gx . s, a2, a3, a4), deterministic (fixed tile order per block).
-__global__ void __launch_bounds__(256) k_energy_diff_hi_tile3(Geom g, Mat<float> m,
+__global__ void __launch_bounds__(128, 4) k_energy_diff_hi_tile3(Geom g, Mat<float> m,
                                                               const double* __restrict__ x,
                                                               const double* __restrict__ s,
                                                               const double* __restrict__ gx,
                                                               double* partials, unsigned* counter,
                                                               double* out) {
-  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN, NT = 256;
+  constexpr int T = 8, NN = T + 1, NH = NN * NN * NN, NT = 128;
   __shared__ float4 xs[NH], ss[NH];
   const int tx = (g.ne[0] + T - 1) / T, ty = (g.ne[1] + T - 1) / T, tz = (g.ne[2] + T - 1) / T;
   const long long ntiles = (long long)tx * ty * tz;
@@ -1468,7 +1468,7 @@ cudaError_t elem_energy_diff_hi(const Geom& g, const Mat<double>& m, const doubl
   if (g.dim == 3) {
     const long long tiles = (long long)((g.ne[0] + 7) / 8) * ((g.ne[1] + 7) / 8) * ((g.ne[2] + 7) / 8);
     const int nt = int(std::min<long long>(tiles, kMaxBlocks));
-    k_energy_diff_hi_tile3<<<nt, 256, 0, st>>>(g, cast_mat<float>(m), x, sv, gx, s.partials,
+    k_energy_diff_hi_tile3<<<nt, 128, 0, st>>>(g, cast_mat<float>(m), x, sv, gx, s.partials,
                                                 s.counter, out);
   } else
     k_energy_diff_hi<2><<<nb, 256, 0, st>>>(g, cast_mat<float>(m), x, sv, gx, n, s.partials,
