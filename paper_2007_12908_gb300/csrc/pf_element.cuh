@@ -257,6 +257,7 @@ __device__ __forceinline__ T elem_energy(const T (*xe)[1 << D], const Mat<T>& m)
   for (int i = 0; i < D; ++i) interp<D, T>(xe[i], dummy, gu[i]);
   interp<D, T>(xe[D], cv, gc);
   T e = T(0);
+  const T ils = T(1) / m.ls;  // one division per element, not one per Gauss point
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     T G[D][D];
@@ -275,7 +276,7 @@ __device__ __forceinline__ T elem_energy(const T (*xe)[1 << D], const Mat<T>& m)
       const T t = gc[k][q] * m.inv_h;
       gc2 += t * t;
     }
-    e += g * psi + T(0.5) * m.Gc * (cv[q] * cv[q] / m.ls + m.ls * gc2) + m.p * g * s.tr;
+    e += g * psi + T(0.5) * m.Gc * (cv[q] * cv[q] * ils + m.ls * gc2) + m.p * g * s.tr;
   }
   return m.w * e;
 }
@@ -379,6 +380,7 @@ __device__ __forceinline__ void elem_gradient(const T (*xe)[1 << D], const Mat<T
   T su[D][D][NQ], s0[NQ], sc[D][NQ];
   const T omk = T(1) - m.k;
   const T kc = m.w * m.Gc * m.ls * m.inv_h * m.inv_h;
+  const T gcl = m.Gc / m.ls;  // one division per element, not one per Gauss point
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     T G[D][D];
@@ -405,7 +407,7 @@ __device__ __forceinline__ void elem_gradient(const T (*xe)[1 << D], const Mat<T
         su[k][i][q] = v;
       }
     }
-    s0[q] = m.w * (dg * (psi + m.p * e.tr) + m.Gc * cv[q] / m.ls);
+    s0[q] = m.w * (dg * (psi + m.p * e.tr) + gcl * cv[q]);
 #pragma unroll
     for (int k = 0; k < D; ++k) sc[k][q] = kc * gc[k][q];
   }
