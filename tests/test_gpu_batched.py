@@ -284,8 +284,8 @@ def test_batched_rejects_3d():
 def test_batched_draw_sampled_against_oracle():
     """Eight instances of the uneven batch draw (two of each size, their
     line networks) in one launch: sampled nodes of a 1025^2 and a 129^2
-    instance against the oracle, and v.Hv of every instance against the
-    FP64 dot of its product."""
+    instance and their energies against the oracle, and v.Hv of every
+    instance against the FP64 dot of its product."""
     torch = require_cuda()
     import paper_2007_12908_gb300 as pf
     from oracle import pf_oracle as O
@@ -317,11 +317,14 @@ def test_batched_draw_sampled_against_oracle():
     for k in range(len(Hs)):
         yk, vk = host(ys[k]), host(vs[k])
         assert abs(d[k] - float(vk @ yk)) <= 1e-6 * float(np.sum(np.abs(vk * yk))), k
+    E = B.energy([torch.from_numpy(x).cuda() for x in xs64])
     for k in (0, len(Hs) - 1):  # a 129^2 and a 1025^2 instance
         n = sizes[pick[k]]
         levels = int(round(np.log2((n - 1) / 16))) + 1
         Ho = O.Hierarchy(2, (17, 17), 1 / 16, levels, O.Params(E=1.0, nu=0.3, Gc=1.0, p=1e-3))
         g = Ho.fine
+        eo = O.energy(g, Ho.prm, xs64[k])
+        assert abs(E[k] - eo) <= 1e-10 * abs(eo), (n, E[k], eo)
         nodes = np.unique(np.concatenate([PI.rng(700 + k).choice(g.N, size=300, replace=False),
                                           [0, g.N - 1, g.n[0] - 1, g.N - g.n[0]]]))
         elems = g.elements_touching(nodes)
