@@ -104,6 +104,7 @@ def test_defaults_and_validation_on_host(lib):
     assert lib.pf_mesh_hierarchy_destroy(None) == B.PF_OK
     assert lib.pf_state_save(None, None, b"x") == B.PF_EINVAL
     assert lib.pf_state_load(None, None, None) == B.PF_EINVAL
+    assert lib.pf_get_fields(None, 0, B.PF_FIELD_C_PREV, None) == B.PF_EINVAL
 
 
 def test_batch_validation_on_host(lib):
