@@ -159,8 +159,7 @@ __global__ void __launch_bounds__(256) k_cg_init4(long long n4, const float* __r
                                                   const float* __restrict__ mi, bool pc,
                                                   float* __restrict__ r, float* __restrict__ p,
                                                   float* __restrict__ w, float* __restrict__ ga,
-                                                  float* __restrict__ gb,
-                                                  float* __restrict__ zo, double* partials,
+                                                  float* __restrict__ gb, double* partials,
                                                   unsigned* counter, double* out) {
   float rr = 0.f, rz = 0.f;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4;
@@ -184,7 +183,6 @@ __global__ void __launch_bounds__(256) k_cg_init4(long long n4, const float* __r
     CgInitOp::lane(l4.w, h4.w, s4.w, g4.w, hs4.w, m4.w, r4.w, p4.w, ga4.w, gb4.w, rr, rz);
     st4(r, j, r4);
     st4(p, j, p4);
-    if (zo) st4(zo, j, p4);  // z = M^-1 r, the start direction
     st4(w, j, z4);
     st4(ga, j, ga4);
     st4(gb, j, gb4);
@@ -207,17 +205,14 @@ __device__ __forceinline__ void cg_update_lane(float al, float a, float b, float
   rz += r * (m * r);
 }
 
-// With zo set, also zo = M^-1 r of the updated residual (the next
-// direction's first term, read by the element-owned product in place of r
-// and M^-1); groups with no free dof keep the zo of the CG start (0).
 __global__ void __launch_bounds__(256) k_cg_update4(long long n4, const float* __restrict__ ga,
                                                     const float* __restrict__ gb,
                                                     const float* __restrict__ q,
                                                     const float* __restrict__ p,
                                                     const float* __restrict__ mi, bool pc,
                                                     float* __restrict__ w, float* __restrict__ r,
-                                                    float* __restrict__ zo, CgCtrl* c,
-                                                    double* partials, unsigned* counter) {
+                                                    CgCtrl* c, double* partials,
+                                                    unsigned* counter) {
   if (c->done) return;
   const float al = float(c->alpha);
   float rr = 0.f, lv = 0.f, rz = 0.f;
@@ -254,16 +249,6 @@ __global__ void __launch_bounds__(256) k_cg_update4(long long n4, const float* _
     if (f1) {
       st4(w, j1, ww[1]);
       st4(r, j1, rv[1]);
-    }
-    if (zo) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (!(k ? f1 : f0)) continue;
-        const float4 m4 = mm[k], r4 = rv[k];
-        st4(zo, k ? j1 : j0,
-            make_float4(__fmul_rn(m4.x, r4.x), __fmul_rn(m4.y, r4.y), __fmul_rn(m4.z, r4.z),
-                        __fmul_rn(m4.w, r4.w)));
-      }
     }
   }
   double acc[3] = {double(rr), double(lv), double(rz)};
@@ -435,9 +420,6 @@ struct Solver {
   // (grad h at B.x - B.s: an accepted step not yet applied to the gradient)
   enum { G_NONE = 0, G_AT_X = 1, G_STEP = 2 };
   std::vector<int> gstate;
-  // z = M^-1 r of the running FP32 subproblem on an element-owned level
-  // (written by the CG start and update, read by the product), else null
-  float* zdir = nullptr;
 
   Solver(pf_hierarchy* h, const pf_rmtr_params& p, pf_rmtr_stats& s)
       : H(h), P(p), S(s), st(h->st), L(h->L), F(h->dim + 1), mixed(p.precision == PF_FP32),
@@ -796,15 +778,13 @@ struct Solver {
     const long long n4 = pad4(B.n) / 4;
     if (!gstored(l) && hessvec32_dot_fused(H->geo[l], H->etile_part)) {
       // the direction update of the previous iteration (beta = 0 after a
-      // restart, where p = M^-1 r already) is formed inside the product,
-      // from z = M^-1 r as the update stored it (zdir), else from r and M^-1
-      const CgDirIn dir = zdir ? CgDirIn{zdir, nullptr} : CgDirIn{r, pc ? mi : nullptr};
+      // restart, where p = M^-1 r already) is formed inside the product
       ck(elem_hessvec32_dot(H->geo[l], H->mat[l], B.xlag32, const_cast<float*>(p), q, c,
                             H->scratch.partials, H->scratch.counter, H->etile_part, H->p_dev,
-                            dir, s),
+                            CgDirIn{r, pc ? mi : nullptr}, s),
          "hessvec32_dot");
       k_cg_update4<<<resident_grid(k_cg_update4, n4), 256, 0, s>>>(
-          n4, ga, gb, q, p, mi, pc, w, r, zdir, c, H->scratch.partials, H->scratch.counter);
+          n4, ga, gb, q, p, mi, pc, w, r, c, H->scratch.partials, H->scratch.counter);
       ck(cudaGetLastError(), "cg_update");
       return 3;
     }
@@ -823,7 +803,7 @@ struct Solver {
       launches += 1 + (gstored(l) ? 1 : hessvec32_launches(H->geo[l], H->etile_part));
     }
     k_cg_update4<<<resident_grid(k_cg_update4, n4), 256, 0, s>>>(
-        n4, ga, gb, q, p, mi, pc, w, r, nullptr, c, H->scratch.partials, H->scratch.counter);
+        n4, ga, gb, q, p, mi, pc, w, r, c, H->scratch.partials, H->scratch.counter);
     ck(cudaGetLastError(), "cg_update");
     k_cg_dir4<<<resident_grid(k_cg_dir4, n4), 256, 0, s>>>(n4, ga, r, mi, pc, const_cast<float*>(p),
                                                             c);
@@ -1170,13 +1150,7 @@ struct Solver {
       ck(cudaGetLastError(), "zero_pad");
       S.launches += 1;
     }
-    // z = M^-1 r for the element-owned product's direction, in the free
-    // second half of the FP32 Jacobi buffer (3D: n = pad4(n))
-    zdir = (np == n && !gstored(l) && hessvec32_dot_fused(H->geo[l], H->etile_part))
-               ? half(B.minv, 1)
-               : nullptr;
     subproblem_t<float>(l, delta, cg_max, v);
-    zdir = nullptr;
     const float* s32 = v.s;
     double* s = B.s;
     map(n, [=] __device__(long long i) { s[i] = double(s32[i]); });
@@ -1263,8 +1237,8 @@ struct Solver {
       if constexpr (std::is_same<V, float>::value) {
         const long long n4 = pad4(n) / 4;
         k_cg_init4<<<resident_grid(k_cg_init4, n4), 256, 0, st>>>(
-            n4, lo, hi, s, g, Hs, mi, pc, r, p, w, ga, gb, zdir, H->scratch.partials,
-            H->scratch.counter, H->d_res);
+            n4, lo, hi, s, g, Hs, mi, pc, r, p, w, ga, gb, H->scratch.partials, H->scratch.counter,
+            H->d_res);
         ck(cudaGetLastError(), "cg_init");
         S.launches += 1;
         if (graph) {
