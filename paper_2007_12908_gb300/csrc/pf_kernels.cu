@@ -329,8 +329,9 @@ __global__ void __launch_bounds__(TS::THREADS, sizeof(TC) == 4 ? 2 : 1)
 // with 8 16-byte shared loads at fixed offsets, and the colour-phase sums
 // add one float4 per node.  Same element algebra and the same fixed
 // summation order as k_elem_scatter<3, float, ..., OP_HESS>.
-// T: tile edge in nodes, 8 (256 threads, three element rounds) or 4 (128
-// threads, one round) for grids too small to give every SM two 8^3 tiles.
+// T: tile edge in nodes, 8 (128 threads, six element rounds, four CTAs per
+// SM) or 4 (128 threads, one round) for grids too small to give every SM
+// two 8^3 tiles.
 template <int T>
 struct HessTile {
   static constexpr int THREADS = 128;  // four CTAs per SM at 128 registers (8^3 tiles)
