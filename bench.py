@@ -162,6 +162,28 @@ def job_seconds_per_load_step(rank_seconds, dist=None, device="cpu"):
     return slowest, slowest / dist.get_world_size()
 
 
+def shard_instances(n, rank, world):
+    """The instances of an n-instance batch that rank `rank` of `world`
+    solves: round-robin, so every rank gets a like mix of the draw's sizes
+    (the draw is sorted by size) and every instance is solved once."""
+    return [i for i in range(n) if i % world == rank]
+
+
+def batched_job(rank_seconds, rank_dofs, dist=None, device="cpu"):
+    """Strong scaling of the batched workload over the ranks: each rank
+    times its own share of the instances; the job lasts as long as the
+    slowest rank and covers every rank's dofs.  Returns (the slowest rank's
+    seconds per batch step, the batch's total dofs); a collective call."""
+    if dist is None:
+        return rank_seconds, rank_dofs
+    import torch
+    t = torch.tensor([float(rank_seconds)], dtype=torch.float64, device=device)
+    d = torch.tensor([float(rank_dofs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(d, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(d.item())
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -1108,9 +1130,10 @@ def time_batched_ops(pf, torch, Hs, states, K, bps=0):
             "speedup_vs_one_launch_per_instance": one / us, "launches_timed": K}
 
 
-def batched_instances(pf, torch, count, streams, stride=1):
+def batched_instances(pf, torch, count, streams, stride=1, pick=None):
     sizes, counts = PI.batched_grid_draw(PI.SEED_2D_BATCHED, 64)
-    pick = list(range(0, 64, stride))[:count]
+    if pick is None:
+        pick = list(range(0, 64, stride))[:count]
     Hs, xs = [], []
     for i in pick:
         n, nf = sizes[i], counts[i]
@@ -1150,12 +1173,20 @@ def run_batched(args):
     1025^2 nodes; 10-1000 line fractures, +-30 deg families) run
     concurrently, each on its own stream, by the library's host workers."""
     import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2007_12908_gb300 import build
     build.build()
     import paper_2007_12908_gb300 as pf
     prm = pf.default_params(precision=pf.PF_FP32 if args.precision == "mixed" else pf.PF_FP64,
                             start=pf.PF_START_EXTRAPOLATE if args.start == "extrapolate" else pf.PF_START_PLAIN)
-    sizes, counts, Hs, xs = batched_instances(pf, torch, 64, True)
+    # the 64 instances are independent: each rank solves its share, no
+    # collective on the data path
+    sizes, counts, Hs, xs = batched_instances(pf, torch, 64, True, pick=shard_instances(64, rank, world))
     dofs = sum(H.ndof() for H in Hs)
     # the tile autotuner on every instance (per level: the fastest FP32
     # Hessian tile variant, measured), unless --no-autotune
@@ -1170,9 +1201,13 @@ def run_batched(args):
         for H in Hs:
             pf.pressure_set(H, 1e-3 * t)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         out = pf.rmtr_load_step_batch(Hs, xs, prm, n_threads=threads, check=False)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         return time.perf_counter() - t0, out
 
     for t in range(1, args.warmup + 1):
@@ -1185,18 +1220,24 @@ def run_batched(args):
         times.append(dt)
         outs.append(out)
     clk = clocks.stop()
-    sec = statistics.mean(times)
-    ops = time_batched_ops(pf, torch, Hs, xs, 20)
+    sec, total_dofs = batched_job(statistics.mean(times), dofs, dist, "cuda")
+    ops = time_batched_ops(pf, torch, Hs, xs, 20) if world == 1 else None
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
     line = {
         "metric": "batched RMTR load steps: GDoF/s over 64 uneven 2D instances",
-        "value": dofs / sec / 1e9, "unit": "GDoF/s (load steps)", "n_gpus": 1,
+        "value": total_dofs / sec / 1e9, "unit": "GDoF/s (load steps)", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
-        "config": {"workload": "2d_batched_64_uneven_129-1025", "instances": len(Hs), "dofs": dofs,
-                   "sizes": sizes, "fractures": counts, "precision": args.precision,
-                   "start": args.start, "threads": args.batch_threads or len(Hs)},
-        "instances_per_s": len(Hs) / sec,
+        "config": {"workload": "2d_batched_64_uneven_129-1025", "instances": 64, "dofs": total_dofs,
+                   "instances_on_rank0": len(Hs), "sizes_on_rank0": sizes,
+                   "fractures_on_rank0": counts, "precision": args.precision,
+                   "start": args.start, "threads": args.batch_threads or len(Hs),
+                   "parallelism": f"instances sharded round-robin over {world} GPU(s)"},
+        "instances_per_s": 64 / sec,
         "tile_variants": {k: v[0] for k, v in tuned.items()},
         "converged": [sum(o["converged"] for o in out) for out in outs],
         "cycles_mean": [statistics.mean(o["cycles"] for o in out) for out in outs],
