@@ -77,3 +77,29 @@ def test_energy_noalloc_leaves_device_memory_unchanged():
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
     assert float(out.item()) == first  # fixed-order reduction: the same value every call
+
+
+def test_energy_noalloc_captures_in_global_mode():
+    """After the first call, the call records into a CUDA graph under
+    global capture mode, where any device allocation (in any thread) would
+    invalidate the capture; the replayed graph gives the same energy."""
+    torch = require_cuda()
+    from paper_2007_12908_gb300 import _binding as B
+    n = (33, 33, 33)
+    N = n[0] * n[1] * n[2]
+    x = dev(PI.random_state(11, 3, N, u_scale=1e-3, c_hi=1.0), torch.float64)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    args = (3, n, 1 / 32, 1.0, 0.25, 1.0, 2 / 32, 0.0, 1e-3, x, out)
+    B.energy_noalloc(*args)
+    torch.cuda.synchronize()
+    ref = float(out.item())
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="global"):
+        B.energy_noalloc(*args, stream=s)
+    out.zero_()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(out.item()) == ref
